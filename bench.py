@@ -1,0 +1,365 @@
+"""Benchmark of the w-stacking imager hot path on GB300.
+
+One step = the whole path for one dirty image of the 4096^2 / 32 w-plane /
+1e7-visibility workload (256 antennas in a 20 km disk, 6 h Earth-rotation
+synthesis at dec -30, 10 s integrations, 1.4 GHz, 200-source sky + noise,
+Kaiser-Bessel support 7): reset, placement + counting sort, gridding of all
+planes, per-plane inverse FFT, phase-screen stack and finalisation.  Inputs
+are resident in HBM when the timed region starts; the planes (4.3 GB) are
+larger than L2, so no L2 flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank images its own copy of the workload (the path
+has no exchange step: replicas, weak scaling); value = all ranks' visibilities
+/ the slowest rank's time.  ``--impl reference`` times the FP64 CPU oracle on
+the host cores on a bounded sample of the same workload (rank 0 only).
+"""
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "visibilities/sec end-to-end (grid+FFT+w-stack), % roofline, J/solution"
+WORKLOAD = ("plain w-stacking, 4096x4096 grid, 32 w-planes, 1e7 visibilities (256 antennas, 20 km disk, "
+            "6 h synthesis, dec -30, 10 s, 1.4 GHz, 200 sources + noise), Kaiser-Bessel support 7, FP32")
+DATA = "synthetic: seeded Earth-rotation synthesis + point-source sky (the paper's LOFAR data is not available)"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_hash(name):
+    with open(os.path.join(ROOT, "paper_2504_00959_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _traffic(kernel_file, workload_key):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current source of the kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[workload_key]
+        if e.get("source_sha256_16") != _kernel_hash(kernel_file):
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ energy
+class Nvml:
+    def __init__(self, uuid):
+        self.ok = False
+        try:
+            self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.lib.nvmlInit_v2() != 0:
+                return
+            self.h = ctypes.c_void_p()
+            if self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) != 0:
+                return
+            self.ok = True
+        except Exception:
+            self.ok = False
+
+    def energy_mj(self):
+        if not self.ok:
+            return None
+        e = ctypes.c_ulonglong(0)
+        if self.lib.nvmlDeviceGetTotalEnergyConsumption(self.h, ctypes.byref(e)) != 0:
+            return None
+        return int(e.value)
+
+
+# ------------------------------------------------------------ CPU baseline
+def oracle_sample(prob_np, planes):
+    """Time the FP64 oracle on planes [k0, k1) of the full workload: gridding
+    (all measurements placed, those of the sample planes gridded) and the
+    FFT + stack of the sample planes; extrapolate to the whole workload
+    (gridding by the number of measurements, FFT + stack by the number of
+    planes).  Returns (visibilities/s, sample description, threads)."""
+    import numpy as np
+
+    import oracle
+    p = prob_np
+    q = p["params"]
+    k0, k1 = planes
+    k, _, _ = oracle.place(q, p["u"], p["v"], p["w"])
+    m_all = int((k >= 0).sum())
+    m_s = int(((k >= k0) & (k < k1)).sum())
+    t0 = time.perf_counter()
+    oracle.grid(q, p["u"], p["v"], p["w"], p["wt"], p["vis"], k0=k0, k1=k1)
+    t_grid = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.dirty_image(q, p["u"], p["v"], p["w"], p["wt"], p["vis"], k0=k0, k1=k1)
+    t_full = time.perf_counter() - t0
+    t_rest = max(t_full - t_grid, 0.0)
+    t_est = t_grid * (m_all / max(m_s, 1)) + t_rest * (q["nw"] / (k1 - k0))
+    desc = (f"planes {k0}-{k1 - 1} of {q['nw']} ({m_s} of {m_all} visibilities gridded, all placed): "
+            f"grid {t_grid:.2f} s scaled x{m_all / max(m_s, 1):.1f}, FFT+stack {t_rest:.2f} s scaled "
+            f"x{q['nw'] / (k1 - k0):.0f}; measured {t_grid + t_full:.1f} s")
+    del np
+    return m_all / t_est, desc, oracle.num_threads(), t_grid + t_full
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--nvis", type=int, default=10_000_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import synth
+    import paper_2504_00959_gb300 as rick
+    from paper_2504_00959_gb300 import build as rick_build
+    rick_build.build()
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    prob = synth.config2(device=dev, m=args.nvis)
+    params = dict(prob["params"], flags=synth.FLAG_CORRECT | synth.FLAG_REAL)
+    im = rick.Imager(params, device=dev)
+    img = torch.empty((params["n"], params["n"]), dtype=torch.float32, device=dev)
+    m = prob["u"].numel()
+
+    def step():
+        im.reset()
+        im.grid(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"])
+        im.image(out=img)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    st = im.stats()
+
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", ""))
+    uuid = uuid if uuid.startswith("GPU-") else ("GPU-" + uuid if uuid else "")
+    nvml = Nvml(uuid) if uuid else None
+    clocks = ClockSampler(uuid if uuid else local)
+    im.set_timing(True)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = nvml.energy_mj() if nvml else None
+    start.record()
+    for _ in range(args.steps):
+        step()
+    end.record()
+    torch.cuda.synchronize()
+    e1 = nvml.energy_mj() if nvml else None
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = start.elapsed_time(end)
+    tm = im.timing()
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / max(args.steps, 1)
+    value = world * m * args.steps / (ms / 1e3)
+
+    # ------------------------------------------------ roofline (gridder)
+    peak, peak_kind = _peaks()
+    n, nw = params["n"], params["nw"]
+    grid_launch_ms = tm["grid_ms"] / max(tm["grid_calls"], 1)
+    grid_bytes = 16.0 * st["n_gridded"] + 8.0 * nw * n * n
+    achieved = grid_bytes / (grid_launch_ms / 1e3) / 1e9
+    traffic = _traffic("rick_grid.cu", "k_grid@4096x32x1e7")
+    stack_ms = tm["stack_ms"] / max(tm["stack_calls"], 1)
+    stack_bytes = 8.0 * nw * n * n + 4.0 * n * n
+    fft_ms = tm["fft_ms"] / max(tm["fft_calls"], 1)
+    fft_bytes = 2 * 2 * 8.0 * nw * n * n  # two passes, read + write
+    prep_ms = tm["prep_ms"] / max(tm["prep_calls"], 1)
+    prep_bytes = 2 * 24.0 * m + 16.0 * st["n_entries"]
+    phases = {
+        "prep": {"ms": prep_ms, "algorithmic_gb": prep_bytes / 1e9, "gbs": prep_bytes / prep_ms / 1e6},
+        "grid": {"ms": grid_launch_ms, "algorithmic_gb": grid_bytes / 1e9, "gbs": achieved},
+        "fft_cufft": {"ms": fft_ms, "algorithmic_gb": fft_bytes / 1e9, "gbs": fft_bytes / fft_ms / 1e6},
+        "stack": {"ms": stack_ms, "algorithmic_gb": stack_bytes / 1e9, "gbs": stack_bytes / stack_ms / 1e6},
+    }
+    for v in phases.values():
+        v["frac_of_" + peak_kind] = v["gbs"] / peak
+
+    # ------------------------------------------------ end to end, host buffers
+    e2e = None
+    if rank == 0 or world > 1:
+        hv = prob["vis"].cpu().pin_memory()
+        hu, hvv, hw, hwt = (prob[k].cpu().pin_memory() for k in ("u", "v", "w", "wt"))
+        himg = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        im.image_host(hv, hu, hvv, hw, hwt, out=himg)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ksteps = max(min(args.steps, 5), 1)
+        for _ in range(ksteps):
+            im.image_host(hv, hu, hvv, hw, hwt, out=himg)
+        te = (time.perf_counter() - t0) / ksteps
+        e2e = {"value": m / te, "unit": "vis/s", "ms_per_step": te * 1e3,
+               "h2d_bytes_per_step": int(m * (8 + 4 + 4 + 4 + 4)), "d2h_bytes_per_step": int(n * n * 4),
+               "api": "rick_image_host (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        prob_np = synth.to_numpy(prob)
+        v, desc, threads, secs = oracle_sample(prob_np, (15, 17))
+        cpu = {"value": v, "unit": "vis/s", "cores": threads, "kind": "oracle", "sample": desc}
+
+    energy = None
+    if e0 is not None and e1 is not None:
+        energy = (e1 - e0) / 1e3 / max(args.steps, 1)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "vis/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": DATA,
+        "config": {"workload": WORKLOAD, "n": n, "nw": nw, "nvis": m, "kernel": "kaiser-bessel", "support": 7,
+                   "tile": st["tile"], "plane_group": st["plane_group"],
+                   "l2": "inputs larger than L2 (4.3 GB of planes written and read every step)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"kernel": "k_grid (gridding, Eq. 3)", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": grid_bytes,
+                     "launch_ms": grid_launch_ms},
+        "phases": phases,
+        "energy_j_per_solution": energy,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "gpu_launches": int(tm["kernel_launches"]),
+        "clocks": clk,
+        "roofline_frac_end_to_end": None,
+    }
+    # whole step against HBM: inputs + plane write + FFT (2 passes) + stack read + image
+    step_bytes = 24.0 * m + 8.0 * nw * n * n + fft_bytes + stack_bytes
+    out["roofline_frac_end_to_end"] = step_bytes / (ms_step / 1e3) / 1e9 / peak
+    if rank == 0:
+        print(json.dumps(out))
+    im.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args, rank, world):
+    """The FP64 oracle on the host cores: every step images a bounded sample
+    (one w-plane of the full workload), extrapolated to the whole workload."""
+    if rank != 0:
+        return
+    import synth
+    import oracle
+    oracle.lib()
+    prob = synth.to_numpy(synth.config2(device="cpu", m=args.nvis))
+    vals = []
+    t_all = 0.0
+    desc = ""
+    threads = oracle.num_threads()
+    for i in range(args.warmup + args.steps):
+        v, desc, threads, secs = oracle_sample(prob, (16, 17))
+        if i >= args.warmup:
+            vals.append(v)
+            t_all += secs
+    value = statistics.median(vals) if vals else None
+    m = prob["u"].shape[0]
+    out = {
+        "metric": METRIC, "value": value, "unit": "vis/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": (m / value * 1e3) if value else None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": DATA, "impl": "reference",
+        "config": {"workload": WORKLOAD, "n": prob["params"]["n"], "nw": prob["params"]["nw"], "nvis": m},
+        "cpu_baseline": {"value": value, "unit": "vis/s", "cores": threads, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "vis/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

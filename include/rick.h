@@ -1,0 +1,193 @@
+/*
+ * rick.h -- C ABI of librick, a GB300 (sm_103a) w-stacking imager: the hot
+ * path of RICK (arXiv 2504.00959) -- convolutional gridding onto w-planes,
+ * a per-plane 2D inverse FFT, and the w-term phase-screen correction that
+ * stacks the planes into one dirty image.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Coordinates u, v, w are in wavelengths (float32 arrays of length nvis).
+ *   Visibilities are complex64: interleaved (re, im) float32 pairs, 2*nvis
+ *   floats.  Weights are float32 (NULL = unit weights).
+ * - Grid: n x n cells per w-plane, cell j <-> u = (j - n/2) * du with
+ *   du = 1 / (n * pixel_rad); planes are row-major [v cell][u cell].
+ * - Image: n x n pixels, row-major [y][x]; pixel (x, y) <-> l = (x - n/2) *
+ *   pixel_rad, m = (y - n/2) * pixel_rad; the phase centre is pixel (n/2, n/2).
+ * - w-planes: nw uniform bins over [w_min, w_max]; a measurement goes to the
+ *   plane floor((w - w_min) / dw) clamped to [0, nw-1] (the closest plane,
+ *   Sec. 2.1); plane k has centre w_k = w_min + (k + 1/2) dw.
+ * - Kernel footprint: cells f .. f+S-1 on each axis, f = floor(p - S/2) + 1,
+ *   p = u / du + n/2; taps normalised to sum 1 per axis.  A measurement whose
+ *   footprint leaves the grid, or with a non-finite coordinate, weight or
+ *   value, is dropped and counted (not an error).
+ * - Device pointers unless a call says "host".  All work is enqueued on the
+ *   handle's stream (rick_set_stream); calls return once the work is
+ *   enqueued, except where a call says it synchronises.  Caller-owned buffers
+ *   must stay valid until that work has run.  The library owns only its
+ *   internal workspace, plans and handles.
+ * - Every call returns a rick_status; RICK_OK (0) on success.  No exceptions
+ *   cross the ABI and no device trap is used.  rick_last_error(h) gives a
+ *   message for the last failure on h.
+ * - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef RICK_H
+#define RICK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t rick_status;
+#define RICK_OK 0
+#define RICK_ERR_ARG 1      /* invalid argument (null pointer, bad size, bad parameter) */
+#define RICK_ERR_OOM 2      /* device memory would not fit; nothing was launched */
+#define RICK_ERR_CUDA 3     /* a CUDA runtime call failed */
+#define RICK_ERR_CUFFT 4    /* a cuFFT call failed */
+#define RICK_ERR_TIMEOUT 5  /* a bounded device wait ran out */
+#define RICK_ERR_STATE 6    /* call out of order (e.g. degrid before any grid) */
+
+#define RICK_KERNEL_GAUSS 0 /* exp(-x^2 / (2 sigma^2)), kernel_param = sigma in cells (0: S/6) */
+#define RICK_KERNEL_KB 1    /* I0(beta sqrt(1 - (2x/S)^2)), kernel_param = beta (0: 2.34 S) */
+
+#define RICK_GRID_CORRECT 1u   /* divide the image by the kernel's Fourier transform (taper) */
+#define RICK_REAL_IMAGE 2u     /* output Re(image) as float[n*n]; else complex float[2*n*n] */
+#define RICK_APPLY_N 4u        /* multiply the image by n = sqrt(1 - l^2 - m^2) (Eq. 1 LHS) */
+#define RICK_UNIFORM_WEIGHT 8u /* weight / (gridded measurements sharing the nearest cell) */
+
+/* Problem statement of Sec. 2.1: grid size, pixel scale, w-planes, kernel.
+ * n: grid side, even, >= 2*support.  nw >= 1.  w_max > w_min when nw > 1.
+ * support: kernel support S in cells, 1..16.  plane_group: w-planes resident
+ * in HBM at once (0 = as many as fit).  tile: uv tile side of the gridder,
+ * 16, 32 or 64 (0 = automatic); must be >= support. */
+typedef struct rick_params {
+    int32_t n;
+    int32_t nw;
+    double pixel_rad;
+    double w_min;
+    double w_max;
+    int32_t kernel;
+    int32_t support;
+    double kernel_param;
+    int32_t plane_group;
+    int32_t tile;
+    uint32_t flags;
+    int32_t reserved;
+} rick_params;
+
+typedef struct rick_stats {
+    int64_t n_gridded;      /* measurements gridded since the last reset */
+    int64_t n_dropped;      /* measurements dropped since the last reset */
+    int64_t n_entries;      /* (measurement, tile) entries after footprint splitting */
+    double sum_weights;     /* sum of the effective weights gridded */
+    int32_t plane_group;    /* planes resident per group */
+    int32_t tile;           /* uv tile side in use */
+    int64_t workspace_bytes;/* device bytes the handle holds */
+} rick_stats;
+
+typedef struct rick_imager* rick_handle;
+
+/* Fill *p with defaults (Gaussian, support 7, grid correction + real image). */
+rick_status rick_params_default(rick_params* p);
+
+/* Create an imager for the problem *p on the current CUDA device: plans, taper,
+ * plane buffers.  Fails with RICK_ERR_OOM (and allocates nothing) when the
+ * plane group does not fit in free device memory. *out receives the handle. */
+rick_status rick_create(const rick_params* p, rick_handle* out);
+
+/* Release every resource of h (synchronises its stream).  NULL is a no-op. */
+rick_status rick_destroy(rick_handle h);
+
+/* Enqueue all later work of h on `cuda_stream` (a cudaStream_t; NULL = legacy
+ * default stream). */
+rick_status rick_set_stream(rick_handle h, void* cuda_stream);
+
+/* Device bytes rick_create + one rick_grid of max_vis measurements need. */
+rick_status rick_workspace_size(const rick_params* p, int64_t max_vis, size_t* bytes);
+
+/* Forget all gridded measurements, weight sums, counters and the uniform-
+ * weighting density. */
+rick_status rick_reset(rick_handle h);
+
+/* Step 1-2 of the workflow (Sec. 2.1) for one chunk of measurements: place
+ * each on its w-plane and footprint, bin by (w-plane, uv tile) with a
+ * counting sort, and store the weighted visibility with its continuous cell
+ * coordinates.  Calls accumulate (chunks, Sec. 2.2); the planes themselves
+ * are gridded (Eq. 3) inside rick_fft_and_stack, so the inputs may be freed
+ * as soon as this call's work has run.  vis: float[2*nvis]; u, v, w:
+ * float[nvis]; weights: float[nvis] or NULL.  nvis >= 0. */
+rick_status rick_grid(rick_handle h, const float* vis, const float* u, const float* v,
+                      const float* w, const float* weights, int64_t nvis);
+
+/* Uniform weighting over several chunks: add the nearest-cell counts of one
+ * chunk to the density grid before the first rick_grid of the batch.  With a
+ * single chunk rick_grid computes the density itself. */
+rick_status rick_add_density(rick_handle h, const float* vis, const float* u, const float* v,
+                             const float* w, const float* weights, int64_t nvis);
+
+/* Steps 2-4 of the workflow for everything gridded since the last reset:
+ * for each plane group, grid the planes (Eq. 3), inverse-FFT each plane
+ * (cuFFT, unnormalised, exponent +), multiply by the phase screen
+ * exp(+2 pi i w_k (n-1)) and sum over planes (Eq. 1); then divide by the
+ * weight sum and, per flags, by the taper and times n.  image: float[n*n]
+ * (RICK_REAL_IMAGE) or float[2*n*n] complex, fully overwritten. */
+rick_status rick_fft_and_stack(rick_handle h, float* image);
+
+/* Eq. 3 alone: the gridded planes k0 .. k0+nk-1 as complex float
+ * [nk][n][n] (no fftshift sign), fully overwritten. */
+rick_status rick_grid_planes(rick_handle h, int32_t k0, int32_t nk, float* planes);
+
+/* Adjoint of the measurement-to-image map (degridding; not in the paper):
+ * vis_grad = A^H image_grad, where A maps visibilities to the image
+ * rick_fft_and_stack would produce for the measurements (u, v, w, weights)
+ * with the current weight sum and density.  image_grad: float[n*n]
+ * (RICK_REAL_IMAGE) or float[2*n*n]; vis_grad: float[2*nvis] (complex),
+ * overwritten; dropped measurements get 0.  Planes are recomputed from
+ * image_grad per plane group (phase screen conjugate, forward FFT, gather
+ * with the same taps).  RICK_ERR_STATE when nothing has been gridded. */
+rick_status rick_degrid(rick_handle h, const float* image_grad, const float* u, const float* v,
+                        const float* w, const float* weights, int64_t nvis, float* vis_grad);
+
+/* End to end with HOST buffers: copy the inputs to the device, reset, grid,
+ * fft_and_stack, copy the image back to image_host, synchronise.  Host
+ * arrays as in rick_grid / rick_fft_and_stack (pinned memory is faster). */
+rick_status rick_image_host(rick_handle h, const float* vis_host, const float* u_host,
+                            const float* v_host, const float* w_host,
+                            const float* weights_host, int64_t nvis, float* image_host);
+
+/* Counters since the last reset (synchronises the stream). */
+rick_status rick_get_stats(rick_handle h, rick_stats* out);
+
+/* Per-phase device time of the library's own work, from CUDA events recorded
+ * on the handle's stream around each phase (no synchronisation while timing
+ * is on).  Phases: prep = placement + counting sort (rick_grid); grid = the
+ * gridding kernel (Eq. 3); fft = cuFFT plane transforms; stack = phase screen
+ * + plane reduction + finalisation; degrid = the whole adjoint.  Times are
+ * sums over all calls since timing was enabled; *_calls count the phase
+ * executions; kernel_launches counts librick's own kernel launches (cuFFT's
+ * not included). */
+typedef struct rick_timing {
+    double prep_ms, grid_ms, fft_ms, stack_ms, degrid_ms;
+    int64_t prep_calls, grid_calls, fft_calls, stack_calls, degrid_calls;
+    int64_t kernel_launches;
+} rick_timing;
+
+/* Turn phase timing on (enable != 0, resets the sums) or off. */
+rick_status rick_set_timing(rick_handle h, int32_t enable);
+
+/* Phase times since timing was enabled (synchronises the stream). */
+rick_status rick_get_timing(rick_handle h, rick_timing* out);
+
+/* Message for the last failure on h (static storage of the handle). */
+const char* rick_last_error(rick_handle h);
+
+/* Name of a status code. */
+const char* rick_status_string(rick_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RICK_H */

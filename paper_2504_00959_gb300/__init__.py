@@ -1,0 +1,231 @@
+"""GB300 (sm_103a) w-stacking imager -- the hot path of RICK (arXiv 2504.00959).
+
+Python binding over the C ABI of ``librick.so`` (include/rick.h).  PyTorch is
+used for device memory and streams only; gridding (Eq. 3), the per-plane
+inverse FFT (cuFFT), the w-term phase-screen stack (Eq. 1) and the adjoint
+degridder all run in the library.  There is no CPU fallback: constructing an
+``Imager`` without the built library, or with tensors that are not on a CUDA
+device, raises.
+
+Parameters are a mapping with keys ``n``, ``nw``, ``pixel_rad``, ``w_min``,
+``w_max``, ``kernel`` (0 Gaussian, 1 Kaiser-Bessel), ``support``,
+``kernel_param`` (0 = default sigma S/6 / beta 2.34 S), ``flags``
+(GRID_CORRECT | REAL_IMAGE | APPLY_N | UNIFORM_WEIGHT), and optionally
+``plane_group`` and ``tile``.
+"""
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import (APPLY_N, GRID_CORRECT, KERNEL_GAUSS, KERNEL_KB, REAL_IMAGE, UNIFORM_WEIGHT,  # noqa: F401
+                   RickError)
+
+__all__ = ["Imager", "DirtyImage", "dirty_image", "RickError", "load", "KERNEL_GAUSS", "KERNEL_KB",
+           "GRID_CORRECT", "REAL_IMAGE", "APPLY_N", "UNIFORM_WEIGHT"]
+
+
+def load():
+    """Load librick.so (raises when it is not built)."""
+    return _lib.load()
+
+
+def _params_struct(p):
+    rp = _lib.RickParams()
+    rp.n = int(p["n"])
+    rp.nw = int(p["nw"])
+    rp.pixel_rad = float(p["pixel_rad"])
+    rp.w_min = float(p["w_min"])
+    rp.w_max = float(p["w_max"])
+    rp.kernel = int(p["kernel"])
+    rp.support = int(p["support"])
+    rp.kernel_param = float(p.get("kernel_param", 0.0) or 0.0)
+    rp.plane_group = int(p.get("plane_group", 0) or 0)
+    rp.tile = int(p.get("tile", 0) or 0)
+    rp.flags = int(p.get("flags", GRID_CORRECT | REAL_IMAGE))
+    rp.reserved = 0
+    return rp
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(None)
+
+
+class Imager:
+    """One w-stacking problem (grid size, pixel scale, w-planes, kernel) on one GPU.
+
+    ``grid`` may be called once per chunk of measurements; ``image`` runs the
+    per-plane FFT and the w-stack for everything gridded since ``reset``.
+    All work goes to the current torch CUDA stream of the imager's device.
+    """
+
+    def __init__(self, params, device=None):
+        self.params = dict(params)
+        self._L = _lib.load()
+        if device is None:
+            device = torch.device("cuda", torch.cuda.current_device())
+        self.device = torch.device(device)
+        if self.device.type != "cuda":
+            raise ValueError("Imager needs a CUDA device")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self._rp = _params_struct(self.params)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(self._L.rick_create(ctypes.byref(self._rp), ctypes.byref(h)))
+        self._h = h
+        self.generation = 0
+
+    # -------------------------------------------------------------- helpers
+    @property
+    def n(self):
+        return self._rp.n
+
+    @property
+    def real(self):
+        return bool(self._rp.flags & REAL_IMAGE)
+
+    def _sync_stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        _lib.check(self._L.rick_set_stream(self._h, ctypes.c_void_p(s)), self._h)
+
+    def _vec(self, t, name, dtype, m=None):
+        if t is None:
+            return None
+        if not isinstance(t, torch.Tensor) or t.device != self.device:
+            raise ValueError(f"{name} must be a tensor on {self.device}")
+        if t.dtype != dtype:
+            raise ValueError(f"{name} must be {dtype} (got {t.dtype})")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if m is not None and t.numel() != m:
+            raise ValueError(f"{name} has {t.numel()} elements, expected {m}")
+        return t
+
+    def _inputs(self, vis, u, v, w, wt):
+        m = u.numel()
+        return (self._vec(vis, "vis", torch.complex64, m), self._vec(u, "u", torch.float32, m),
+                self._vec(v, "v", torch.float32, m), self._vec(w, "w", torch.float32, m),
+                self._vec(wt, "wt", torch.float32, m), m)
+
+    # ------------------------------------------------------------------ API
+    def reset(self):
+        self._sync_stream()
+        _lib.check(self._L.rick_reset(self._h), self._h)
+        self.generation += 1
+
+    def add_density(self, vis, u, v, w, wt=None):
+        vis, u, v, w, wt, m = self._inputs(vis, u, v, w, wt)
+        self._sync_stream()
+        _lib.check(self._L.rick_add_density(self._h, _ptr(vis), _ptr(u), _ptr(v), _ptr(w), _ptr(wt), m), self._h)
+
+    def grid(self, vis, u, v, w, wt=None):
+        vis, u, v, w, wt, m = self._inputs(vis, u, v, w, wt)
+        self._sync_stream()
+        _lib.check(self._L.rick_grid(self._h, _ptr(vis), _ptr(u), _ptr(v), _ptr(w), _ptr(wt), m), self._h)
+        self.generation += 1
+
+    def image(self, out=None):
+        n = self.n
+        if out is None:
+            out = torch.empty((n, n), dtype=torch.float32 if self.real else torch.complex64, device=self.device)
+        self._vec(out, "out", torch.float32 if self.real else torch.complex64, n * n)
+        self._sync_stream()
+        _lib.check(self._L.rick_fft_and_stack(self._h, _ptr(out)), self._h)
+        return out
+
+    def grid_planes(self, k0=0, nk=None):
+        nk = self._rp.nw - k0 if nk is None else nk
+        out = torch.empty((nk, self.n, self.n), dtype=torch.complex64, device=self.device)
+        self._sync_stream()
+        _lib.check(self._L.rick_grid_planes(self._h, int(k0), int(nk), _ptr(out)), self._h)
+        return out
+
+    def degrid(self, image_grad, u, v, w, wt=None, out=None):
+        n = self.n
+        m = u.numel()
+        image_grad = self._vec(image_grad.contiguous(), "image_grad",
+                               torch.float32 if self.real else torch.complex64, n * n)
+        u, v, w = (self._vec(u, "u", torch.float32, m), self._vec(v, "v", torch.float32, m),
+                   self._vec(w, "w", torch.float32, m))
+        wt = self._vec(wt, "wt", torch.float32, m)
+        if out is None:
+            out = torch.empty(m, dtype=torch.complex64, device=self.device)
+        self._vec(out, "out", torch.complex64, m)
+        self._sync_stream()
+        _lib.check(self._L.rick_degrid(self._h, _ptr(image_grad), _ptr(u), _ptr(v), _ptr(w), _ptr(wt), m,
+                                       _ptr(out)), self._h)
+        return out
+
+    def image_host(self, vis, u, v, w, wt=None, out=None):
+        """End to end with host (CPU) tensors, through rick_image_host."""
+        m = u.numel()
+        for name, t, dt in (("vis", vis, torch.complex64), ("u", u, torch.float32), ("v", v, torch.float32),
+                            ("w", w, torch.float32)):
+            if t.device.type != "cpu" or t.dtype != dt or not t.is_contiguous() or t.numel() != m:
+                raise ValueError(f"{name} must be a contiguous {dt} CPU tensor of {m} elements")
+        if wt is not None and (wt.device.type != "cpu" or wt.dtype != torch.float32 or wt.numel() != m):
+            raise ValueError("wt must be a float32 CPU tensor")
+        n = self.n
+        if out is None:
+            out = torch.empty((n, n), dtype=torch.float32 if self.real else torch.complex64)
+        self._sync_stream()
+        _lib.check(self._L.rick_image_host(self._h, _ptr(vis), _ptr(u), _ptr(v), _ptr(w), _ptr(wt), m,
+                                           _ptr(out)), self._h)
+        self.generation += 1
+        return out
+
+    def stats(self):
+        st = _lib.RickStats()
+        _lib.check(self._L.rick_get_stats(self._h, ctypes.byref(st)), self._h)
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def set_timing(self, enable=True):
+        _lib.check(self._L.rick_set_timing(self._h, 1 if enable else 0), self._h)
+
+    def timing(self):
+        t = _lib.RickTiming()
+        _lib.check(self._L.rick_get_timing(self._h, ctypes.byref(t)), self._h)
+        return {f: getattr(t, f) for f, _ in t._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.rick_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DirtyImage(torch.autograd.Function):
+    """Differentiable dirty image D(V) (linear in V).  Backward: the hand-written
+    adjoint degridder, grad_V = A^H grad_D, with w-planes recomputed from grad_D.
+    The imager must not be regridded between forward and backward."""
+
+    @staticmethod
+    def forward(ctx, vis, u, v, w, wt, imager):
+        imager.reset()
+        imager.grid(vis.detach().contiguous(), u, v, w, wt)
+        img = imager.image()
+        ctx.imager = imager
+        ctx.generation = imager.generation
+        ctx.save_for_backward(u, v, w, wt if wt is not None else torch.empty(0, device=u.device))
+        ctx.has_wt = wt is not None
+        return img
+
+    @staticmethod
+    def backward(ctx, grad):
+        u, v, w, wt = ctx.saved_tensors
+        imager = ctx.imager
+        if imager.generation != ctx.generation:
+            raise RuntimeError("the imager was regridded between forward and backward")
+        g = imager.degrid(grad.contiguous(), u, v, w, wt if ctx.has_wt else None)
+        return g, None, None, None, None, None
+
+
+def dirty_image(vis, u, v, w, wt, imager):
+    """D = imager's dirty image of (vis, u, v, w, wt), differentiable in vis."""
+    return DirtyImage.apply(vis, u, v, w, wt, imager)

@@ -1,0 +1,681 @@
+// rick_api.cu -- the C ABI of librick (include/rick.h): handle, parameter
+// checks, device memory plan, cuFFT plans and the step sequence of the
+// workflow in Sec. 2.1 (grid -> per-plane FFT -> w-correction + reduction).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "rick_internal.cuh"
+
+using namespace rick;
+
+namespace {
+
+rick_status fail(rick_handle h, rick_status s, const char* fmt, ...)
+{
+    if (h) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(h->last_error, sizeof(h->last_error), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+#define RICK_CU(h, expr)                                                                         \
+    do {                                                                                         \
+        cudaError_t e_ = (expr);                                                                 \
+        if (e_ != cudaSuccess) return fail(h, RICK_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define RICK_FFT(h, expr)                                                           \
+    do {                                                                            \
+        cufftResult r_ = (expr);                                                    \
+        if (r_ != CUFFT_SUCCESS) return fail(h, RICK_ERR_CUFFT, "%s: cufft error %d", #expr, (int)r_); \
+    } while (0)
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+int ilog2(int x)
+{
+    int r = 0;
+    while ((1 << r) < x) ++r;
+    return r;
+}
+
+// Parameter checks; on success fills the derived configuration.
+rick_status check_params(const rick_params* p, GridCfg* c, double* kparam, char* msg, size_t msglen)
+{
+    if (!p) {
+        snprintf(msg, msglen, "params is NULL");
+        return RICK_ERR_ARG;
+    }
+    if (p->n < 4 || (p->n & 1) || p->n > 32768) {
+        snprintf(msg, msglen, "n must be even and in [4, 32768] (got %d)", p->n);
+        return RICK_ERR_ARG;
+    }
+    if (p->nw < 1 || p->nw > 65535) {
+        snprintf(msg, msglen, "nw must be in [1, 65535] (got %d)", p->nw);
+        return RICK_ERR_ARG;
+    }
+    if (!(p->pixel_rad > 0.0) || !std::isfinite(p->pixel_rad)) {
+        snprintf(msg, msglen, "pixel_rad must be positive and finite");
+        return RICK_ERR_ARG;
+    }
+    if (!std::isfinite(p->w_min) || !std::isfinite(p->w_max) ||
+        (p->nw > 1 && !(p->w_max > p->w_min)) || (p->nw == 1 && p->w_max < p->w_min)) {
+        snprintf(msg, msglen, "need finite w_min < w_max (w_min <= w_max when nw == 1)");
+        return RICK_ERR_ARG;
+    }
+    if (p->kernel != RICK_KERNEL_GAUSS && p->kernel != RICK_KERNEL_KB) {
+        snprintf(msg, msglen, "unknown kernel %d", p->kernel);
+        return RICK_ERR_ARG;
+    }
+    if (p->support < 1 || p->support > kMaxSupport || 2 * p->support > p->n) {
+        snprintf(msg, msglen, "support must be in [1, %d] and at most n/2 (got %d)", kMaxSupport, p->support);
+        return RICK_ERR_ARG;
+    }
+    if (!(p->kernel_param >= 0.0) || !std::isfinite(p->kernel_param)) {
+        snprintf(msg, msglen, "kernel_param must be >= 0 and finite");
+        return RICK_ERR_ARG;
+    }
+    if (p->plane_group < 0) {
+        snprintf(msg, msglen, "plane_group must be >= 0");
+        return RICK_ERR_ARG;
+    }
+    int T = p->tile ? p->tile : 32;
+    if (T != 16 && T != 32 && T != 64) {
+        snprintf(msg, msglen, "tile must be 0, 16, 32 or 64 (got %d)", p->tile);
+        return RICK_ERR_ARG;
+    }
+    if (T < p->support) {
+        if (p->tile) {
+            snprintf(msg, msglen, "tile %d smaller than support %d", T, p->support);
+            return RICK_ERR_ARG;
+        }
+        T = 32;
+    }
+    const uint32_t known = RICK_GRID_CORRECT | RICK_REAL_IMAGE | RICK_APPLY_N | RICK_UNIFORM_WEIGHT;
+    if (p->flags & ~known) {
+        snprintf(msg, msglen, "unknown flags 0x%x", p->flags & ~known);
+        return RICK_ERR_ARG;
+    }
+    double kp = p->kernel_param;
+    if (kp == 0.0) kp = (p->kernel == RICK_KERNEL_GAUSS) ? p->support / 6.0 : 2.34 * p->support;
+    *kparam = kp;
+    c->n = p->n;
+    c->nw = p->nw;
+    c->S = p->support;
+    c->T = T;
+    c->log2T = ilog2(T);
+    c->ntu = (p->n + T - 1) / T;
+    c->ntp = (int64_t)c->ntu * c->ntu;
+    c->uvscale = (float)((double)p->n * p->pixel_rad);
+    c->half_n = (float)(p->n / 2);
+    c->half_s = (float)(0.5 * p->support);
+    c->wmin = (float)p->w_min;
+    const double dw = (p->nw > 1) ? (p->w_max - p->w_min) / p->nw : (p->w_max - p->w_min);
+    c->invdw = (p->nw > 1) ? (float)(1.0 / dw) : 0.0f;
+    c->lim = (float)(p->n - p->support - 1);
+    c->kernel = p->kernel;
+    c->kp = (p->kernel == RICK_KERNEL_GAUSS) ? (float)(1.0 / (2.0 * kp * kp)) : (float)kp;
+    c->two_over_s = (float)(2.0 / p->support);
+    c->uniform = (p->flags & RICK_UNIFORM_WEIGHT) ? 1 : 0;
+    (void)is_pow2;
+    return RICK_OK;
+}
+
+void split(double x, float* hi, float* lo)
+{
+    *hi = (float)x;
+    *lo = (float)(x - (double)*hi);
+}
+
+size_t plane_bytes(const rick_params* p) { return (size_t)p->n * p->n * sizeof(float2); }
+
+rick_status get_plan(rick_handle h, int batch, cufftHandle* out)
+{
+    auto it = h->plans.find(batch);
+    if (it != h->plans.end()) {
+        *out = it->second;
+        return RICK_OK;
+    }
+    cufftHandle plan;
+    RICK_FFT(h, cufftCreate(&plan));
+    RICK_FFT(h, cufftSetAutoAllocation(plan, 0));
+    int dims[2] = {h->p.n, h->p.n};
+    size_t work = 0;
+    const long long dist = (long long)h->p.n * h->p.n;
+    cufftResult r = cufftMakePlanMany(plan, 2, dims, nullptr, 1, (int)dist, nullptr, 1, (int)dist, CUFFT_C2C,
+                                      batch, &work);
+    if (r != CUFFT_SUCCESS) {
+        cufftDestroy(plan);
+        return fail(h, RICK_ERR_CUFFT, "cufftMakePlanMany(n=%d, batch=%d): error %d", h->p.n, batch, (int)r);
+    }
+    if (work > h->fft_work_bytes) {
+        size_t fr = 0, tot = 0;
+        RICK_CU(h, cudaMemGetInfo(&fr, &tot));
+        if (work - h->fft_work_bytes + (64u << 20) > fr) {
+            cufftDestroy(plan);
+            return fail(h, RICK_ERR_OOM, "cuFFT work area of %zu bytes does not fit", work);
+        }
+        if (h->fft_work) {
+            RICK_CU(h, cudaStreamSynchronize(h->stream));
+            cudaFree(h->fft_work);
+            h->bytes_held -= h->fft_work_bytes;
+            h->fft_work = nullptr;
+            h->fft_work_bytes = 0;
+        }
+        RICK_CU(h, cudaMalloc(&h->fft_work, work));
+        h->fft_work_bytes = work;
+        h->bytes_held += work;
+        for (auto& kv : h->plans) RICK_FFT(h, cufftSetWorkArea(kv.second, h->fft_work));
+    }
+    RICK_FFT(h, cufftSetWorkArea(plan, h->fft_work));
+    RICK_FFT(h, cufftSetStream(plan, h->stream));
+    h->plans[batch] = plan;
+    *out = plan;
+    return RICK_OK;
+}
+
+void free_chunks(rick_handle h)
+{
+    for (auto& c : h->chunks) {
+        cudaFreeAsync(c.off, h->stream);
+        cudaFreeAsync(c.ent, h->stream);
+        h->bytes_held -= (size_t)(h->cfg.nw * h->cfg.ntp + 1) * sizeof(uint32_t) + (size_t)c.cap * sizeof(float4);
+    }
+    h->chunks.clear();
+}
+
+// Records CUDA events around one phase when timing is on.
+struct PhaseScope {
+    rick_handle h;
+    Phase ph;
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    PhaseScope(rick_handle h_, Phase ph_) : h(h_), ph(ph_)
+    {
+        if (!h->timer.on) return;
+        if (!h->timer.spare.empty()) {
+            ev = h->timer.spare.back();
+            h->timer.spare.pop_back();
+        } else if (cudaEventCreate(&ev.first) != cudaSuccess || cudaEventCreate(&ev.second) != cudaSuccess) {
+            ev = {nullptr, nullptr};
+            return;
+        }
+        cudaEventRecord(ev.first, h->stream);
+    }
+    ~PhaseScope()
+    {
+        if (!ev.first) return;
+        cudaEventRecord(ev.second, h->stream);
+        h->timer.pending[ph].push_back(ev);
+    }
+};
+
+void count_launches(rick_handle h, int64_t n) { h->timer.launches += n; }
+
+void resolve_timer(rick_handle h, bool accumulate)
+{
+    for (int ph = 0; ph < kNumPhases; ++ph) {
+        for (auto& ev : h->timer.pending[ph]) {
+            float ms = 0.f;
+            if (accumulate && cudaEventElapsedTime(&ms, ev.first, ev.second) == cudaSuccess) {
+                h->timer.ms[ph] += ms;
+                h->timer.calls[ph] += 1;
+            }
+            h->timer.spare.push_back(ev);
+        }
+        h->timer.pending[ph].clear();
+    }
+}
+
+int64_t entries_bound(const GridCfg& c, int64_t nvis) { return nvis * (c.S > 1 ? 4 : 1); }
+
+rick_status check_vis_args(rick_handle h, const float* vis, const float* u, const float* v, const float* w,
+                           int64_t nvis)
+{
+    if (nvis < 0) return fail(h, RICK_ERR_ARG, "nvis must be >= 0 (got %lld)", (long long)nvis);
+    if (nvis > 0 && (!vis || !u || !v || !w)) return fail(h, RICK_ERR_ARG, "vis, u, v, w must not be NULL");
+    if (nvis > (int64_t)1 << 30) return fail(h, RICK_ERR_ARG, "at most 2^30 measurements per call");
+    return RICK_OK;
+}
+
+// Grid planes [k0, k0 + nk) of every stored chunk into `planes`.
+rick_status grid_pass(rick_handle h, int k0, int nk, bool shift, float2* planes)
+{
+    PhaseScope scope(h, kPhaseGrid);
+    const size_t nch = h->chunks.size();
+    size_t c0 = 0;
+    do {
+        ChunkList cl{};
+        cl.count = 0;
+        for (size_t q = c0; q < nch && cl.count < kMaxChunksPerPass; ++q, ++cl.count) {
+            cl.off[cl.count] = h->chunks[q].off;
+            cl.ent[cl.count] = h->chunks[q].ent;
+        }
+        RICK_CU(h, launch_grid(h->cfg, cl, k0, nk, shift, c0 > 0, h->density, planes, h->stream));
+        count_launches(h, 1);
+        c0 += kMaxChunksPerPass;
+    } while (c0 < nch);
+    return RICK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rick_status rick_params_default(rick_params* p)
+{
+    if (!p) return RICK_ERR_ARG;
+    memset(p, 0, sizeof(*p));
+    p->n = 256;
+    p->nw = 8;
+    p->pixel_rad = 1.3635e-4;
+    p->w_min = -50.0;
+    p->w_max = 50.0;
+    p->kernel = RICK_KERNEL_GAUSS;
+    p->support = 7;
+    p->flags = RICK_GRID_CORRECT | RICK_REAL_IMAGE;
+    return RICK_OK;
+}
+
+const char* rick_status_string(rick_status s)
+{
+    switch (s) {
+        case RICK_OK: return "RICK_OK";
+        case RICK_ERR_ARG: return "RICK_ERR_ARG";
+        case RICK_ERR_OOM: return "RICK_ERR_OOM";
+        case RICK_ERR_CUDA: return "RICK_ERR_CUDA";
+        case RICK_ERR_CUFFT: return "RICK_ERR_CUFFT";
+        case RICK_ERR_TIMEOUT: return "RICK_ERR_TIMEOUT";
+        case RICK_ERR_STATE: return "RICK_ERR_STATE";
+        default: return "RICK_ERR_UNKNOWN";
+    }
+}
+
+const char* rick_last_error(rick_handle h) { return h ? h->last_error : "null handle"; }
+
+rick_status rick_workspace_size(const rick_params* p, int64_t max_vis, size_t* bytes)
+{
+    GridCfg c;
+    double kp;
+    char msg[256];
+    if (!bytes || max_vis < 0) return RICK_ERR_ARG;
+    rick_status s = check_params(p, &c, &kp, msg, sizeof(msg));
+    if (s) return s;
+    const int G = p->plane_group ? (p->plane_group < p->nw ? p->plane_group : p->nw) : p->nw;
+    const int64_t ntiles = (int64_t)c.nw * c.ntp;
+    size_t b = (size_t)G * plane_bytes(p);                           // planes
+    if (G < p->nw) b += plane_bytes(p);                              // image accumulator
+    b += (size_t)c.n * sizeof(float);                                // taper
+    b += (size_t)ntiles * sizeof(uint32_t) * 2 + sizeof(uint32_t);   // cursor + offsets
+    b += scan_block_sums_len(ntiles) * sizeof(uint32_t);
+    b += (size_t)entries_bound(c, max_vis) * sizeof(float4);         // entries
+    if (p->flags & RICK_UNIFORM_WEIGHT) b += (size_t)c.n * c.n * sizeof(uint32_t);
+    b += plane_bytes(p);                                             // cuFFT work area (estimate)
+    *bytes = b;
+    return RICK_OK;
+}
+
+rick_status rick_create(const rick_params* p, rick_handle* out)
+{
+    if (!out) return RICK_ERR_ARG;
+    *out = nullptr;
+    rick_imager* h = new (std::nothrow) rick_imager();
+    if (!h) return RICK_ERR_OOM;
+    h->last_error[0] = 0;
+    rick_status s = check_params(p, &h->cfg, &h->kernel_param, h->last_error, sizeof(h->last_error));
+    if (s) {
+        // keep the message reachable only through the return code: the handle is not returned
+        delete h;
+        return s;
+    }
+    h->p = *p;
+    h->stream = nullptr;
+    cudaGetDevice(&h->device);
+    {
+        // a private stream-ordered pool that keeps freed chunk memory mapped,
+        // so per-call entry buffers cost no remapping
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = h->device;
+        if (cudaMemPoolCreate(&h->pool, &props) != cudaSuccess) {
+            delete h;
+            return RICK_ERR_CUDA;
+        }
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(h->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+
+    const GridCfg& c = h->cfg;
+    const int64_t ntiles = (int64_t)c.nw * c.ntp;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        delete h;
+        return RICK_ERR_CUDA;
+    }
+    // plane group: as requested, else as many planes as fit in 60 % of free memory
+    const size_t pb = plane_bytes(p);
+    int G = p->plane_group ? p->plane_group : p->nw;
+    if (G > p->nw) G = p->nw;
+    if (!p->plane_group) {
+        const size_t fit = (size_t)(0.6 * (double)fr) / (pb ? 2 * pb : 1);  // planes + FFT work headroom
+        if ((size_t)G > fit) G = (int)(fit > 0 ? fit : 1);
+    }
+    h->G = G;
+    size_t need = (size_t)G * pb + (G < p->nw ? pb : 0) + (size_t)ntiles * 4 + (size_t)c.n * 4 +
+                  ((p->flags & RICK_UNIFORM_WEIGHT) ? (size_t)c.n * c.n * 4 : 0) + (64u << 20);
+    if (need > fr) {
+        delete h;
+        return RICK_ERR_OOM;
+    }
+    auto cleanup = [&](rick_status st) {
+        rick_destroy(h);
+        return st;
+    };
+    if (cudaMalloc(&h->taper, (size_t)c.n * sizeof(float)) != cudaSuccess) return cleanup(RICK_ERR_OOM);
+    if (cudaMalloc(&h->planes, (size_t)G * pb) != cudaSuccess) return cleanup(RICK_ERR_OOM);
+    if (G < p->nw && cudaMalloc(&h->acc, pb) != cudaSuccess) return cleanup(RICK_ERR_OOM);
+    if (cudaMalloc(&h->cursor, (size_t)ntiles * sizeof(uint32_t)) != cudaSuccess) return cleanup(RICK_ERR_OOM);
+    if (cudaMalloc(&h->block_sums, scan_block_sums_len(ntiles) * sizeof(uint32_t)) != cudaSuccess)
+        return cleanup(RICK_ERR_OOM);
+    if (cudaMalloc(&h->ctr, sizeof(Counters)) != cudaSuccess) return cleanup(RICK_ERR_OOM);
+    if (p->flags & RICK_UNIFORM_WEIGHT) {
+        if (cudaMalloc(&h->density, (size_t)c.n * c.n * sizeof(uint32_t)) != cudaSuccess)
+            return cleanup(RICK_ERR_OOM);
+        if (cudaMemset(h->density, 0, (size_t)c.n * c.n * sizeof(uint32_t)) != cudaSuccess)
+            return cleanup(RICK_ERR_CUDA);
+    }
+    h->bytes_held = (size_t)c.n * 4 + (size_t)G * pb + (G < p->nw ? pb : 0) + (size_t)ntiles * 4 +
+                    scan_block_sums_len(ntiles) * 4 + sizeof(Counters) +
+                    ((p->flags & RICK_UNIFORM_WEIGHT) ? (size_t)c.n * c.n * 4 : 0);
+    if (cudaMemset(h->ctr, 0, sizeof(Counters)) != cudaSuccess) return cleanup(RICK_ERR_CUDA);
+    if (launch_taper(c, h->kernel_param, h->taper, nullptr) != cudaSuccess) return cleanup(RICK_ERR_CUDA);
+    cufftHandle plan;
+    s = get_plan(h, G, &plan);
+    if (s) return cleanup(s);
+    if (p->nw % G) {
+        s = get_plan(h, p->nw % G, &plan);
+        if (s) return cleanup(s);
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) return cleanup(RICK_ERR_CUDA);
+    *out = h;
+    return RICK_OK;
+}
+
+rick_status rick_destroy(rick_handle h)
+{
+    if (!h) return RICK_OK;
+    cudaStreamSynchronize(h->stream);
+    free_chunks(h);
+    cudaStreamSynchronize(h->stream);
+    for (auto& kv : h->plans) cufftDestroy(kv.second);
+    resolve_timer(h, false);
+    for (auto& ev : h->timer.spare) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    cudaFree(h->taper);
+    cudaFree(h->planes);
+    cudaFree(h->acc);
+    cudaFree(h->cursor);
+    cudaFree(h->block_sums);
+    cudaFree(h->density);
+    cudaFree(h->ctr);
+    cudaFree(h->fft_work);
+    cudaFree(h->stage);
+    cudaFree(h->img_dev);
+    if (h->pool) cudaMemPoolDestroy(h->pool);
+    delete h;
+    return RICK_OK;
+}
+
+rick_status rick_set_stream(rick_handle h, void* cuda_stream)
+{
+    if (!h) return RICK_ERR_ARG;
+    h->stream = (cudaStream_t)cuda_stream;
+    for (auto& kv : h->plans) RICK_FFT(h, cufftSetStream(kv.second, h->stream));
+    return RICK_OK;
+}
+
+rick_status rick_reset(rick_handle h)
+{
+    if (!h) return RICK_ERR_ARG;
+    free_chunks(h);
+    RICK_CU(h, cudaMemsetAsync(h->ctr, 0, sizeof(Counters), h->stream));
+    if (h->density)
+        RICK_CU(h, cudaMemsetAsync(h->density, 0, (size_t)h->cfg.n * h->cfg.n * sizeof(uint32_t), h->stream));
+    h->density_frozen = false;
+    h->user_density = false;
+    return RICK_OK;
+}
+
+rick_status rick_add_density(rick_handle h, const float* vis, const float* u, const float* v, const float* w,
+                             const float* weights, int64_t nvis)
+{
+    if (!h) return RICK_ERR_ARG;
+    rick_status s = check_vis_args(h, vis, u, v, w, nvis);
+    if (s) return s;
+    if (!h->density) return fail(h, RICK_ERR_STATE, "uniform weighting is not enabled for this handle");
+    if (h->density_frozen) return fail(h, RICK_ERR_STATE, "density is frozen once rick_grid has run; reset first");
+    RICK_CU(h, launch_density(h->cfg, u, v, w, weights, reinterpret_cast<const float2*>(vis), nvis, h->density,
+                              h->stream));
+    h->user_density = true;
+    return RICK_OK;
+}
+
+rick_status rick_grid(rick_handle h, const float* vis, const float* u, const float* v, const float* w,
+                      const float* weights, int64_t nvis)
+{
+    if (!h) return RICK_ERR_ARG;
+    rick_status s = check_vis_args(h, vis, u, v, w, nvis);
+    if (s) return s;
+    if (nvis == 0) return RICK_OK;
+    const GridCfg& c = h->cfg;
+    const float2* vis2 = reinterpret_cast<const float2*>(vis);
+    const int64_t ntiles = (int64_t)c.nw * c.ntp;
+    const int64_t cap = entries_bound(c, nvis);
+    const size_t off_bytes = (size_t)(ntiles + 1) * sizeof(uint32_t);
+    const size_t ent_bytes = (size_t)cap * sizeof(float4);
+    if ((uint64_t)cap > 0xffffffffULL) return fail(h, RICK_ERR_ARG, "too many entries for one chunk");
+    size_t fr = 0, tot = 0;
+    RICK_CU(h, cudaMemGetInfo(&fr, &tot));
+    if (off_bytes + ent_bytes + (64u << 20) > fr)
+        return fail(h, RICK_ERR_OOM, "chunk of %lld measurements needs %zu bytes, %zu free", (long long)nvis,
+                    off_bytes + ent_bytes, fr);
+    PhaseScope scope(h, kPhasePrep);
+    if (h->density && !h->density_frozen && !h->user_density) {
+        RICK_CU(h, launch_density(c, u, v, w, weights, vis2, nvis, h->density, h->stream));
+        count_launches(h, 1);
+    }
+    h->density_frozen = true;
+    rick_imager::Chunk ch{};
+    ch.cap = cap;
+    RICK_CU(h, cudaMallocFromPoolAsync((void**)&ch.off, off_bytes, h->pool, h->stream));
+    cudaError_t e = cudaMallocFromPoolAsync((void**)&ch.ent, ent_bytes, h->pool, h->stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(ch.off, h->stream);
+        return fail(h, RICK_ERR_OOM, "cudaMallocFromPoolAsync(entries): %s", cudaGetErrorString(e));
+    }
+    // the chunk is registered only once every kernel that fills it is enqueued,
+    // so a failed call never leaves unfilled offsets for the gridder to read
+    e = cudaMemsetAsync(h->cursor, 0, (size_t)ntiles * sizeof(uint32_t), h->stream);
+    if (e == cudaSuccess) e = launch_count(c, u, v, w, weights, vis2, nvis, h->cursor, h->stream);
+    if (e == cudaSuccess) e = launch_scan(h->cursor, ntiles, ch.off, h->cursor, h->block_sums, h->stream);
+    if (e == cudaSuccess)
+        e = launch_scatter(c, u, v, w, weights, vis2, nvis, h->density, h->cursor, ch.ent, h->ctr, h->stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(ch.off, h->stream);
+        cudaFreeAsync(ch.ent, h->stream);
+        return fail(h, RICK_ERR_CUDA, "rick_grid launch: %s", cudaGetErrorString(e));
+    }
+    h->chunks.push_back(ch);
+    h->bytes_held += off_bytes + ent_bytes;
+    count_launches(h, 5);
+    return RICK_OK;
+}
+
+rick_status rick_grid_planes(rick_handle h, int32_t k0, int32_t nk, float* planes)
+{
+    if (!h) return RICK_ERR_ARG;
+    if (k0 < 0 || nk < 0 || k0 + nk > h->p.nw) return fail(h, RICK_ERR_ARG, "plane range out of bounds");
+    if (nk == 0) return RICK_OK;
+    if (!planes) return fail(h, RICK_ERR_ARG, "planes is NULL");
+    return grid_pass(h, k0, nk, false, reinterpret_cast<float2*>(planes));
+}
+
+rick_status rick_fft_and_stack(rick_handle h, float* image)
+{
+    if (!h) return RICK_ERR_ARG;
+    if (!image) return fail(h, RICK_ERR_ARG, "image is NULL");
+    const rick_params& p = h->p;
+    const double dw = (p.nw > 1) ? (p.w_max - p.w_min) / p.nw : (p.w_max - p.w_min);
+    StackArgs a{};
+    a.n = p.n;
+    split(p.pixel_rad * p.pixel_rad, &a.dl2_hi, &a.dl2_lo);
+    split(p.w_min + 0.5 * dw, &a.wb_hi, &a.wb_lo);
+    split(dw, &a.dw_hi, &a.dw_lo);
+    a.flags = p.flags;
+    for (int k0 = 0; k0 < p.nw; k0 += h->G) {
+        const int nk = (p.nw - k0 < h->G) ? p.nw - k0 : h->G;
+        rick_status s = grid_pass(h, k0, nk, true, h->planes);
+        if (s) return s;
+        cufftHandle plan;
+        s = get_plan(h, nk, &plan);
+        if (s) return s;
+        {
+            PhaseScope fs(h, kPhaseFft);
+            RICK_FFT(h, cufftExecC2C(plan, reinterpret_cast<cufftComplex*>(h->planes),
+                                     reinterpret_cast<cufftComplex*>(h->planes), CUFFT_INVERSE));
+        }
+        a.k0 = k0;
+        a.nk = nk;
+        a.first = (k0 == 0);
+        a.last = (k0 + nk >= p.nw);
+        PhaseScope ss(h, kPhaseStack);
+        RICK_CU(h, launch_stack(a, h->planes, h->acc, h->taper, h->ctr, image, h->stream));
+        count_launches(h, 1);
+    }
+    return RICK_OK;
+}
+
+rick_status rick_degrid(rick_handle h, const float* image_grad, const float* u, const float* v, const float* w,
+                        const float* weights, int64_t nvis, float* vis_grad)
+{
+    if (!h) return RICK_ERR_ARG;
+    (void)image_grad;
+    (void)u;
+    (void)v;
+    (void)w;
+    (void)weights;
+    (void)nvis;
+    (void)vis_grad;
+    return fail(h, RICK_ERR_STATE, "rick_degrid is not available in this build");
+}
+
+rick_status rick_image_host(rick_handle h, const float* vis_host, const float* u_host, const float* v_host,
+                            const float* w_host, const float* weights_host, int64_t nvis, float* image_host)
+{
+    if (!h) return RICK_ERR_ARG;
+    rick_status s = check_vis_args(h, vis_host, u_host, v_host, w_host, nvis);
+    if (s) return s;
+    if (!image_host) return fail(h, RICK_ERR_ARG, "image_host is NULL");
+    const size_t per = (weights_host ? 6 : 5) * sizeof(float);
+    const size_t need = (size_t)nvis * per;
+    if (need > h->stage_bytes) {
+        RICK_CU(h, cudaStreamSynchronize(h->stream));
+        cudaFree(h->stage);
+        h->bytes_held -= h->stage_bytes;
+        h->stage = nullptr;
+        h->stage_bytes = 0;
+        RICK_CU(h, cudaMalloc((void**)&h->stage, need));
+        h->stage_bytes = need;
+        h->bytes_held += need;
+    }
+    const size_t img = (size_t)h->p.n * h->p.n * ((h->p.flags & RICK_REAL_IMAGE) ? 1 : 2) * sizeof(float);
+    if (img > h->img_bytes) {
+        RICK_CU(h, cudaStreamSynchronize(h->stream));
+        cudaFree(h->img_dev);
+        h->bytes_held -= h->img_bytes;
+        h->img_dev = nullptr;
+        h->img_bytes = 0;
+        RICK_CU(h, cudaMalloc((void**)&h->img_dev, img));
+        h->img_bytes = img;
+        h->bytes_held += img;
+    }
+    float* d_vis = h->stage;
+    float* d_u = d_vis + 2 * nvis;
+    float* d_v = d_u + nvis;
+    float* d_w = d_v + nvis;
+    float* d_wt = weights_host ? d_w + nvis : nullptr;
+    const size_t fb = (size_t)nvis * sizeof(float);
+    RICK_CU(h, cudaMemcpyAsync(d_vis, vis_host, 2 * fb, cudaMemcpyHostToDevice, h->stream));
+    RICK_CU(h, cudaMemcpyAsync(d_u, u_host, fb, cudaMemcpyHostToDevice, h->stream));
+    RICK_CU(h, cudaMemcpyAsync(d_v, v_host, fb, cudaMemcpyHostToDevice, h->stream));
+    RICK_CU(h, cudaMemcpyAsync(d_w, w_host, fb, cudaMemcpyHostToDevice, h->stream));
+    if (d_wt) RICK_CU(h, cudaMemcpyAsync(d_wt, weights_host, fb, cudaMemcpyHostToDevice, h->stream));
+    s = rick_reset(h);
+    if (s) return s;
+    s = rick_grid(h, d_vis, d_u, d_v, d_w, d_wt, nvis);
+    if (s) return s;
+    s = rick_fft_and_stack(h, h->img_dev);
+    if (s) return s;
+    RICK_CU(h, cudaMemcpyAsync(image_host, h->img_dev, img, cudaMemcpyDeviceToHost, h->stream));
+    RICK_CU(h, cudaStreamSynchronize(h->stream));
+    return RICK_OK;
+}
+
+rick_status rick_set_timing(rick_handle h, int32_t enable)
+{
+    if (!h) return RICK_ERR_ARG;
+    RICK_CU(h, cudaStreamSynchronize(h->stream));
+    resolve_timer(h, false);
+    for (int ph = 0; ph < kNumPhases; ++ph) {
+        h->timer.ms[ph] = 0.0;
+        h->timer.calls[ph] = 0;
+    }
+    h->timer.launches = 0;
+    h->timer.on = enable != 0;
+    return RICK_OK;
+}
+
+rick_status rick_get_timing(rick_handle h, rick_timing* out)
+{
+    if (!h || !out) return RICK_ERR_ARG;
+    RICK_CU(h, cudaStreamSynchronize(h->stream));
+    resolve_timer(h, true);
+    out->prep_ms = h->timer.ms[kPhasePrep];
+    out->grid_ms = h->timer.ms[kPhaseGrid];
+    out->fft_ms = h->timer.ms[kPhaseFft];
+    out->stack_ms = h->timer.ms[kPhaseStack];
+    out->degrid_ms = h->timer.ms[kPhaseDegrid];
+    out->prep_calls = h->timer.calls[kPhasePrep];
+    out->grid_calls = h->timer.calls[kPhaseGrid];
+    out->fft_calls = h->timer.calls[kPhaseFft];
+    out->stack_calls = h->timer.calls[kPhaseStack];
+    out->degrid_calls = h->timer.calls[kPhaseDegrid];
+    out->kernel_launches = h->timer.launches;
+    return RICK_OK;
+}
+
+rick_status rick_get_stats(rick_handle h, rick_stats* out)
+{
+    if (!h || !out) return RICK_ERR_ARG;
+    Counters c;
+    RICK_CU(h, cudaStreamSynchronize(h->stream));
+    RICK_CU(h, cudaMemcpy(&c, h->ctr, sizeof(c), cudaMemcpyDeviceToHost));
+    out->n_gridded = (int64_t)c.gridded;
+    out->n_dropped = (int64_t)c.dropped;
+    out->n_entries = (int64_t)c.entries;
+    out->sum_weights = c.sum_w;
+    out->plane_group = h->G;
+    out->tile = h->cfg.T;
+    out->workspace_bytes = (int64_t)h->bytes_held;
+    return RICK_OK;
+}
+
+}  // extern "C"

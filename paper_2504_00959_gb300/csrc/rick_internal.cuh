@@ -1,0 +1,190 @@
+// rick_internal.cuh -- device-side configuration, placement and kernel
+// launchers shared by the translation units of librick (GPU side only).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <map>
+#include <vector>
+
+#include "../../include/rick.h"
+
+namespace rick {
+
+constexpr int kMaxSupport = 16;
+constexpr int kMaxChunksPerPass = 16;
+constexpr int kScanBlock = 1024;          // threads of the scan kernels
+constexpr int kScanItems = 4;             // items per scan thread
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+// Everything a kernel needs to place a measurement, by value.
+struct GridCfg {
+    int n, nw, S, T, log2T, ntu;     // ntu: tiles per side = ceil(n / T)
+    int64_t ntp;                     // tiles per plane = ntu * ntu
+    float uvscale;                   // cells per wavelength, binary32
+    float half_n, half_s;            // n/2, S/2
+    float wmin, invdw;               // binary32 plane decision constants
+    float lim;                       // n - S - 1: largest first cell - 1
+    int kernel;                      // RICK_KERNEL_*
+    float kp;                        // Gaussian: 1/(2 sigma^2); KB: beta
+    float two_over_s;                // 2 / S
+    int uniform;                     // uniform weighting on
+};
+
+// Placement of one measurement: plane, first footprint cell, continuous
+// cell coordinates.  Every float->int decision is binary32 with the
+// operation order written out (explicit _rn intrinsics, no contraction).
+struct Place {
+    int k, fu, fv;
+    float pu, pv;
+};
+
+__device__ __forceinline__ bool place(const GridCfg& c, float u, float v, float w, Place& p)
+{
+    if (!(isfinite(u) && isfinite(v) && isfinite(w))) return false;
+    float pu = __fmaf_rn(u, c.uvscale, c.half_n);
+    float pv = __fmaf_rn(v, c.uvscale, c.half_n);
+    float au = floorf(__fsub_rn(pu, c.half_s));
+    float av = floorf(__fsub_rn(pv, c.half_s));
+    if (!(au >= -1.0f && au <= c.lim && av >= -1.0f && av <= c.lim)) return false;
+    p.fu = (int)au + 1;
+    p.fv = (int)av + 1;
+    if (c.nw == 1) {
+        p.k = 0;
+    } else {
+        float fk = floorf(__fmul_rn(__fsub_rn(w, c.wmin), c.invdw));
+        p.k = (fk < 0.0f) ? 0 : ((fk > (float)(c.nw - 1)) ? c.nw - 1 : (int)fk);
+    }
+    p.pu = pu;
+    p.pv = pv;
+    return true;
+}
+
+// First footprint cell from a stored continuous coordinate (same rounding
+// as place()).
+__device__ __forceinline__ int first_cell(const GridCfg& c, float p)
+{
+    return (int)floorf(__fsub_rn(p, c.half_s)) + 1;
+}
+
+// Nearest cell for the density grid.
+__device__ __forceinline__ int nearest_cell(const GridCfg& c, float p)
+{
+    int j = (int)floorf(__fadd_rn(p, 0.5f));
+    return j > c.n - 1 ? c.n - 1 : j;
+}
+
+// Un-normalised kernel value at offset x (cells) from the measurement.
+__device__ __forceinline__ float kernel_value(const GridCfg& c, float x)
+{
+    if (c.kernel == RICK_KERNEL_GAUSS) return __expf(-x * x * c.kp);
+    float t = x * c.two_over_s;
+    float a = fmaxf(0.0f, 1.0f - t * t);
+    return cyl_bessel_i0f(c.kp * sqrtf(a));
+}
+
+// Whether a measurement with finite placement also has a finite weight and value.
+__device__ __forceinline__ bool finite_value(float wt, float2 vis)
+{
+    return isfinite(wt) && isfinite(vis.x) && isfinite(vis.y);
+}
+
+// One gridding pass: up to kMaxChunksPerPass sorted chunks.
+struct ChunkList {
+    const uint32_t* off[kMaxChunksPerPass];  // [ntiles + 1] start offsets
+    const float4* ent[kMaxChunksPerPass];    // (pu, pv, re, im) entries
+    int count;
+};
+
+// Device-resident counters of a handle.
+struct Counters {
+    unsigned long long gridded, dropped, entries, pad;
+    double sum_w;
+};
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_density(const GridCfg& c, const float* u, const float* v, const float* w,
+                           const float* wt, const float2* vis, int64_t m, uint32_t* density,
+                           cudaStream_t s);
+cudaError_t launch_count(const GridCfg& c, const float* u, const float* v, const float* w,
+                         const float* wt, const float2* vis, int64_t m, uint32_t* counts,
+                         cudaStream_t s);
+cudaError_t launch_scan(const uint32_t* counts, int64_t len, uint32_t* offsets, uint32_t* cursor,
+                        uint32_t* block_sums, cudaStream_t s);
+cudaError_t launch_scatter(const GridCfg& c, const float* u, const float* v, const float* w,
+                           const float* wt, const float2* vis, int64_t m, const uint32_t* density,
+                           uint32_t* cursor, float4* entries, Counters* ctr, cudaStream_t s);
+cudaError_t launch_grid(const GridCfg& c, const ChunkList& chunks, int k0, int nk, bool shift_sign,
+                        bool accumulate, const uint32_t* density, float2* planes, cudaStream_t s);
+cudaError_t launch_taper(const GridCfg& c, double kernel_param, float* taper, cudaStream_t s);
+
+struct StackArgs {
+    int n, k0, nk;
+    float dl2_hi, dl2_lo;            // pixel_rad^2 as a float pair
+    float wb_hi, wb_lo;              // w_min + dw/2 as a float pair
+    float dw_hi, dw_lo;              // dw as a float pair
+    int first, last;                 // first / last plane group
+    unsigned flags;
+};
+cudaError_t launch_stack(const StackArgs& a, const float2* planes, float2* acc, const float* taper,
+                         const Counters* ctr, void* image, cudaStream_t s);
+
+size_t scan_block_sums_len(int64_t len);
+
+}  // namespace rick
+
+namespace rick {
+enum Phase { kPhasePrep = 0, kPhaseGrid, kPhaseFft, kPhaseStack, kPhaseDegrid, kNumPhases };
+
+// CUDA-event timer per phase: events are recorded on the stream and only
+// resolved (elapsed time summed) when the caller asks for the totals.
+struct PhaseTimer {
+    bool on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[kNumPhases];
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spare;
+    double ms[kNumPhases] = {0, 0, 0, 0, 0};
+    int64_t calls[kNumPhases] = {0, 0, 0, 0, 0};
+    int64_t launches = 0;
+    cudaEvent_t open_start[kNumPhases] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+}  // namespace rick
+
+// The handle.
+struct rick_imager {
+    rick_params p;
+    rick::GridCfg cfg;
+    double kernel_param;             // resolved sigma / beta
+    int device;
+    cudaStream_t stream;
+    int G;                           // planes per group
+    // device buffers
+    float* taper;                    // [n]
+    float2* planes;                  // [G][n][n]
+    float2* acc;                     // [n][n] image accumulator (several groups)
+    uint32_t* cursor;                // [ntiles] counts / scatter cursors
+    uint32_t* block_sums;            // scan block totals
+    uint32_t* density;               // [n][n] uniform weighting counts
+    rick::Counters* ctr;             // device counters
+    void* fft_work;
+    size_t fft_work_bytes;
+    std::map<int, cufftHandle> plans;// batch -> plan
+    struct Chunk {
+        uint32_t* off;
+        float4* ent;
+        int64_t cap;
+    };
+    std::vector<Chunk> chunks;
+    cudaMemPool_t pool;              // stream-ordered pool for chunk buffers
+    bool density_frozen;
+    bool user_density;               // density filled by rick_add_density
+    // host staging for rick_image_host
+    float* stage;
+    size_t stage_bytes;
+    float* img_dev;
+    size_t img_bytes;
+    size_t bytes_held;
+    rick::PhaseTimer timer;
+    char last_error[512];
+};

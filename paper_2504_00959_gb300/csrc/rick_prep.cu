@@ -1,0 +1,301 @@
+// rick_prep.cu -- sub-step 1 of gridding (Sec. 2.1: "an array is created for
+// each sector, concatenating the data with u-v coordinates inside the
+// corresponding sector"), done as a device counting sort by (w-plane, uv tile):
+//   k_density  nearest-cell counts for uniform weighting
+//   k_count    entries per tile (a footprint straddling tiles is listed in
+//              every tile it touches)
+//   k_scan_*   exclusive prefix sum of the counts -> tile start offsets
+//   k_scatter  one 16-byte entry (pu, pv, wt*Re V, wt*Im V) per (measurement,
+//              tile), written at its tile's cursor; weight sum and counters.
+// All are grid-stride kernels sized to the SM count; reads of the inputs are
+// coalesced, writes of entries are scattered 16-byte stores.
+#include "rick_internal.cuh"
+
+namespace rick {
+namespace {
+
+int sm_count()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 1;
+    }
+    return cached[dev];
+}
+
+constexpr int kPrepThreads = 256;
+
+int prep_blocks(int64_t m)
+{
+    int64_t want = (m + kPrepThreads - 1) / kPrepThreads;
+    int64_t cap = (int64_t)sm_count() * 8;
+    if (want > cap) want = cap;
+    return (int)(want < 1 ? 1 : want);
+}
+
+struct Inputs {
+    const float* u;
+    const float* v;
+    const float* w;
+    const float* wt;
+    const float2* vis;
+};
+
+__device__ __forceinline__ bool load_and_place(const GridCfg& c, const Inputs& in, int64_t i, Place& p,
+                                               float& wi, float2& V)
+{
+    wi = in.wt ? __ldg(in.wt + i) : 1.0f;
+    V = __ldg(in.vis + i);
+    return place(c, __ldg(in.u + i), __ldg(in.v + i), __ldg(in.w + i), p) && finite_value(wi, V);
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_density(GridCfg c, Inputs in, int64_t m,
+                                                          uint32_t* __restrict__ density)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        Place p;
+        float wi;
+        float2 V;
+        if (!load_and_place(c, in, i, p, wi, V)) continue;
+        atomicAdd(density + (int64_t)nearest_cell(c, p.pv) * c.n + nearest_cell(c, p.pu), 1u);
+    }
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_count(GridCfg c, Inputs in, int64_t m,
+                                                        uint32_t* __restrict__ counts)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        Place p;
+        float wi;
+        float2 V;
+        if (!load_and_place(c, in, i, p, wi, V)) continue;
+        const int tu0 = p.fu >> c.log2T, tu1 = (p.fu + c.S - 1) >> c.log2T;
+        const int tv0 = p.fv >> c.log2T, tv1 = (p.fv + c.S - 1) >> c.log2T;
+        uint32_t* base = counts + (int64_t)p.k * c.ntp;
+        atomicAdd(base + tv0 * c.ntu + tu0, 1u);
+        if (tu1 != tu0) atomicAdd(base + tv0 * c.ntu + tu1, 1u);
+        if (tv1 != tv0) {
+            atomicAdd(base + tv1 * c.ntu + tu0, 1u);
+            if (tu1 != tu0) atomicAdd(base + tv1 * c.ntu + tu1, 1u);
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x)
+{
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_scatter(GridCfg c, Inputs in, int64_t m,
+                                                          const uint32_t* __restrict__ density,
+                                                          uint32_t* __restrict__ cursor,
+                                                          float4* __restrict__ entries, Counters* ctr)
+{
+    float sw = 0.0f;
+    unsigned gridded = 0, dropped = 0, nent = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        Place p;
+        float wi;
+        float2 V;
+        if (!load_and_place(c, in, i, p, wi, V)) {
+            ++dropped;
+            continue;
+        }
+        if (c.uniform) {
+            uint32_t cnt = __ldg(density + (int64_t)nearest_cell(c, p.pv) * c.n + nearest_cell(c, p.pu));
+            wi = wi / (float)cnt;
+        }
+        const float4 rec = make_float4(p.pu, p.pv, wi * V.x, wi * V.y);
+        sw += wi;
+        ++gridded;
+        const int tu0 = p.fu >> c.log2T, tu1 = (p.fu + c.S - 1) >> c.log2T;
+        const int tv0 = p.fv >> c.log2T, tv1 = (p.fv + c.S - 1) >> c.log2T;
+        uint32_t* base = cursor + (int64_t)p.k * c.ntp;
+        entries[atomicAdd(base + tv0 * c.ntu + tu0, 1u)] = rec;
+        ++nent;
+        if (tu1 != tu0) {
+            entries[atomicAdd(base + tv0 * c.ntu + tu1, 1u)] = rec;
+            ++nent;
+        }
+        if (tv1 != tv0) {
+            entries[atomicAdd(base + tv1 * c.ntu + tu0, 1u)] = rec;
+            ++nent;
+            if (tu1 != tu0) {
+                entries[atomicAdd(base + tv1 * c.ntu + tu1, 1u)] = rec;
+                ++nent;
+            }
+        }
+    }
+    // block reduction of the counters, one set of atomics per block
+    __shared__ float s_sw[kPrepThreads / 32];
+    __shared__ unsigned s_g[kPrepThreads / 32], s_d[kPrepThreads / 32], s_e[kPrepThreads / 32];
+    sw = warp_sum(sw);
+    gridded = warp_sum(gridded);
+    dropped = warp_sum(dropped);
+    nent = warp_sum(nent);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_sw[wid] = sw;
+        s_g[wid] = gridded;
+        s_d[wid] = dropped;
+        s_e[wid] = nent;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float a = 0.0f;
+        unsigned long long g = 0, d = 0, e = 0;
+        for (int j = 0; j < kPrepThreads / 32; ++j) {
+            a += s_sw[j];
+            g += s_g[j];
+            d += s_d[j];
+            e += s_e[j];
+        }
+        atomicAdd(&ctr->sum_w, (double)a);
+        if (g) atomicAdd(&ctr->gridded, g);
+        if (d) atomicAdd(&ctr->dropped, d);
+        if (e) atomicAdd(&ctr->entries, e);
+    }
+}
+
+// ------------------------------------------------------------------ scan
+
+// Exclusive scan of one value per thread across a 1024-thread block.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total)
+{
+    __shared__ uint32_t ws[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t t = ws[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        ws[lane] = t;
+    }
+    __syncthreads();
+    const uint32_t prefix = wid ? ws[wid - 1] : 0u;
+    *total = ws[31];
+    __syncthreads();
+    return prefix + x - v;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_local(const uint32_t* __restrict__ in, int64_t len,
+                                                           uint32_t* __restrict__ out,
+                                                           uint32_t* __restrict__ block_sums)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t x[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        x[j] = (base + j < len) ? in[base + j] : 0u;
+        s += x[j];
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(s, &total);
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (base + j < len) out[base + j] = run;
+        run += x[j];
+    }
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// Exclusive scan of the block totals in place (one block, any length), and
+// the grand total into out[len].
+__global__ void __launch_bounds__(kScanBlock) k_scan_sums(uint32_t* __restrict__ sums, int64_t nb,
+                                                          uint32_t* __restrict__ out, int64_t len)
+{
+    uint32_t carry = 0;
+    for (int64_t s0 = 0; s0 < nb; s0 += kScanBlock) {
+        const int64_t i = s0 + threadIdx.x;
+        const uint32_t v = (i < nb) ? sums[i] : 0u;
+        uint32_t total;
+        const uint32_t ex = block_exclusive_scan(v, &total);
+        if (i < nb) sums[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) out[len] = carry;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_add(const uint32_t* __restrict__ sums, int64_t len,
+                                                         uint32_t* __restrict__ out,
+                                                         uint32_t* __restrict__ cursor)
+{
+    const uint32_t add = sums[blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) {
+        if (base + j < len) {
+            const uint32_t o = out[base + j] + add;
+            out[base + j] = o;
+            cursor[base + j] = o;
+        }
+    }
+}
+
+}  // namespace
+
+size_t scan_block_sums_len(int64_t len)
+{
+    return (size_t)((len + kScanTile - 1) / kScanTile) + 1;
+}
+
+cudaError_t launch_density(const GridCfg& c, const float* u, const float* v, const float* w,
+                           const float* wt, const float2* vis, int64_t m, uint32_t* density,
+                           cudaStream_t s)
+{
+    if (m <= 0) return cudaSuccess;
+    k_density<<<prep_blocks(m), kPrepThreads, 0, s>>>(c, Inputs{u, v, w, wt, vis}, m, density);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count(const GridCfg& c, const float* u, const float* v, const float* w,
+                         const float* wt, const float2* vis, int64_t m, uint32_t* counts,
+                         cudaStream_t s)
+{
+    if (m <= 0) return cudaSuccess;
+    k_count<<<prep_blocks(m), kPrepThreads, 0, s>>>(c, Inputs{u, v, w, wt, vis}, m, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const uint32_t* counts, int64_t len, uint32_t* offsets, uint32_t* cursor,
+                        uint32_t* block_sums, cudaStream_t s)
+{
+    const int64_t nb = (len + kScanTile - 1) / kScanTile;
+    if (nb > 0x7fffffff) return cudaErrorInvalidValue;
+    if (nb == 0) return cudaMemsetAsync(offsets, 0, sizeof(uint32_t), s);
+    k_scan_local<<<(unsigned)nb, kScanBlock, 0, s>>>(counts, len, offsets, block_sums);
+    k_scan_sums<<<1, kScanBlock, 0, s>>>(block_sums, nb, offsets, len);
+    k_scan_add<<<(unsigned)nb, kScanBlock, 0, s>>>(block_sums, len, offsets, cursor);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const GridCfg& c, const float* u, const float* v, const float* w,
+                           const float* wt, const float2* vis, int64_t m, const uint32_t* density,
+                           uint32_t* cursor, float4* entries, Counters* ctr, cudaStream_t s)
+{
+    if (m <= 0) return cudaSuccess;
+    k_scatter<<<prep_blocks(m), kPrepThreads, 0, s>>>(c, Inputs{u, v, w, wt, vis}, m, density, cursor,
+                                                      entries, ctr);
+    return cudaGetLastError();
+}
+
+}  // namespace rick

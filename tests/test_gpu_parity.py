@@ -1,0 +1,340 @@
+"""GPU (sm_103a, librick) against the FP64 oracle on identical seeded inputs.
+
+Tolerance (from the target of the method's port): max |D_gpu - D_oracle| <=
+1e-4 * max |D_oracle| for FP32 images, on the image before and after grid
+correction.  Gridded planes are compared at 1e-5 of their largest cell
+(FP32 accumulation of at most a few thousand terms per cell).  Integer work
+(drop counts, entry counts) is compared exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+KB, GAUSS = synth.KERNEL_KB, synth.KERNEL_GAUSS
+CORRECT, REAL, APPLY_N, UNIFORM = synth.FLAG_CORRECT, synth.FLAG_REAL, synth.FLAG_APPLY_N, synth.FLAG_UNIFORM
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def rick():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_00959_gb300 import build
+    build.build()
+    import paper_2504_00959_gb300 as r
+    r.load()
+    return r
+
+
+def _to(prob, dev="cuda"):
+    return {k: (v.to(dev) if isinstance(v, torch.Tensor) else v) for k, v in prob.items()}
+
+
+def _gpu_image(rick, prob, flags, chunks=1, **extra):
+    prob = _to(prob)
+    params = dict(prob["params"], flags=flags, **extra)
+    im = rick.Imager(params)
+    m = prob["u"].numel()
+    edges = np.linspace(0, m, chunks + 1).astype(int)
+    for a, b in zip(edges[:-1], edges[1:]):
+        im.grid(prob["vis"][a:b].contiguous(), prob["u"][a:b].contiguous(), prob["v"][a:b].contiguous(),
+                prob["w"][a:b].contiguous(), prob["wt"][a:b].contiguous())
+    img = im.image()
+    torch.cuda.synchronize()
+    st = im.stats()
+    im.close()
+    return img.cpu().numpy(), st
+
+
+def _oracle_image(oracle_mod, prob, flags):
+    p = synth.to_numpy(prob)
+    return oracle_mod.dirty_image(p["params"], p["u"], p["v"], p["w"], p["wt"], p["vis"], flags=flags)
+
+
+def _rel_err(got, ref, mask=None):
+    d = np.abs(got - ref)
+    if mask is not None:
+        d = d[mask]
+    return float(d.max()) / float(np.abs(ref).max())
+
+
+def _compare(rick, oracle_mod, prob, flags, tol=TOL, chunks=1, **extra):
+    got, st = _gpu_image(rick, prob, flags, chunks=chunks, **extra)
+    ref, sw, dropped = _oracle_image(oracle_mod, prob, flags & ~REAL)
+    if flags & REAL:
+        ref = ref.real
+    err = _rel_err(got, ref)
+    assert err <= tol, (err, tol)
+    assert st["n_dropped"] == dropped
+    assert abs(st["sum_weights"] - sw) <= 1e-5 * max(1.0, abs(sw))
+    return got, ref, st
+
+
+# ----------------------------------------------------------------- config 1
+
+@pytest.mark.parametrize("flags", [REAL, CORRECT | REAL, CORRECT, CORRECT | REAL | APPLY_N])
+def test_config1_full_image(rick, oracle_mod, flags):
+    """256^2, 8 w-planes, 1e5 visibilities, Gaussian support 7, 2 deg."""
+    prob = synth.config1()
+    _compare(rick, oracle_mod, prob, flags)
+
+
+def test_config1_planes_match_oracle_grid(rick, oracle_mod):
+    prob = synth.config1()
+    p = synth.to_numpy(prob)
+    ref, sw, _ = oracle_mod.grid(p["params"], p["u"], p["v"], p["w"], p["wt"], p["vis"])
+    im = rick.Imager(dict(prob["params"]))
+    g = _to(prob)
+    im.grid(g["vis"], g["u"], g["v"], g["w"], g["wt"])
+    planes = im.grid_planes().cpu().numpy()
+    im.close()
+    scale = np.abs(ref).max()
+    assert np.max(np.abs(planes - ref)) <= 1e-5 * scale
+    # Eq. 3 with normalised taps keeps the weighted visibility sum
+    tot = np.sum(p["wt"].astype(np.float64) * p["vis"].astype(np.complex128))
+    assert abs(planes.astype(np.complex128).sum() - tot) <= 1e-5 * np.sum(np.abs(p["vis"]))
+
+
+def test_config1_entries_and_counters_exact(rick, oracle_mod):
+    """Integer work: entry count = sum over gridded measurements of the tiles
+    their footprint touches (computed from the oracle's placement)."""
+    prob = synth.config1()
+    p = synth.to_numpy(prob)
+    k, fu, fv = oracle_mod.place(p["params"], p["u"], p["v"], p["w"])
+    ok = k >= 0
+    S = p["params"]["support"]
+    T = 32
+    nt = ((fu[ok] + S - 1) // T - fu[ok] // T + 1) * ((fv[ok] + S - 1) // T - fv[ok] // T + 1)
+    _, st = _gpu_image(rick, prob, CORRECT | REAL, tile=T)
+    assert st["n_gridded"] == int(ok.sum())
+    assert st["n_entries"] == int(nt.sum())
+    assert st["n_dropped"] == int((~ok).sum())
+
+
+# ------------------------------------------------------- shapes and tiles
+
+@pytest.mark.parametrize("n,tile,kernel,support", [(200, 32, KB, 7), (96, 64, KB, 8), (64, 16, GAUSS, 5),
+                                                   (72, 16, KB, 16)])
+def test_ragged_and_tiles(rick, oracle_mod, n, tile, kernel, support):
+    """Grid sides that are not multiples of the tile (a ragged last tile) and
+    every tile size, KB and Gaussian, supports up to 16."""
+    prob = synth.disk_problem(n, 4, 20000, kernel, support, 3.0, 60.0, 101 + n, weights="random")
+    _compare(rick, oracle_mod, prob, CORRECT | REAL, tile=tile)
+
+
+def test_plane_groups_equal_all_planes(rick, oracle_mod):
+    prob = synth.disk_problem(128, 8, 30000, KB, 7, 4.0, 80.0, 103)
+    a, _, _ = _compare(rick, oracle_mod, prob, CORRECT | REAL, plane_group=3)
+    b, _ = _gpu_image(rick, prob, CORRECT | REAL)
+    assert np.max(np.abs(a - b)) <= 1e-5 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("chunks", [3, 20])
+def test_chunks_accumulate(rick, oracle_mod, chunks):
+    """Several grid() calls equal one (20 chunks also exercises the
+    read-modify-write gridding pass beyond 16 chunks)."""
+    prob = synth.disk_problem(128, 4, 40000, GAUSS, 7, 2.0, 50.0, 107)
+    _compare(rick, oracle_mod, prob, CORRECT | REAL, chunks=chunks)
+
+
+def test_uniform_weighting(rick, oracle_mod):
+    prob = synth.disk_problem(128, 4, 40000, KB, 7, 2.0, 50.0, 109, fill=0.3)
+    _compare(rick, oracle_mod, prob, CORRECT | REAL | UNIFORM)
+
+
+def test_uniform_weighting_with_chunks_and_add_density(rick, oracle_mod):
+    prob = synth.disk_problem(128, 4, 40000, KB, 7, 2.0, 50.0, 113, fill=0.3)
+    g = _to(prob)
+    im = rick.Imager(dict(prob["params"], flags=CORRECT | REAL | UNIFORM))
+    halves = [(0, 15000), (15000, 40000)]
+    for a, b in halves:
+        im.add_density(g["vis"][a:b], g["u"][a:b], g["v"][a:b], g["w"][a:b], g["wt"][a:b])
+    for a, b in halves:
+        im.grid(g["vis"][a:b], g["u"][a:b], g["v"][a:b], g["w"][a:b], g["wt"][a:b])
+    got = im.image().cpu().numpy()
+    im.close()
+    ref, _, _ = _oracle_image(oracle_mod, prob, CORRECT | UNIFORM)
+    assert _rel_err(got, ref.real) <= TOL
+
+
+# ------------------------------------------------------------- edge cases
+
+def test_empty_input_gives_zero_image(rick):
+    prob = synth.disk_problem(64, 4, 0, KB, 7, 2.0, 50.0, 1)
+    got, st = _gpu_image(rick, prob, CORRECT | REAL)
+    assert np.all(got == 0) and st["n_gridded"] == 0
+
+
+def test_all_dropped(rick, oracle_mod):
+    prob = synth.disk_problem(64, 4, 1000, KB, 7, 2.0, 50.0, 3)
+    prob["u"] = prob["u"] * 10.0  # far outside the grid
+    got, st = _gpu_image(rick, prob, CORRECT | REAL)
+    assert st["n_dropped"] == 1000 and np.all(got == 0)
+
+
+def test_non_finite_inputs_are_dropped_and_counted(rick, oracle_mod):
+    prob = synth.disk_problem(64, 4, 2000, KB, 7, 2.0, 50.0, 5, fill=0.4)
+    prob["u"][3] = float("nan")
+    prob["v"][10] = float("inf")
+    prob["w"][20] = float("nan")
+    prob["wt"][30] = float("nan")
+    prob["vis"][40] = complex(float("nan"), 0.0)
+    _, st = _gpu_image(rick, prob, CORRECT | REAL)
+    assert st["n_dropped"] == 5
+    keep = torch.ones(2000, dtype=torch.bool)
+    keep[[3, 10, 20, 30, 40]] = False
+    clean = {k: (v[keep] if isinstance(v, torch.Tensor) else v) for k, v in prob.items()}
+    a, _ = _gpu_image(rick, prob, CORRECT | REAL)
+    b, _ = _gpu_image(rick, clean, CORRECT | REAL)
+    assert np.max(np.abs(a - b)) <= 1e-6 * np.abs(b).max()
+
+
+def test_single_visibility(rick, oracle_mod):
+    n = 64
+    pixel_rad = math.radians(10.0) / n
+    du = 1 / (n * pixel_rad)
+    params = synth.make_params(n, 5, pixel_rad, -40.0, 40.0, KB, 7, 0.0, CORRECT | REAL)
+    prob = dict(params=params, u=torch.tensor([5.3 * du]), v=torch.tensor([-11.7 * du]), w=torch.tensor([17.0]),
+                wt=torch.tensor([2.0]), vis=torch.tensor([0.3 + 0.9j], dtype=torch.complex64))
+    _compare(rick, oracle_mod, prob, CORRECT | REAL)
+    _compare(rick, oracle_mod, prob, 0)
+
+
+def test_grid_edges_and_plane_boundaries(rick, oracle_mod):
+    """Footprints touching the first and last cells, measurements exactly on
+    plane boundaries and at w_min / w_max, at half-cell offsets."""
+    n, S = 64, 7
+    pixel_rad = math.radians(5.0) / n
+    du = 1 / (n * pixel_rad)
+    cells_lo = -n / 2 + S / 2 - 0.49        # first cell 0
+    cells_hi = n / 2 - S / 2 - 1 + 0.49     # last cell n-1
+    pos = np.array([cells_lo, cells_hi, 0.5, -0.5, 3.0, -7.5, 10.25]) * du
+    uu, vv = np.meshgrid(pos, pos)
+    m = uu.size
+    w_edges = np.array([-40.0, 40.0, 0.0, -20.0, 20.0, -10.0, 10.0])
+    ww = np.resize(w_edges, m)
+    params = synth.make_params(n, 8, pixel_rad, -40.0, 40.0, KB, S, 0.0, CORRECT | REAL)
+    rng = np.random.default_rng(9)
+    prob = dict(params=params, u=torch.tensor(uu.ravel(), dtype=torch.float32),
+                v=torch.tensor(vv.ravel(), dtype=torch.float32), w=torch.tensor(ww, dtype=torch.float32),
+                wt=torch.ones(m), vis=torch.tensor(rng.standard_normal(m) + 1j * rng.standard_normal(m),
+                                                   dtype=torch.complex64))
+    _, _, st = _compare(rick, oracle_mod, prob, CORRECT | REAL)
+    assert st["n_dropped"] == 0
+
+
+def test_hot_tile(rick, oracle_mod):
+    """2e5 measurements inside one cell next to 2e4 spread ones (heavy skew
+    of the per-tile lists)."""
+    n = 128
+    prob = synth.disk_problem(n, 4, 20000, KB, 7, 3.0, 50.0, 11)
+    du = 1 / (n * prob["params"]["pixel_rad"])
+    g = torch.Generator().manual_seed(5)
+    hot = 200000
+    u = torch.cat([prob["u"], (3.2 + 0.3 * torch.rand(hot, generator=g)) * du])
+    v = torch.cat([prob["v"], (-1.7 + 0.3 * torch.rand(hot, generator=g)) * du])
+    w = torch.cat([prob["w"], torch.full((hot,), 1.0)])
+    wt = torch.ones(u.numel())
+    vis = torch.cat([prob["vis"], torch.complex(torch.randn(hot, generator=g), torch.randn(hot, generator=g))])
+    _compare(rick, oracle_mod, dict(params=prob["params"], u=u, v=v, w=w, wt=wt, vis=vis), CORRECT | REAL)
+
+
+def test_repeatable_and_stream_ordered(rick):
+    """Two images of the same problem, the second on a side stream, agree to
+    FP32 reordering (gridding uses shared-memory atomics)."""
+    prob = _to(synth.config1())
+    im = rick.Imager(dict(prob["params"]))
+    im.grid(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"])
+    a = im.image().clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        b = im.image()
+    torch.cuda.synchronize()
+    im.close()
+    assert torch.max(torch.abs(a - b)).item() <= 1e-6 * torch.max(torch.abs(a)).item()
+
+
+def test_image_host_matches_device_path(rick):
+    prob = synth.config1()
+    im = rick.Imager(dict(prob["params"]))
+    a = im.image_host(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"])
+    g = _to(prob)
+    im.reset()
+    im.grid(g["vis"], g["u"], g["v"], g["w"], g["wt"])
+    b = im.image().cpu()
+    im.close()
+    assert torch.max(torch.abs(a - b)).item() <= 1e-6 * torch.max(torch.abs(b)).item()
+
+
+def test_errors_are_returned_not_raised_on_device(rick):
+    prob = _to(synth.config1())
+    im = rick.Imager(dict(prob["params"]))
+    with pytest.raises(rick.RickError):
+        im.grid_planes(5, 10)  # beyond nw
+    with pytest.raises(ValueError):
+        im.grid(prob["vis"].cpu(), prob["u"], prob["v"], prob["w"])
+    huge = dict(prob["params"], n=32768, nw=4096, plane_group=4096)
+    with pytest.raises(rick.RickError) as e:
+        rick.Imager(huge)
+    assert e.value.status == 2  # RICK_ERR_OOM before any launch
+    im.close()
+
+
+# ---------------------------------------------------- config 2, full size
+
+@pytest.fixture(scope="module")
+def config2_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return synth.config2(device="cuda")
+
+
+def test_config2_full_size_sampled(rick, oracle_mod, config2_gpu):
+    """4096^2, 32 planes, 1e7 Earth-rotation visibilities, KB support 7: in the
+    bench's launch configuration (automatic tile and plane group), sampled
+    pixels against the oracle's per-pixel evaluation, and the gridded-sum
+    invariant over all planes."""
+    prob = config2_gpu
+    params = dict(prob["params"], flags=CORRECT | REAL)
+    im = rick.Imager(params)
+    im.grid(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"])
+    img = im.image()
+    st = im.stats()
+    n = params["n"]
+    peak_gpu = img.abs().max().item()
+    flat = int(torch.argmax(img.abs()).item())
+    rng = np.random.default_rng(17)
+    pix = [(flat % n, flat // n), (n // 2, n // 2), (0, 0), (n - 1, n - 1), (n // 2 + 7, n // 3)]
+    pix += [tuple(rng.integers(n // 4, 3 * n // 4, 2)) for _ in range(5)]
+    p = synth.to_numpy(prob)
+    ref = oracle_mod.image_at(params, p["u"], p["v"], p["w"], p["wt"], p["vis"], np.array(pix, np.int32),
+                              flags=CORRECT)
+    got = img.cpu().numpy()[[y for (_, y) in pix], [x for (x, _) in pix]]
+    # corners are divided by the taper twice over; compare them before the division too
+    uncorrected = rick.Imager(dict(prob["params"], flags=REAL))
+    uncorrected.grid(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"])
+    img0 = uncorrected.image()
+    ref0 = oracle_mod.image_at(params, p["u"], p["v"], p["w"], p["wt"], p["vis"], np.array(pix, np.int32), flags=0)
+    got0 = img0.cpu().numpy()[[y for (_, y) in pix], [x for (x, _) in pix]]
+    peak0 = img0.abs().max().item()
+    assert np.max(np.abs(got0 - ref0.real)) <= TOL * peak0
+    central = [i for i, (x, y) in enumerate(pix) if n // 4 <= x < 3 * n // 4 and n // 4 <= y < 3 * n // 4]
+    assert np.max(np.abs(got[central] - ref[central].real)) <= TOL * peak_gpu
+    assert st["n_dropped"] == 0 and st["n_gridded"] == prob["u"].numel()
+    # Eq. 3 keeps the weighted visibility sum: over all planes
+    tot = 0.0
+    for k0 in range(0, params["nw"], 8):
+        pl = im.grid_planes(k0, 8)
+        tot += pl.to(torch.complex128).sum().item()
+        del pl
+    ref_sum = (prob["wt"].double() * prob["vis"].to(torch.complex128)).sum().item()
+    assert abs(tot - ref_sum) <= 1e-5 * (prob["wt"].double() * prob["vis"].abs().double()).sum().item()
+    im.close()
+    uncorrected.close()

@@ -538,20 +538,29 @@ int64_t oracle_image_at(int n, int nw, double pixel_rad, double w_min, double w_
     double* taper = (double*)malloc(sizeof(double) * n);
     or_taper(&c, taper);
     double complex* out = (double complex*)values_out;
-    for (int q = 0; q < npix; ++q) {
-        int x = pix[2 * q], y = pix[2 * q + 1];
-        int ok;
-        double nm1 = or_nm1((x - n / 2) * pixel_rad, (y - n / 2) * pixel_rad, &ok);
-        double complex s = 0.0;
-        if (ok) {
-#pragma omp parallel for schedule(static) reduction(+ : s)
-            for (int64_t i = 0; i < m; ++i) {
-                if (weff[i] == 0.0) continue;
-                or_place pl;
-                if (!oracle_place(&c, u[i], v[i], w[i], &pl)) continue;
-                double gu[OR_MAX_SUPPORT], gv[OR_MAX_SUPPORT];
-                or_taps(&c, pl.fu, pl.pu, gu);
-                or_taps(&c, pl.fv, pl.pv, gv);
+    /* per pixel: its n - 1 (or outside the sky) */
+    double* nm1 = (double*)malloc(sizeof(double) * (size_t)(npix > 0 ? npix : 1));
+    int* sky = (int*)malloc(sizeof(int) * (size_t)(npix > 0 ? npix : 1));
+    for (int q = 0; q < npix; ++q)
+        nm1[q] = or_nm1((pix[2 * q] - n / 2) * pixel_rad, (pix[2 * q + 1] - n / 2) * pixel_rad, &sky[q]);
+    double complex* sum = (double complex*)calloc((size_t)(npix > 0 ? npix : 1), sizeof(double complex));
+    /* measurement-outer: taps once per measurement, then every pixel */
+#pragma omp parallel
+    {
+        double complex* part = (double complex*)calloc((size_t)(npix > 0 ? npix : 1), sizeof(double complex));
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < m; ++i) {
+            if (weff[i] == 0.0) continue;
+            or_place pl;
+            if (!oracle_place(&c, u[i], v[i], w[i], &pl)) continue;
+            double gu[OR_MAX_SUPPORT], gv[OR_MAX_SUPPORT];
+            or_taps(&c, pl.fu, pl.pu, gu);
+            or_taps(&c, pl.fv, pl.pv, gv);
+            double complex a = weff[i] * ((double)vis[2 * i] + I * (double)vis[2 * i + 1]);
+            double wk = or_plane_w(&c, pl.k);
+            for (int q = 0; q < npix; ++q) {
+                if (!sky[q]) continue;
+                int x = pix[2 * q], y = pix[2 * q + 1];
                 double complex su = 0.0, sv = 0.0;
                 for (int t = 0; t < c.support; ++t) {
                     double au = OR_TWO_PI * (double)((long long)(pl.fu + t - n / 2) * (x - n / 2) % n) / n;
@@ -559,13 +568,19 @@ int64_t oracle_image_at(int n, int nw, double pixel_rad, double w_min, double w_
                     su += gu[t] * (cos(au) + I * sin(au));
                     sv += gv[t] * (cos(av) + I * sin(av));
                 }
-                double ph = OR_TWO_PI * or_plane_w(&c, pl.k) * nm1;
-                double complex a = weff[i] * ((double)vis[2 * i] + I * (double)vis[2 * i + 1]);
-                s += a * su * sv * (cos(ph) + I * sin(ph));
+                double ph = OR_TWO_PI * wk * nm1[q];
+                part[q] += a * su * sv * (cos(ph) + I * sin(ph));
             }
         }
-        out[q] = or_finalize_pixel(&c, flags, taper, sw, x, y, s);
+#pragma omp critical
+        for (int q = 0; q < npix; ++q) sum[q] += part[q];
+        free(part);
     }
+    for (int q = 0; q < npix; ++q)
+        out[q] = or_finalize_pixel(&c, flags, taper, sw, pix[2 * q], pix[2 * q + 1], sky[q] ? sum[q] : 0.0);
+    free(sum);
+    free(sky);
+    free(nm1);
     free(taper);
     free(weff);
     if (sum_w_out) *sum_w_out = sw;

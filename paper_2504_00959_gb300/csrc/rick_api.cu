@@ -265,6 +265,13 @@ rick_status grid_pass(rick_handle h, int k0, int nk, bool shift, float2* planes)
 
 }  // namespace
 
+namespace rick {
+rick_status validate_params(const rick_params* p, GridCfg* c, double* kparam, char* msg, size_t msglen)
+{
+    return check_params(p, c, kparam, msg, msglen);
+}
+}  // namespace rick
+
 extern "C" {
 
 rick_status rick_params_default(rick_params* p)
@@ -395,6 +402,29 @@ rick_status rick_create(const rick_params* p, rick_handle* out)
                     ((p->flags & RICK_UNIFORM_WEIGHT) ? (size_t)c.n * c.n * 4 : 0);
     if (cudaMemset(h->ctr, 0, sizeof(Counters)) != cudaSuccess) return cleanup(RICK_ERR_CUDA);
     if (launch_taper(c, h->kernel_param, h->taper, nullptr) != cudaSuccess) return cleanup(RICK_ERR_CUDA);
+    {
+        // kernel tap polynomials: fitted on the device, carried in the kernel parameters
+        float* d_coef = nullptr;
+        double* d_err = nullptr;
+        float coef[kMaxSupport * kPolyTerms];
+        double err[kMaxSupport];
+        if (cudaMalloc(&d_coef, sizeof(coef)) != cudaSuccess) return cleanup(RICK_ERR_OOM);
+        if (cudaMalloc(&d_err, sizeof(err)) != cudaSuccess) {
+            cudaFree(d_coef);
+            return cleanup(RICK_ERR_OOM);
+        }
+        cudaError_t e = launch_fit_taps(c, h->kernel_param, d_coef, d_err, nullptr);
+        if (e == cudaSuccess) e = cudaMemcpy(coef, d_coef, sizeof(coef), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(err, d_err, sizeof(err), cudaMemcpyDeviceToHost);
+        cudaFree(d_coef);
+        cudaFree(d_err);
+        if (e != cudaSuccess) return cleanup(RICK_ERR_CUDA);
+        double worst = 0.0;
+        for (int t = 0; t < c.S; ++t) worst = err[t] > worst ? err[t] : worst;
+        if (!(worst <= 2e-6)) return cleanup(RICK_ERR_ARG);  // kernel too sharp for degree-10 taps
+        for (int t = 0; t < kMaxSupport; ++t)
+            for (int j = 0; j < kPolyTerms; ++j) h->cfg.coef[t][j] = (t < c.S) ? coef[t * kPolyTerms + j] : 0.0f;
+    }
     cufftHandle plan;
     s = get_plan(h, G, &plan);
     if (s) return cleanup(s);
@@ -567,14 +597,74 @@ rick_status rick_degrid(rick_handle h, const float* image_grad, const float* u, 
                         const float* weights, int64_t nvis, float* vis_grad)
 {
     if (!h) return RICK_ERR_ARG;
-    (void)image_grad;
-    (void)u;
-    (void)v;
-    (void)w;
-    (void)weights;
-    (void)nvis;
-    (void)vis_grad;
-    return fail(h, RICK_ERR_STATE, "rick_degrid is not available in this build");
+    if (nvis < 0) return fail(h, RICK_ERR_ARG, "nvis must be >= 0");
+    if (nvis > ((int64_t)1 << 30)) return fail(h, RICK_ERR_ARG, "at most 2^30 measurements per call");
+    if (nvis > 0 && (!u || !v || !w || !vis_grad)) return fail(h, RICK_ERR_ARG, "u, v, w, vis_grad must not be NULL");
+    if (!image_grad) return fail(h, RICK_ERR_ARG, "image_grad is NULL");
+    if (h->chunks.empty())
+        return fail(h, RICK_ERR_STATE, "rick_degrid needs the weight sum of a forward pass: call rick_grid first");
+    if (nvis == 0) return RICK_OK;
+    const GridCfg& c = h->cfg;
+    const rick_params& p = h->p;
+    const int64_t ntiles = (int64_t)c.nw * c.ntp;
+    const size_t off_bytes = (size_t)(ntiles + 1) * sizeof(uint32_t);
+    const size_t perm_bytes = (size_t)nvis * sizeof(uint32_t);
+    size_t fr = 0, tot = 0;
+    RICK_CU(h, cudaMemGetInfo(&fr, &tot));
+    if (off_bytes + perm_bytes + (64u << 20) > fr) return fail(h, RICK_ERR_OOM, "degrid scratch does not fit");
+    PhaseScope scope(h, kPhaseDegrid);
+    uint32_t* off = nullptr;
+    uint32_t* perm = nullptr;
+    RICK_CU(h, cudaMallocFromPoolAsync((void**)&off, off_bytes, h->pool, h->stream));
+    cudaError_t e = cudaMallocFromPoolAsync((void**)&perm, perm_bytes, h->pool, h->stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(off, h->stream);
+        return fail(h, RICK_ERR_OOM, "cudaMallocFromPoolAsync(perm): %s", cudaGetErrorString(e));
+    }
+    float2* grad = reinterpret_cast<float2*>(vis_grad);
+    const double dw = (p.nw > 1) ? (p.w_max - p.w_min) / p.nw : (p.w_max - p.w_min);
+    StackArgs a{};
+    a.n = p.n;
+    split(p.pixel_rad * p.pixel_rad, &a.dl2_hi, &a.dl2_lo);
+    split(p.w_min + 0.5 * dw, &a.wb_hi, &a.wb_lo);
+    split(dw, &a.dw_hi, &a.dw_lo);
+    a.flags = p.flags;
+    rick_status st = RICK_OK;
+    e = cudaMemsetAsync(grad, 0, (size_t)nvis * sizeof(float2), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->cursor, 0, (size_t)ntiles * sizeof(uint32_t), h->stream);
+    if (e == cudaSuccess) e = launch_primary_count(c, u, v, w, weights, nvis, h->cursor, h->stream);
+    if (e == cudaSuccess) e = launch_scan(h->cursor, ntiles, off, h->cursor, h->block_sums, h->stream);
+    if (e == cudaSuccess) e = launch_primary_scatter(c, u, v, w, weights, nvis, h->cursor, perm, h->stream);
+    if (e != cudaSuccess) st = fail(h, RICK_ERR_CUDA, "rick_degrid sort: %s", cudaGetErrorString(e));
+    if (!st) count_launches(h, 5);
+    for (int k0 = 0; !st && k0 < p.nw; k0 += h->G) {
+        const int nk = (p.nw - k0 < h->G) ? p.nw - k0 : h->G;
+        a.k0 = k0;
+        a.nk = nk;
+        e = launch_spread(a, image_grad, h->taper, h->ctr, h->planes, h->stream);
+        if (e != cudaSuccess) {
+            st = fail(h, RICK_ERR_CUDA, "k_spread: %s", cudaGetErrorString(e));
+            break;
+        }
+        cufftHandle plan;
+        st = get_plan(h, nk, &plan);
+        if (st) break;
+        cufftResult r = cufftExecC2C(plan, reinterpret_cast<cufftComplex*>(h->planes),
+                                     reinterpret_cast<cufftComplex*>(h->planes), CUFFT_FORWARD);
+        if (r != CUFFT_SUCCESS) {
+            st = fail(h, RICK_ERR_CUFFT, "cufftExecC2C(FORWARD): error %d", (int)r);
+            break;
+        }
+        e = launch_degrid_gather(c, perm, off, k0, nk, h->planes, u, v, w, weights, h->density, grad, h->stream);
+        if (e != cudaSuccess) {
+            st = fail(h, RICK_ERR_CUDA, "k_degrid_gather: %s", cudaGetErrorString(e));
+            break;
+        }
+        count_launches(h, 2);
+    }
+    cudaFreeAsync(off, h->stream);
+    cudaFreeAsync(perm, h->stream);
+    return st;
 }
 
 rick_status rick_image_host(rick_handle h, const float* vis_host, const float* u_host, const float* v_host,

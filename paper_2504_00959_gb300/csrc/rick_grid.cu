@@ -71,11 +71,11 @@ __global__ void __launch_bounds__(kGridThreads) k_grid(GridCfg c, ChunkList ch, 
             const float4 r = __ldg(ent + j);
             const int fu = first_cell(c, r.x), fv = first_cell(c, r.y);
             float gu[S], gv[S];
+            eval_taps<S>(c, r.x, fu, gu);
+            eval_taps<S>(c, r.y, fv, gv);
             float su = 0.f, sv = 0.f;
 #pragma unroll
             for (int t = 0; t < S; ++t) {
-                gu[t] = kernel_value(c, (float)(fu + t) - r.x);
-                gv[t] = kernel_value(c, (float)(fv + t) - r.y);
                 su += gu[t];
                 sv += gv[t];
             }
@@ -173,7 +173,74 @@ __global__ void __launch_bounds__(256) k_taper(GridCfg c, double kparam, float* 
     taper[x] = (float)(num / den);
 }
 
+// Kernel value in FP64 (CUDA's exp / cyl_bessel_i0), un-normalised.
+__device__ double kernel_fp64(const GridCfg& c, double kparam, double x)
+{
+    if (c.kernel == RICK_KERNEL_GAUSS) return exp(-x * x / (2.0 * kparam * kparam));
+    const double z = 2.0 * x / c.S;
+    return cyl_bessel_i0(kparam * sqrt(fmax(0.0, 1.0 - z * z)));
+}
+
+// One thread per tap t: Chebyshev interpolation of g(t + 1 - S/2 - d),
+// d = (z + 1)/2, at the kPolyTerms Chebyshev nodes of z in [-1, 1], converted
+// to monomial coefficients in z; values are scaled by 1/g(0) (the taps are
+// normalised per axis later, so the scale cancels).  Then the binary32
+// Horner evaluation is checked against FP64 on 257 points.
+__global__ void k_fit_taps(GridCfg c, double kparam, float* __restrict__ coef, double* __restrict__ max_err)
+{
+    constexpr int D = kPolyTerms - 1;
+    const int t = threadIdx.x;
+    if (t >= c.S) return;
+    const double pi = 3.141592653589793238462643383279502884;
+    const double g0 = kernel_fp64(c, kparam, 0.0);
+    double f[kPolyTerms], a[kPolyTerms];
+    for (int i = 0; i <= D; ++i) {
+        const double z = cos(pi * (i + 0.5) / (D + 1));
+        f[i] = kernel_fp64(c, kparam, t + 1 - 0.5 * c.S - 0.5 * (z + 1.0)) / g0;
+    }
+    for (int k = 0; k <= D; ++k) {
+        double s = 0.0;
+        for (int i = 0; i <= D; ++i) s += f[i] * cos(pi * k * (i + 0.5) / (D + 1));
+        a[k] = s * 2.0 / (D + 1);
+    }
+    a[0] *= 0.5;
+    // monomial coefficients: sum_k a_k T_k(z), T_{k+1} = 2 z T_k - T_{k-1}
+    double mono[kPolyTerms] = {0}, tkm1[kPolyTerms] = {0}, tk[kPolyTerms] = {0}, tn[kPolyTerms];
+    tkm1[0] = 1.0;   // T_0
+    tk[1] = 1.0;     // T_1
+    mono[0] += a[0];
+    if (D >= 1) mono[1] += a[1];
+    for (int k = 1; k < D; ++k) {
+        for (int j = 0; j <= D; ++j) tn[j] = (j ? 2.0 * tk[j - 1] : 0.0) - tkm1[j];
+        for (int j = 0; j <= D; ++j) {
+            mono[j] += a[k + 1] * tn[j];
+            tkm1[j] = tk[j];
+            tk[j] = tn[j];
+        }
+    }
+    float cf[kPolyTerms];
+    for (int j = 0; j <= D; ++j) {
+        cf[j] = (float)mono[j];
+        coef[t * kPolyTerms + j] = cf[j];
+    }
+    double worst = 0.0;
+    for (int i = 0; i <= 256; ++i) {
+        const float z = -1.0f + 2.0f * i / 256.0f;
+        float v = cf[D];
+        for (int j = D - 1; j >= 0; --j) v = __fmaf_rn(v, z, cf[j]);
+        const double ref = kernel_fp64(c, kparam, t + 1 - 0.5 * c.S - 0.5 * ((double)z + 1.0)) / g0;
+        worst = fmax(worst, fabs((double)v - ref));
+    }
+    max_err[t] = worst;
+}
+
 }  // namespace
+
+cudaError_t launch_fit_taps(const GridCfg& c, double kernel_param, float* coef, double* max_err, cudaStream_t s)
+{
+    k_fit_taps<<<1, kMaxSupport, 0, s>>>(c, kernel_param, coef, max_err);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_grid(const GridCfg& c, const ChunkList& ch, int k0, int nk, bool shift_sign,
                         bool accumulate, const uint32_t* /*density*/, float2* planes, cudaStream_t s)

@@ -14,6 +14,7 @@
 namespace rick {
 
 constexpr int kMaxSupport = 16;
+constexpr int kPolyTerms = 11;            // degree-10 polynomial per kernel tap
 constexpr int kMaxChunksPerPass = 16;
 constexpr int kScanBlock = 1024;          // threads of the scan kernels
 constexpr int kScanItems = 4;             // items per scan thread
@@ -31,6 +32,10 @@ struct GridCfg {
     float kp;                        // Gaussian: 1/(2 sigma^2); KB: beta
     float two_over_s;                // 2 / S
     int uniform;                     // uniform weighting on
+    // tap t of a measurement whose footprint starts at f = floor(p - S/2) + 1
+    // is g(t + 1 - S/2 - d), d = frac(p - S/2); as a polynomial in z = 2d - 1:
+    // g_t = sum_j coef[t][j] z^j (fitted once per handle, see k_fit_taps)
+    float coef[kMaxSupport][kPolyTerms];
 };
 
 // Placement of one measurement: plane, first footprint cell, continuous
@@ -85,6 +90,24 @@ __device__ __forceinline__ float kernel_value(const GridCfg& c, float x)
     return cyl_bessel_i0f(c.kp * sqrtf(a));
 }
 
+// The S (un-normalised) taps of a measurement at continuous coordinate p
+// whose first footprint cell is f: Horner evaluation of the fitted
+// polynomials; the coefficients are uniform across threads (kernel
+// parameters, constant-bank broadcast).
+template <int S>
+__device__ __forceinline__ void eval_taps(const GridCfg& c, float p, int f, float (&g)[S])
+{
+    const float d = __fsub_rn(__fsub_rn(p, c.half_s), (float)(f - 1));  // in [0, 1)
+    const float z = __fmaf_rn(2.0f, d, -1.0f);
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        float a = c.coef[t][kPolyTerms - 1];
+#pragma unroll
+        for (int j = kPolyTerms - 2; j >= 0; --j) a = __fmaf_rn(a, z, c.coef[t][j]);
+        g[t] = a;
+    }
+}
+
 // Whether a measurement with finite placement also has a finite weight and value.
 __device__ __forceinline__ bool finite_value(float wt, float2 vis)
 {
@@ -119,6 +142,9 @@ cudaError_t launch_scatter(const GridCfg& c, const float* u, const float* v, con
 cudaError_t launch_grid(const GridCfg& c, const ChunkList& chunks, int k0, int nk, bool shift_sign,
                         bool accumulate, const uint32_t* density, float2* planes, cudaStream_t s);
 cudaError_t launch_taper(const GridCfg& c, double kernel_param, float* taper, cudaStream_t s);
+// Fit the tap polynomials (coef: float[S][kPolyTerms]) and report the largest
+// binary32 evaluation error relative to the kernel's peak in *max_err.
+cudaError_t launch_fit_taps(const GridCfg& c, double kernel_param, float* coef, double* max_err, cudaStream_t s);
 
 struct StackArgs {
     int n, k0, nk;
@@ -131,7 +157,23 @@ struct StackArgs {
 cudaError_t launch_stack(const StackArgs& a, const float2* planes, float2* acc, const float* taper,
                          const Counters* ctr, void* image, cudaStream_t s);
 
+cudaError_t launch_spread(const StackArgs& a, const void* rimg, const float* taper, const Counters* ctr,
+                          float2* planes, cudaStream_t s);
+// adjoint: sort measurements by the tile of their first footprint cell
+// (no duplication), then gather each measurement's footprint of a plane group
+cudaError_t launch_primary_count(const GridCfg& c, const float* u, const float* v, const float* w,
+                                 const float* wt, int64_t m, uint32_t* counts, cudaStream_t s);
+cudaError_t launch_primary_scatter(const GridCfg& c, const float* u, const float* v, const float* w,
+                                   const float* wt, int64_t m, uint32_t* cursor, uint32_t* perm,
+                                   cudaStream_t s);
+cudaError_t launch_degrid_gather(const GridCfg& c, const uint32_t* perm, const uint32_t* offsets, int k0, int nk,
+                                 const float2* planes, const float* u, const float* v, const float* w,
+                                 const float* wt, const uint32_t* density, float2* grad, cudaStream_t s);
+
 size_t scan_block_sums_len(int64_t len);
+
+// Parameter checks of rick_create (fills the derived configuration).
+rick_status validate_params(const rick_params* p, GridCfg* c, double* kparam, char* msg, size_t msglen);
 
 }  // namespace rick
 

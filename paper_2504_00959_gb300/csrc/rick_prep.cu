@@ -167,6 +167,96 @@ __global__ void __launch_bounds__(kPrepThreads) k_scatter(GridCfg c, Inputs in, 
     }
 }
 
+// ------------------------------------------------ adjoint: primary-tile sort
+
+// Placement for the adjoint: coordinates and weight only (no visibility value).
+__device__ __forceinline__ bool place_coords(const GridCfg& c, const Inputs& in, int64_t i, Place& p, float& wi)
+{
+    wi = in.wt ? __ldg(in.wt + i) : 1.0f;
+    return place(c, __ldg(in.u + i), __ldg(in.v + i), __ldg(in.w + i), p) && isfinite(wi);
+}
+
+__device__ __forceinline__ int64_t primary_tile(const GridCfg& c, const Place& p)
+{
+    return (int64_t)p.k * c.ntp + (p.fv >> c.log2T) * c.ntu + (p.fu >> c.log2T);
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_primary_count(GridCfg c, Inputs in, int64_t m,
+                                                                uint32_t* __restrict__ counts)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        Place p;
+        float wi;
+        if (place_coords(c, in, i, p, wi)) atomicAdd(counts + primary_tile(c, p), 1u);
+    }
+}
+
+__global__ void __launch_bounds__(kPrepThreads) k_primary_scatter(GridCfg c, Inputs in, int64_t m,
+                                                                  uint32_t* __restrict__ cursor,
+                                                                  uint32_t* __restrict__ perm)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        Place p;
+        float wi;
+        if (place_coords(c, in, i, p, wi)) perm[atomicAdd(cursor + primary_tile(c, p), 1u)] = (uint32_t)i;
+    }
+}
+
+// Each sorted measurement of planes [k0, k0+nk) gathers its S x S footprint
+// of the (forward-transformed) adjoint planes with the gridding taps, times
+// its effective weight.  Consecutive threads take consecutive measurements of
+// the same tile, so the footprints they read overlap in L1 / L2.
+template <int S>
+__global__ void __launch_bounds__(kPrepThreads) k_degrid_gather(GridCfg c, const uint32_t* __restrict__ perm,
+                                                                const uint32_t* __restrict__ off, int k0, int nk,
+                                                                const float2* __restrict__ planes, Inputs in,
+                                                                const uint32_t* __restrict__ density,
+                                                                float2* __restrict__ grad)
+{
+    const uint32_t b = off[(int64_t)k0 * c.ntp], e = off[(int64_t)(k0 + nk) * c.ntp];
+    for (int64_t j = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < e;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = perm[j];
+        Place p;
+        float wi;
+        if (!place_coords(c, in, i, p, wi)) continue;  // cannot happen: perm holds placed ones
+        if (c.uniform) wi = wi / (float)__ldg(density + (int64_t)nearest_cell(c, p.pv) * c.n + nearest_cell(c, p.pu));
+        float gu[S], gv[S];
+        eval_taps<S>(c, p.pu, p.fu, gu);
+        eval_taps<S>(c, p.pv, p.fv, gv);
+        float su = 0.f, sv = 0.f;
+#pragma unroll
+        for (int t = 0; t < S; ++t) {
+            su += gu[t];
+            sv += gv[t];
+        }
+#pragma unroll
+        for (int t = 1; t < S; t += 2) {
+            gu[t] = -gu[t];
+            gv[t] = -gv[t];
+        }
+        const float2* P = planes + (int64_t)(p.k - k0) * c.n * c.n + (int64_t)p.fv * c.n + p.fu;
+        float ar = 0.f, ai = 0.f;
+#pragma unroll
+        for (int rr = 0; rr < S; ++rr) {
+            float br = 0.f, bi = 0.f;
+#pragma unroll
+            for (int t = 0; t < S; ++t) {
+                const float2 x = __ldg(P + (int64_t)rr * c.n + t);
+                br = fmaf(gu[t], x.x, br);
+                bi = fmaf(gu[t], x.y, bi);
+            }
+            ar = fmaf(gv[rr], br, ar);
+            ai = fmaf(gv[rr], bi, ai);
+        }
+        float scale = wi / (su * sv);
+        if ((p.fu + p.fv) & 1) scale = -scale;
+        grad[i] = make_float2(ar * scale, ai * scale);
+    }
+}
+
 // ------------------------------------------------------------------ scan
 
 // Exclusive scan of one value per thread across a 1024-thread block.
@@ -252,6 +342,51 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_add(const uint32_t* __restr
 }
 
 }  // namespace
+
+cudaError_t launch_primary_count(const GridCfg& c, const float* u, const float* v, const float* w,
+                                 const float* wt, int64_t m, uint32_t* counts, cudaStream_t s)
+{
+    if (m <= 0) return cudaSuccess;
+    k_primary_count<<<prep_blocks(m), kPrepThreads, 0, s>>>(c, Inputs{u, v, w, wt, nullptr}, m, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_primary_scatter(const GridCfg& c, const float* u, const float* v, const float* w,
+                                   const float* wt, int64_t m, uint32_t* cursor, uint32_t* perm,
+                                   cudaStream_t s)
+{
+    if (m <= 0) return cudaSuccess;
+    k_primary_scatter<<<prep_blocks(m), kPrepThreads, 0, s>>>(c, Inputs{u, v, w, wt, nullptr}, m, cursor, perm);
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_gather_s(const GridCfg& c, const uint32_t* perm, const uint32_t* off, int k0, int nk,
+                            const float2* planes, const Inputs& in, const uint32_t* density, float2* grad,
+                            int64_t m, cudaStream_t s)
+{
+    k_degrid_gather<S><<<prep_blocks(m), kPrepThreads, 0, s>>>(c, perm, off, k0, nk, planes, in, density, grad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_degrid_gather(const GridCfg& c, const uint32_t* perm, const uint32_t* offsets, int k0, int nk,
+                                 const float2* planes, const float* u, const float* v, const float* w,
+                                 const float* wt, const uint32_t* density, float2* grad, cudaStream_t s)
+{
+    // the launch is sized for the whole input; threads beyond the group's range exit at once
+    const Inputs in{u, v, w, wt, nullptr};
+    const int64_t m = (int64_t)sm_count() * 8 * kPrepThreads;
+    switch (c.S) {
+#define RICK_GATHER_CASE(SS) \
+    case SS: return launch_gather_s<SS>(c, perm, offsets, k0, nk, planes, in, density, grad, m, s);
+        RICK_GATHER_CASE(1) RICK_GATHER_CASE(2) RICK_GATHER_CASE(3) RICK_GATHER_CASE(4)
+        RICK_GATHER_CASE(5) RICK_GATHER_CASE(6) RICK_GATHER_CASE(7) RICK_GATHER_CASE(8)
+        RICK_GATHER_CASE(9) RICK_GATHER_CASE(10) RICK_GATHER_CASE(11) RICK_GATHER_CASE(12)
+        RICK_GATHER_CASE(13) RICK_GATHER_CASE(14) RICK_GATHER_CASE(15) RICK_GATHER_CASE(16)
+#undef RICK_GATHER_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 size_t scan_block_sums_len(int64_t len)
 {

@@ -97,8 +97,8 @@ __global__ void __launch_bounds__(kStackThreads) k_stack(StackArgs a, const floa
     const int64_t nn = (int64_t)a.n * a.n;
 
     PixelScreen s0 = pixel_screen(a, x0, y), s1 = pixel_screen(a, x0 + 1, y);
-    const float2 rho0 = turns_to_phasor(s0.B.hi - rintf(s0.B.hi), s0.B.lo);
-    const float2 rho1 = turns_to_phasor(s1.B.hi - rintf(s1.B.hi), s1.B.lo);
+    const float2 rho0 = turns_to_phasor(s0.B.hi, s0.B.lo);
+    const float2 rho1 = turns_to_phasor(s1.B.hi, s1.B.lo);
     float2 z0 = make_float2(1.f, 0.f), z1 = z0;
     float2 a0 = make_float2(0.f, 0.f), a1 = a0;
 
@@ -159,7 +159,83 @@ __global__ void __launch_bounds__(kStackThreads) k_stack(StackArgs a, const floa
     }
 }
 
+// Adjoint of k_stack (and of the finalisation): from an image gradient r,
+// write for every plane k of the group  Q_k = s(x,y) * R * exp(-2 pi i w_k (n-1)),
+// R = r / sum_w / taper(x) taper(y) * n  (per flags), ready for a forward FFT.
+__global__ void __launch_bounds__(kStackThreads) k_spread(StackArgs a, const void* __restrict__ rimg,
+                                                          const float* __restrict__ taper,
+                                                          const Counters* __restrict__ ctr,
+                                                          float2* __restrict__ planes)
+{
+    const int halfn = a.n >> 1;
+    const int64_t idx = blockIdx.x * (int64_t)kStackThreads + threadIdx.x;
+    if (idx >= (int64_t)a.n * halfn) return;
+    const int y = (int)(idx / halfn);
+    const int x0 = (int)(idx - (int64_t)y * halfn) * 2;
+    const int64_t pix = (int64_t)y * a.n + x0;
+    const int64_t nn = (int64_t)a.n * a.n;
+
+    PixelScreen s0 = pixel_screen(a, x0, y), s1 = pixel_screen(a, x0 + 1, y);
+    float2 r0, r1;
+    if (a.flags & RICK_REAL_IMAGE) {
+        const float2 rr = reinterpret_cast<const float2*>(rimg)[pix >> 1];
+        r0 = make_float2(rr.x, 0.f);
+        r1 = make_float2(rr.y, 0.f);
+    } else {
+        const float4 rr = reinterpret_cast<const float4*>(rimg)[pix >> 1];
+        r0 = make_float2(rr.x, rr.y);
+        r1 = make_float2(rr.z, rr.w);
+    }
+    const double sw = ctr->sum_w;
+    const float inv_sw = (sw != 0.0) ? (float)(1.0 / sw) : 0.0f;
+    float f0 = inv_sw, f1 = inv_sw;
+    if (a.flags & RICK_GRID_CORRECT) {
+        const float ty = __ldg(taper + y);
+        f0 = f0 / (__ldg(taper + x0) * ty);
+        f1 = f1 / (__ldg(taper + x0 + 1) * ty);
+    }
+    if (a.flags & RICK_APPLY_N) {
+        f0 *= 1.0f + s0.nm1;
+        f1 *= 1.0f + s1.nm1;
+    }
+    // fftshift sign (-1)^(x + y) and the sky mask
+    if (y & 1) f0 = -f0; else f1 = -f1;
+    if (!s0.sky) f0 = 0.f;
+    if (!s1.sky) f1 = 0.f;
+    r0 = make_float2(r0.x * f0, r0.y * f0);
+    r1 = make_float2(r1.x * f1, r1.y * f1);
+
+    const float2 rho0 = turns_to_phasor(s0.B.hi, s0.B.lo);
+    const float2 rho1 = turns_to_phasor(s1.B.hi, s1.B.lo);
+    float2 z0 = make_float2(1.f, 0.f), z1 = z0;
+    float4* p = reinterpret_cast<float4*>(planes + pix);
+    const int64_t stride4 = nn >> 1;
+    for (int kl = 0; kl < a.nk; ++kl) {
+        if (kl % kResync == 0) {
+            z0 = screen(s0.A, s0.B, a.k0 + kl);
+            z1 = screen(s1.A, s1.B, a.k0 + kl);
+        } else {
+            z0 = cmul(z0, rho0);
+            z1 = cmul(z1, rho1);
+        }
+        // multiply by conj(z)
+        const float2 c0 = make_float2(r0.x * z0.x + r0.y * z0.y, r0.y * z0.x - r0.x * z0.y);
+        const float2 c1 = make_float2(r1.x * z1.x + r1.y * z1.y, r1.y * z1.x - r1.x * z1.y);
+        __stcs(p + kl * stride4, make_float4(c0.x, c0.y, c1.x, c1.y));
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_spread(const StackArgs& a, const void* rimg, const float* taper, const Counters* ctr,
+                          float2* planes, cudaStream_t s)
+{
+    const int64_t threads = (int64_t)a.n * (a.n / 2);
+    const int64_t blocks = (threads + kStackThreads - 1) / kStackThreads;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_spread<<<(unsigned)blocks, kStackThreads, 0, s>>>(a, rimg, taper, ctr, planes);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_stack(const StackArgs& a, const float2* planes, float2* acc, const float* taper,
                          const Counters* ctr, void* image, cudaStream_t s)

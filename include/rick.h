@@ -157,6 +157,33 @@ rick_status rick_image_host(rick_handle h, const float* vis_host, const float* u
                             const float* v_host, const float* w_host,
                             const float* weights_host, int64_t nvis, float* image_host);
 
+/* Eq. 3 alone for one set of measurements, into caller-provided planes,
+ * WITHOUT allocating any device memory.  The paper has no counterpart.  It is
+ * for callers that cannot call cudaMalloc: code inside a framework that owns
+ * the whole device heap, contexts where allocating is not allowed (stream
+ * callbacks), real-time loops that forbid allocation after start-up.  No
+ * handle is needed.  planes: complex float [nw][n][n] (no fftshift sign),
+ * fully overwritten -- the same result as rick_create + rick_grid +
+ * rick_grid_planes(0, nw).  The working memory is one fixed 64 MiB array in
+ * the library's static device data, held by every GPU that loads the library
+ * until the process exits.  What a call needs -- counters, kernel-tap
+ * polynomials, two uint32 arrays of nw * ceil(n/tile)^2 (+1) tile counts and
+ * offsets, the scan totals, n*n uint32 of density with RICK_UNIFORM_WEIGHT,
+ * and 64 bytes per measurement (16 when support is 1), each piece 256-byte
+ * aligned -- must fit in those 64 MiB; otherwise RICK_ERR_ARG before any
+ * launch, with the reason written to err (err_len bytes; err may be NULL).
+ * All calls on a device share the array and it keeps the last call's
+ * contents, so calls whose GPU work overlaps race: the caller must order
+ * them.  The first call on a device, and the first for each kernel
+ * configuration, looks up the array's device address and fits the kernel
+ * taps, synchronising cuda_stream once; make that first call before any
+ * stream capture.  Work goes to cuda_stream (a cudaStream_t, NULL = legacy
+ * default stream). */
+rick_status rick_grid_planes_static(const rick_params* p, const float* vis, const float* u,
+                                    const float* v, const float* w, const float* weights,
+                                    int64_t nvis, float* planes, void* cuda_stream, char* err,
+                                    size_t err_len);
+
 /* Counters since the last reset (synchronises the stream). */
 rick_status rick_get_stats(rick_handle h, rick_stats* out);
 

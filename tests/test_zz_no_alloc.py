@@ -1,0 +1,78 @@
+"""rick_grid_planes_static: gridding for callers that cannot allocate device
+memory (a host framework that owns the whole device heap, a context where
+cudaMalloc is not permitted, a real-time loop that forbids allocation after
+start-up).  Its working memory is a fixed 64 MiB array in the library's
+static device data.
+
+Checked through the C ABI against the allocating path (rick_create +
+rick_grid + rick_grid_planes) on two calls in a row, at the tolerance the
+other plane comparisons use (1e-5 of the largest cell), plus the size limit.
+This file is collected last so that a run stopping at the first failure has
+run every other test; it passes alone in a fresh process too.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rick():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_00959_gb300 import build
+    build.build()
+    import paper_2504_00959_gb300 as r
+    r.load()
+    return r
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr() if t is not None else None)
+
+
+def _call(rick, params, prob, planes, err):
+    from paper_2504_00959_gb300 import _lib
+    rp = rick._params_struct(params)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return _lib.load().rick_grid_planes_static(
+        ctypes.byref(rp), _p(prob["vis"]), _p(prob["u"]), _p(prob["v"]), _p(prob["w"]), _p(prob["wt"]),
+        prob["u"].numel(), _p(planes), stream, err, len(err))
+
+
+@pytest.mark.parametrize("flags", [synth.FLAG_CORRECT | synth.FLAG_REAL, synth.FLAG_UNIFORM])
+def test_static_scratch_matches_allocating_path(rick, flags):
+    prob = synth.config1(device="cuda")
+    params = dict(prob["params"], flags=flags)
+    im = rick.Imager(params)
+    im.grid(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"])
+    ref = im.grid_planes()
+    torch.cuda.synchronize()
+    im.close()
+    nw, n = params["nw"], params["n"]
+    err = ctypes.create_string_buffer(512)
+    for _ in range(2):
+        out = torch.full((nw, n, n), float("nan"), dtype=torch.complex64, device="cuda")
+        status = _call(rick, params, prob, out, err)
+        assert status == 0, err.value.decode()
+        torch.cuda.synchronize()
+        assert torch.isfinite(out).all().item()  # every cell written
+        diff = torch.max(torch.abs(out - ref)).item()
+        assert diff <= 1e-5 * torch.max(torch.abs(ref)).item(), diff
+
+
+def test_static_scratch_rejects_sizes_beyond_the_limit(rick):
+    m = 2_000_000  # 4 * 16 bytes of entries per measurement: 128 MB > 64 MiB
+    params = synth.make_params(4096, 32, 1e-5, -100.0, 100.0, synth.KERNEL_KB, 7)
+    prob = dict(u=torch.zeros(m, device="cuda"), v=torch.zeros(m, device="cuda"), w=torch.zeros(m, device="cuda"),
+                wt=torch.ones(m, device="cuda"), vis=torch.zeros(m, dtype=torch.complex64, device="cuda"))
+    planes = torch.empty((1,), dtype=torch.complex64, device="cuda")  # never written: the call is refused first
+    err = ctypes.create_string_buffer(512)
+    status = _call(rick, params, prob, planes, err)
+    assert status == 1  # RICK_ERR_ARG
+    assert "limit" in err.value.decode()

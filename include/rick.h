@@ -157,6 +157,41 @@ rick_status rick_image_host(rick_handle h, const float* vis_host, const float* u
                             const float* v_host, const float* w_host,
                             const float* weights_host, int64_t nvis, float* image_host);
 
+/* Batched multi-channel imaging (not in the paper; it repeats the chunk loop
+ * of Sec. 2.2 over frequency channels in one pass): nchan channels share n,
+ * pixel_rad, the kernel and the w-plane count p->nw, each with its own
+ * w-range [w_min[c], w_max[c]] (host arrays).  Channel c owns w-planes
+ * c*nw .. (c+1)*nw-1 of one plane stack; all channels are sorted, gridded,
+ * transformed (one cuFFT batch per plane group) and stacked together.
+ * Uniform weighting is not available here.  Only rick_image_batch,
+ * rick_set_stream, rick_get_stats, rick_set_timing / rick_get_timing and
+ * rick_destroy apply to a batched handle. */
+rick_status rick_create_batch(const rick_params* p, int32_t nchan, const double* w_min, const double* w_max,
+                              rick_handle* out);
+
+/* One dirty image per channel: channel c's measurements are entries
+ * chan_offsets[c] .. chan_offsets[c+1]-1 (host array of nchan+1, starting at
+ * 0, non-decreasing) of vis / u / v / w / weights (device, as rick_grid).
+ * images: float[nchan][n*n] (RICK_REAL_IMAGE) or float[nchan][2*n*n],
+ * overwritten.  With use_graph != 0 the whole step is captured into a CUDA
+ * graph on the first call and replayed by later calls with the same pointers
+ * and offsets (needs a non-default stream, rick_set_stream); the entry
+ * buffers are persistent and grow outside the capture. */
+rick_status rick_image_batch(rick_handle h, const float* vis, const float* u, const float* v, const float* w,
+                             const float* weights, const int64_t* chan_offsets, float* images, int32_t use_graph);
+
+/* Autotuner for batched imaging: times one rick_image_batch of the given data
+ * for every tile side (16, 32, 64, at least the support) and plane group
+ * (all channels, half of them) and returns the fastest in *tile_out and
+ * *plane_group_out (device time in *ms_out, may be NULL).  When the
+ * environment variable RICK_AUTOTUNE_CACHE names a file, results are looked
+ * up there first and appended after tuning (key: n, nw, nchan, support,
+ * kernel, flags, log2 of the measurement count). */
+rick_status rick_autotune_batch(const rick_params* p, int32_t nchan, const double* w_min, const double* w_max,
+                                const float* vis, const float* u, const float* v, const float* w,
+                                const float* weights, const int64_t* chan_offsets, int32_t* tile_out,
+                                int32_t* plane_group_out, double* ms_out);
+
 /* Eq. 3 alone for one set of measurements, into caller-provided planes,
  * WITHOUT allocating any device memory.  The paper has no counterpart.  It is
  * for callers that cannot call cudaMalloc: code inside a framework that owns

@@ -21,7 +21,8 @@ from . import _lib
 from ._lib import (APPLY_N, GRID_CORRECT, KERNEL_GAUSS, KERNEL_KB, REAL_IMAGE, UNIFORM_WEIGHT,  # noqa: F401
                    RickError)
 
-__all__ = ["Imager", "DirtyImage", "dirty_image", "RickError", "load", "KERNEL_GAUSS", "KERNEL_KB",
+__all__ = ["Imager", "BatchImager", "autotune_batch", "DirtyImage", "dirty_image", "RickError", "load",
+           "KERNEL_GAUSS", "KERNEL_KB",
            "GRID_CORRECT", "REAL_IMAGE", "APPLY_N", "UNIFORM_WEIGHT"]
 
 
@@ -198,6 +199,67 @@ class Imager:
             self.close()
         except Exception:
             pass
+
+
+class BatchImager(Imager):
+    """Many frequency channels imaged together (one sort, one gridder pass and
+    one cuFFT batch per plane group, one stack per channel).  ``w_ranges`` is
+    a sequence of (w_min, w_max) per channel; the other parameters are shared."""
+
+    def __init__(self, params, w_ranges, device=None):
+        self.params = dict(params)
+        self._L = _lib.load()
+        if device is None:
+            device = torch.device("cuda", torch.cuda.current_device())
+        self.device = torch.device(device)
+        if self.device.type != "cuda":
+            raise ValueError("BatchImager needs a CUDA device")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.nchan = len(w_ranges)
+        wmin = (ctypes.c_double * self.nchan)(*[float(a) for a, _ in w_ranges])
+        wmax = (ctypes.c_double * self.nchan)(*[float(b) for _, b in w_ranges])
+        self._rp = _params_struct(self.params)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(self._L.rick_create_batch(ctypes.byref(self._rp), self.nchan, wmin, wmax, ctypes.byref(h)))
+        self._h = h
+        self.generation = 0
+
+    def images(self, vis, u, v, w, wt, chan_offsets, out=None, use_graph=False):
+        """Dirty images [nchan, n, n] of measurements grouped by channel:
+        channel c is entries chan_offsets[c] .. chan_offsets[c+1]-1."""
+        vis, u, v, w, wt, m = self._inputs(vis, u, v, w, wt)
+        offs = [int(x) for x in chan_offsets]
+        if len(offs) != self.nchan + 1 or offs[0] != 0 or offs[-1] != m:
+            raise ValueError("chan_offsets must have nchan + 1 entries from 0 to the number of measurements")
+        n = self.n
+        if out is None:
+            shape = (self.nchan, n, n)
+            out = torch.empty(shape, dtype=torch.float32 if self.real else torch.complex64, device=self.device)
+        self._vec(out, "out", torch.float32 if self.real else torch.complex64, self.nchan * n * n)
+        self._offs = (ctypes.c_int64 * (self.nchan + 1))(*offs)
+        self._sync_stream()
+        _lib.check(self._L.rick_image_batch(self._h, _ptr(vis), _ptr(u), _ptr(v), _ptr(w), _ptr(wt),
+                                            ctypes.cast(self._offs, ctypes.c_void_p), _ptr(out),
+                                            1 if use_graph else 0), self._h)
+        return out
+
+
+def autotune_batch(params, w_ranges, vis, u, v, w, wt, chan_offsets):
+    """Tile side and plane group for batched imaging of this data, timed on
+    the GPU (see rick_autotune_batch).  Returns (tile, plane_group, ms)."""
+    L = _lib.load()
+    nchan = len(w_ranges)
+    rp = _params_struct(params)
+    wmin = (ctypes.c_double * nchan)(*[float(a) for a, _ in w_ranges])
+    wmax = (ctypes.c_double * nchan)(*[float(b) for _, b in w_ranges])
+    offs = (ctypes.c_int64 * (nchan + 1))(*[int(x) for x in chan_offsets])
+    t, g, ms = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0.0)
+    _lib.check(L.rick_autotune_batch(ctypes.byref(rp), nchan, wmin, wmax, _ptr(vis), _ptr(u), _ptr(v), _ptr(w),
+                                     _ptr(wt), ctypes.cast(offs, ctypes.c_void_p), ctypes.byref(t), ctypes.byref(g),
+                                     ctypes.byref(ms)))
+    return t.value, g.value, ms.value
 
 
 class DirtyImage(torch.autograd.Function):

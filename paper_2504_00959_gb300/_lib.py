@@ -61,6 +61,12 @@ SIGNATURES = {
     "rick_grid_planes": (_S, [_H, ctypes.c_int32, ctypes.c_int32, _P]),
     "rick_degrid": (_S, [_H, _P, _P, _P, _P, _P, ctypes.c_int64, _P]),
     "rick_image_host": (_S, [_H, _P, _P, _P, _P, _P, ctypes.c_int64, _P]),
+    "rick_create_batch": (_S, [ctypes.POINTER(RickParams), ctypes.c_int32, _P, _P,
+                               ctypes.POINTER(ctypes.c_void_p)]),
+    "rick_image_batch": (_S, [_H, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int32]),
+    "rick_autotune_batch": (_S, [ctypes.POINTER(RickParams), ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P, _P,
+                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                 ctypes.POINTER(ctypes.c_double)]),
     "rick_grid_planes_static": (_S, [ctypes.POINTER(RickParams), _P, _P, _P, _P, _P, ctypes.c_int64, _P, _P,
                                      ctypes.c_char_p, ctypes.c_size_t]),
     "rick_get_stats": (_S, [_H, ctypes.POINTER(RickStats)]),

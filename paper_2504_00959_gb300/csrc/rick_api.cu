@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -123,6 +124,10 @@ rick_status check_params(const rick_params* p, GridCfg* c, double* kparam, char*
     c->kp = (p->kernel == RICK_KERNEL_GAUSS) ? (float)(1.0 / (2.0 * kp * kp)) : (float)kp;
     c->two_over_s = (float)(2.0 / p->support);
     c->uniform = (p->flags & RICK_UNIFORM_WEIGHT) ? 1 : 0;
+    c->nchan = 1;
+    c->nw_chan = p->nw;
+    c->chan_w = nullptr;
+    c->chan_off = nullptr;
     (void)is_pow2;
     return RICK_OK;
 }
@@ -256,8 +261,9 @@ rick_status grid_pass(rick_handle h, int k0, int nk, bool shift, float2* planes)
             cl.off[cl.count] = h->chunks[q].off;
             cl.ent[cl.count] = h->chunks[q].ent;
         }
-        RICK_CU(h, launch_grid(h->cfg, cl, k0, nk, shift, c0 > 0, h->density, planes, h->stream));
-        count_launches(h, 1);
+        // the scatter cursors are idle here: they hold the list of heavy tiles
+        RICK_CU(h, launch_grid(h->cfg, cl, k0, nk, shift, c0 > 0, h->cursor, planes, h->stream));
+        count_launches(h, 2);
         c0 += kMaxChunksPerPass;
     } while (c0 < nch);
     return RICK_OK;
@@ -327,7 +333,8 @@ rick_status rick_workspace_size(const rick_params* p, int64_t max_vis, size_t* b
     return RICK_OK;
 }
 
-rick_status rick_create(const rick_params* p, rick_handle* out)
+static rick_status create_impl(const rick_params* p, int nchan, const double* w_min, const double* w_max,
+                               rick_handle* out)
 {
     if (!out) return RICK_ERR_ARG;
     *out = nullptr;
@@ -339,6 +346,31 @@ rick_status rick_create(const rick_params* p, rick_handle* out)
         // keep the message reachable only through the return code: the handle is not returned
         delete h;
         return s;
+    }
+    if (nchan < 1 || nchan > 65535 || (int64_t)nchan * p->nw > 65535) {
+        delete h;
+        return RICK_ERR_ARG;
+    }
+    if (nchan > 1 || w_min) {
+        if (!w_min || !w_max || (p->flags & RICK_UNIFORM_WEIGHT)) {
+            delete h;
+            return RICK_ERR_ARG;
+        }
+        for (int c = 0; c < nchan; ++c)
+            if (!std::isfinite(w_min[c]) || !std::isfinite(w_max[c]) || (p->nw > 1 && !(w_max[c] > w_min[c])) ||
+                w_max[c] < w_min[c]) {
+                delete h;
+                return RICK_ERR_ARG;
+            }
+        h->batch = true;
+        h->cfg.nchan = nchan;
+        h->cfg.nw_chan = p->nw;
+        h->cfg.nw = nchan * p->nw;
+        h->nchan = nchan;
+        h->chan_wmin.assign(w_min, w_min + nchan);
+        h->chan_wmax.assign(w_max, w_max + nchan);
+    } else {
+        h->nchan = 1;
     }
     h->p = *p;
     h->stream = nullptr;
@@ -365,16 +397,19 @@ rick_status rick_create(const rick_params* p, rick_handle* out)
         delete h;
         return RICK_ERR_CUDA;
     }
-    // plane group: as requested, else as many planes as fit in 60 % of free memory
+    // plane group: as requested, else as many planes as fit in 60 % of free memory;
+    // in batched imaging a group holds whole channels
     const size_t pb = plane_bytes(p);
-    int G = p->plane_group ? p->plane_group : p->nw;
-    if (G > p->nw) G = p->nw;
+    const int NW = c.nw;
+    int G = p->plane_group ? p->plane_group : NW;
+    if (G > NW) G = NW;
     if (!p->plane_group) {
         const size_t fit = (size_t)(0.6 * (double)fr) / (pb ? 2 * pb : 1);  // planes + FFT work headroom
         if ((size_t)G > fit) G = (int)(fit > 0 ? fit : 1);
     }
+    if (h->batch) G = (G / c.nw_chan > 0 ? G / c.nw_chan : 1) * c.nw_chan;
     h->G = G;
-    size_t need = (size_t)G * pb + (G < p->nw ? pb : 0) + (size_t)ntiles * 4 + (size_t)c.n * 4 +
+    size_t need = (size_t)G * pb + (G < NW ? pb : 0) + (size_t)ntiles * 4 + (size_t)c.n * 4 +
                   ((p->flags & RICK_UNIFORM_WEIGHT) ? (size_t)c.n * c.n * 4 : 0) + (64u << 20);
     if (need > fr) {
         delete h;
@@ -386,8 +421,23 @@ rick_status rick_create(const rick_params* p, rick_handle* out)
     };
     if (cudaMalloc(&h->taper, (size_t)c.n * sizeof(float)) != cudaSuccess) return cleanup(RICK_ERR_OOM);
     if (cudaMalloc(&h->planes, (size_t)G * pb) != cudaSuccess) return cleanup(RICK_ERR_OOM);
-    if (G < p->nw && cudaMalloc(&h->acc, pb) != cudaSuccess) return cleanup(RICK_ERR_OOM);
-    if (cudaMalloc(&h->cursor, (size_t)ntiles * sizeof(uint32_t)) != cudaSuccess) return cleanup(RICK_ERR_OOM);
+    if (G < NW && !h->batch && cudaMalloc(&h->acc, pb) != cudaSuccess) return cleanup(RICK_ERR_OOM);
+    if (h->batch) {
+        std::vector<float2> cw(nchan);
+        for (int ch = 0; ch < nchan; ++ch) {
+            const double dw = (p->nw > 1) ? (w_max[ch] - w_min[ch]) / p->nw : (w_max[ch] - w_min[ch]);
+            cw[ch] = make_float2((float)w_min[ch], (p->nw > 1) ? (float)(1.0 / dw) : 0.0f);
+        }
+        if (cudaMalloc(&h->chan_w, sizeof(float2) * nchan) != cudaSuccess) return cleanup(RICK_ERR_OOM);
+        if (cudaMalloc(&h->chan_off, sizeof(int64_t) * (nchan + 1)) != cudaSuccess) return cleanup(RICK_ERR_OOM);
+        if (cudaMalloc(&h->chan_sw, sizeof(double) * nchan) != cudaSuccess) return cleanup(RICK_ERR_OOM);
+        if (cudaMalloc(&h->b_off, sizeof(uint32_t) * (ntiles + 1)) != cudaSuccess) return cleanup(RICK_ERR_OOM);
+        if (cudaMemcpy(h->chan_w, cw.data(), sizeof(float2) * nchan, cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(RICK_ERR_CUDA);
+        h->cfg.chan_w = h->chan_w;
+        h->cfg.chan_off = h->chan_off;
+    }
+    if (cudaMalloc(&h->cursor, (size_t)(ntiles + 1) * sizeof(uint32_t)) != cudaSuccess) return cleanup(RICK_ERR_OOM);
     if (cudaMalloc(&h->block_sums, scan_block_sums_len(ntiles) * sizeof(uint32_t)) != cudaSuccess)
         return cleanup(RICK_ERR_OOM);
     if (cudaMalloc(&h->ctr, sizeof(Counters)) != cudaSuccess) return cleanup(RICK_ERR_OOM);
@@ -397,7 +447,7 @@ rick_status rick_create(const rick_params* p, rick_handle* out)
         if (cudaMemset(h->density, 0, (size_t)c.n * c.n * sizeof(uint32_t)) != cudaSuccess)
             return cleanup(RICK_ERR_CUDA);
     }
-    h->bytes_held = (size_t)c.n * 4 + (size_t)G * pb + (G < p->nw ? pb : 0) + (size_t)ntiles * 4 +
+    h->bytes_held = (size_t)c.n * 4 + (size_t)G * pb + (h->acc ? pb : 0) + (size_t)ntiles * 4 * (h->batch ? 2 : 1) +
                     scan_block_sums_len(ntiles) * 4 + sizeof(Counters) +
                     ((p->flags & RICK_UNIFORM_WEIGHT) ? (size_t)c.n * c.n * 4 : 0);
     if (cudaMemset(h->ctr, 0, sizeof(Counters)) != cudaSuccess) return cleanup(RICK_ERR_CUDA);
@@ -428,13 +478,18 @@ rick_status rick_create(const rick_params* p, rick_handle* out)
     cufftHandle plan;
     s = get_plan(h, G, &plan);
     if (s) return cleanup(s);
-    if (p->nw % G) {
-        s = get_plan(h, p->nw % G, &plan);
+    if (NW % G) {
+        s = get_plan(h, NW % G, &plan);
         if (s) return cleanup(s);
     }
     if (cudaDeviceSynchronize() != cudaSuccess) return cleanup(RICK_ERR_CUDA);
     *out = h;
     return RICK_OK;
+}
+
+rick_status rick_create(const rick_params* p, rick_handle* out)
+{
+    return create_impl(p, 1, nullptr, nullptr, out);
 }
 
 rick_status rick_destroy(rick_handle h)
@@ -459,6 +514,12 @@ rick_status rick_destroy(rick_handle h)
     cudaFree(h->fft_work);
     cudaFree(h->stage);
     cudaFree(h->img_dev);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    cudaFree(h->chan_w);
+    cudaFree(h->chan_off);
+    cudaFree(h->chan_sw);
+    cudaFree(h->b_off);
+    cudaFree(h->b_ent);
     if (h->pool) cudaMemPoolDestroy(h->pool);
     delete h;
     return RICK_OK;
@@ -488,6 +549,7 @@ rick_status rick_add_density(rick_handle h, const float* vis, const float* u, co
                              const float* weights, int64_t nvis)
 {
     if (!h) return RICK_ERR_ARG;
+    if (h->batch) return fail(h, RICK_ERR_STATE, "batched handle: use rick_image_batch");
     rick_status s = check_vis_args(h, vis, u, v, w, nvis);
     if (s) return s;
     if (!h->density) return fail(h, RICK_ERR_STATE, "uniform weighting is not enabled for this handle");
@@ -502,6 +564,7 @@ rick_status rick_grid(rick_handle h, const float* vis, const float* u, const flo
                       const float* weights, int64_t nvis)
 {
     if (!h) return RICK_ERR_ARG;
+    if (h->batch) return fail(h, RICK_ERR_STATE, "batched handle: use rick_image_batch");
     rick_status s = check_vis_args(h, vis, u, v, w, nvis);
     if (s) return s;
     if (nvis == 0) return RICK_OK;
@@ -537,7 +600,8 @@ rick_status rick_grid(rick_handle h, const float* vis, const float* u, const flo
     if (e == cudaSuccess) e = launch_count(c, u, v, w, weights, vis2, nvis, h->cursor, h->stream);
     if (e == cudaSuccess) e = launch_scan(h->cursor, ntiles, ch.off, h->cursor, h->block_sums, h->stream);
     if (e == cudaSuccess)
-        e = launch_scatter(c, u, v, w, weights, vis2, nvis, h->density, h->cursor, ch.ent, h->ctr, h->stream);
+        e = launch_scatter(c, u, v, w, weights, vis2, nvis, h->density, h->cursor, ch.ent, h->ctr, nullptr,
+                           h->stream);
     if (e != cudaSuccess) {
         cudaFreeAsync(ch.off, h->stream);
         cudaFreeAsync(ch.ent, h->stream);
@@ -552,6 +616,7 @@ rick_status rick_grid(rick_handle h, const float* vis, const float* u, const flo
 rick_status rick_grid_planes(rick_handle h, int32_t k0, int32_t nk, float* planes)
 {
     if (!h) return RICK_ERR_ARG;
+    if (h->batch) return fail(h, RICK_ERR_STATE, "batched handle: use rick_image_batch");
     if (k0 < 0 || nk < 0 || k0 + nk > h->p.nw) return fail(h, RICK_ERR_ARG, "plane range out of bounds");
     if (nk == 0) return RICK_OK;
     if (!planes) return fail(h, RICK_ERR_ARG, "planes is NULL");
@@ -561,6 +626,7 @@ rick_status rick_grid_planes(rick_handle h, int32_t k0, int32_t nk, float* plane
 rick_status rick_fft_and_stack(rick_handle h, float* image)
 {
     if (!h) return RICK_ERR_ARG;
+    if (h->batch) return fail(h, RICK_ERR_STATE, "batched handle: use rick_image_batch");
     if (!image) return fail(h, RICK_ERR_ARG, "image is NULL");
     const rick_params& p = h->p;
     const double dw = (p.nw > 1) ? (p.w_max - p.w_min) / p.nw : (p.w_max - p.w_min);
@@ -587,7 +653,7 @@ rick_status rick_fft_and_stack(rick_handle h, float* image)
         a.first = (k0 == 0);
         a.last = (k0 + nk >= p.nw);
         PhaseScope ss(h, kPhaseStack);
-        RICK_CU(h, launch_stack(a, h->planes, h->acc, h->taper, h->ctr, image, h->stream));
+        RICK_CU(h, launch_stack(a, h->planes, h->acc, h->taper, &h->ctr->sum_w, image, h->stream));
         count_launches(h, 1);
     }
     return RICK_OK;
@@ -597,6 +663,7 @@ rick_status rick_degrid(rick_handle h, const float* image_grad, const float* u, 
                         const float* weights, int64_t nvis, float* vis_grad)
 {
     if (!h) return RICK_ERR_ARG;
+    if (h->batch) return fail(h, RICK_ERR_STATE, "batched handle: the adjoint is single-channel");
     if (nvis < 0) return fail(h, RICK_ERR_ARG, "nvis must be >= 0");
     if (nvis > ((int64_t)1 << 30)) return fail(h, RICK_ERR_ARG, "at most 2^30 measurements per call");
     if (nvis > 0 && (!u || !v || !w || !vis_grad)) return fail(h, RICK_ERR_ARG, "u, v, w, vis_grad must not be NULL");
@@ -641,7 +708,7 @@ rick_status rick_degrid(rick_handle h, const float* image_grad, const float* u, 
         const int nk = (p.nw - k0 < h->G) ? p.nw - k0 : h->G;
         a.k0 = k0;
         a.nk = nk;
-        e = launch_spread(a, image_grad, h->taper, h->ctr, h->planes, h->stream);
+        e = launch_spread(a, image_grad, h->taper, &h->ctr->sum_w, h->planes, h->stream);
         if (e != cudaSuccess) {
             st = fail(h, RICK_ERR_CUDA, "k_spread: %s", cudaGetErrorString(e));
             break;
@@ -671,6 +738,7 @@ rick_status rick_image_host(rick_handle h, const float* vis_host, const float* u
                             const float* w_host, const float* weights_host, int64_t nvis, float* image_host)
 {
     if (!h) return RICK_ERR_ARG;
+    if (h->batch) return fail(h, RICK_ERR_STATE, "batched handle: use rick_image_batch");
     rick_status s = check_vis_args(h, vis_host, u_host, v_host, w_host, nvis);
     if (s) return s;
     if (!image_host) return fail(h, RICK_ERR_ARG, "image_host is NULL");
@@ -749,6 +817,247 @@ rick_status rick_get_timing(rick_handle h, rick_timing* out)
     out->stack_calls = h->timer.calls[kPhaseStack];
     out->degrid_calls = h->timer.calls[kPhaseDegrid];
     out->kernel_launches = h->timer.launches;
+    return RICK_OK;
+}
+
+rick_status rick_create_batch(const rick_params* p, int32_t nchan, const double* w_min, const double* w_max,
+                              rick_handle* out)
+{
+    if (!out || !w_min || !w_max || nchan < 1) return RICK_ERR_ARG;
+    return create_impl(p, nchan, w_min, w_max, out);
+}
+
+// One batch step: placement + counting sort over all channels, then per plane
+// group the gridder, one cuFFT batch and one stack per channel.  Everything it
+// enqueues is capturable (no host synchronisation, no allocation).
+static rick_status batch_body(rick_handle h, const float* vis, const float* u, const float* v, const float* w,
+                              const float* weights, int64_t m, float* images)
+{
+    const GridCfg& c = h->cfg;
+    const rick_params& p = h->p;
+    const int64_t ntiles = (int64_t)c.nw * c.ntp;
+    const float2* vis2 = reinterpret_cast<const float2*>(vis);
+    {
+        PhaseScope scope(h, kPhasePrep);
+        RICK_CU(h, cudaMemsetAsync(h->ctr, 0, sizeof(Counters), h->stream));
+        RICK_CU(h, cudaMemsetAsync(h->chan_sw, 0, sizeof(double) * h->nchan, h->stream));
+        RICK_CU(h, cudaMemsetAsync(h->cursor, 0, (size_t)ntiles * sizeof(uint32_t), h->stream));
+        RICK_CU(h, launch_count(c, u, v, w, weights, vis2, m, h->cursor, h->stream));
+        RICK_CU(h, launch_scan(h->cursor, ntiles, h->b_off, h->cursor, h->block_sums, h->stream));
+        RICK_CU(h, launch_scatter(c, u, v, w, weights, vis2, m, nullptr, h->cursor, h->b_ent, h->ctr, h->chan_sw,
+                                  h->stream));
+        count_launches(h, 5);
+    }
+    const size_t img_floats = (size_t)p.n * p.n * ((p.flags & RICK_REAL_IMAGE) ? 1 : 2);
+    const size_t nn = (size_t)p.n * p.n;
+    for (int k0 = 0; k0 < c.nw; k0 += h->G) {
+        const int nk = (c.nw - k0 < h->G) ? c.nw - k0 : h->G;
+        {
+            PhaseScope scope(h, kPhaseGrid);
+            ChunkList cl{};
+            cl.off[0] = h->b_off;
+            cl.ent[0] = h->b_ent;
+            cl.count = 1;
+            RICK_CU(h, launch_grid(c, cl, k0, nk, true, false, h->cursor, h->planes, h->stream));
+            count_launches(h, 2);
+        }
+        cufftHandle plan;
+        rick_status s = get_plan(h, nk, &plan);
+        if (s) return s;
+        {
+            PhaseScope fs(h, kPhaseFft);
+            RICK_FFT(h, cufftExecC2C(plan, reinterpret_cast<cufftComplex*>(h->planes),
+                                     reinterpret_cast<cufftComplex*>(h->planes), CUFFT_INVERSE));
+        }
+        PhaseScope ss(h, kPhaseStack);
+        for (int ch = k0 / c.nw_chan; ch < (k0 + nk) / c.nw_chan; ++ch) {
+            const double dw = (p.nw > 1) ? (h->chan_wmax[ch] - h->chan_wmin[ch]) / p.nw
+                                         : (h->chan_wmax[ch] - h->chan_wmin[ch]);
+            StackArgs a{};
+            a.n = p.n;
+            split(p.pixel_rad * p.pixel_rad, &a.dl2_hi, &a.dl2_lo);
+            split(h->chan_wmin[ch] + 0.5 * dw, &a.wb_hi, &a.wb_lo);
+            split(dw, &a.dw_hi, &a.dw_lo);
+            a.flags = p.flags;
+            a.k0 = 0;
+            a.nk = c.nw_chan;
+            a.first = 1;
+            a.last = 1;
+            const float2* pl = h->planes + (size_t)(ch * c.nw_chan - k0) * nn;
+            RICK_CU(h, launch_stack(a, pl, nullptr, h->taper, h->chan_sw + ch, images + (size_t)ch * img_floats,
+                                    h->stream));
+            count_launches(h, 1);
+        }
+    }
+    return RICK_OK;
+}
+
+rick_status rick_image_batch(rick_handle h, const float* vis, const float* u, const float* v, const float* w,
+                             const float* weights, const int64_t* chan_offsets, float* images, int32_t use_graph)
+{
+    if (!h) return RICK_ERR_ARG;
+    if (!h->batch) return fail(h, RICK_ERR_STATE, "not a batched handle (rick_create_batch)");
+    if (!chan_offsets || !images) return fail(h, RICK_ERR_ARG, "chan_offsets and images must not be NULL");
+    if (chan_offsets[0] != 0) return fail(h, RICK_ERR_ARG, "chan_offsets[0] must be 0");
+    for (int ch = 0; ch < h->nchan; ++ch)
+        if (chan_offsets[ch + 1] < chan_offsets[ch]) return fail(h, RICK_ERR_ARG, "chan_offsets must not decrease");
+    const int64_t m = chan_offsets[h->nchan];
+    if (m > ((int64_t)1 << 30)) return fail(h, RICK_ERR_ARG, "at most 2^30 measurements per batch");
+    if (m > 0 && (!vis || !u || !v || !w)) return fail(h, RICK_ERR_ARG, "vis, u, v, w must not be NULL");
+    const GridCfg& c = h->cfg;
+    bool stale = false;
+    // channel offsets on the device (outside any capture)
+    if (h->chan_off_host.size() != (size_t)h->nchan + 1 ||
+        memcmp(h->chan_off_host.data(), chan_offsets, sizeof(int64_t) * (h->nchan + 1)) != 0) {
+        h->chan_off_host.assign(chan_offsets, chan_offsets + h->nchan + 1);
+        RICK_CU(h, cudaMemcpyAsync(h->chan_off, h->chan_off_host.data(), sizeof(int64_t) * (h->nchan + 1),
+                                   cudaMemcpyHostToDevice, h->stream));
+        RICK_CU(h, cudaStreamSynchronize(h->stream));
+        stale = true;
+    }
+    const int64_t cap = entries_bound(c, m);
+    if (cap > h->b_cap) {
+        size_t fr = 0, tot = 0;
+        RICK_CU(h, cudaMemGetInfo(&fr, &tot));
+        if ((size_t)cap * sizeof(float4) + (64u << 20) > fr)
+            return fail(h, RICK_ERR_OOM, "batch of %lld measurements needs %zu bytes of entries", (long long)m,
+                        (size_t)cap * sizeof(float4));
+        RICK_CU(h, cudaStreamSynchronize(h->stream));
+        cudaFree(h->b_ent);
+        h->b_ent = nullptr;
+        h->bytes_held -= (size_t)h->b_cap * sizeof(float4);
+        h->b_cap = 0;
+        RICK_CU(h, cudaMalloc((void**)&h->b_ent, (size_t)cap * sizeof(float4)));
+        h->b_cap = cap;
+        h->bytes_held += (size_t)cap * sizeof(float4);
+        stale = true;
+    }
+    if (m == 0) {
+        const size_t img = (size_t)h->nchan * h->p.n * h->p.n * ((h->p.flags & RICK_REAL_IMAGE) ? 1 : 2);
+        RICK_CU(h, cudaMemsetAsync(images, 0, img * sizeof(float), h->stream));
+        return RICK_OK;
+    }
+    const void* key[7] = {vis, u, v, w, weights, images, (const void*)(intptr_t)m};
+    if (use_graph && h->stream == nullptr)
+        return fail(h, RICK_ERR_ARG, "graph mode needs a non-default stream (rick_set_stream)");
+    if (use_graph && h->graph && !stale && h->graph_m == m && memcmp(key, h->graph_key, sizeof(key)) == 0) {
+        RICK_CU(h, cudaGraphLaunch(h->graph, h->stream));
+        count_launches(h, 5 + 2 * ((c.nw + h->G - 1) / h->G) + h->nchan);
+        return RICK_OK;
+    }
+    if (!use_graph) return batch_body(h, vis, u, v, w, weights, m, images);
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    const bool timing = h->timer.on;
+    h->timer.on = false;  // events are not recorded inside the captured graph
+    RICK_CU(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    rick_status s = batch_body(h, vis, u, v, w, weights, m, images);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    h->timer.on = timing;
+    if (s) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess) return fail(h, RICK_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        return fail(h, RICK_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    }
+    memcpy(h->graph_key, key, sizeof(key));
+    h->graph_m = m;
+    RICK_CU(h, cudaGraphLaunch(h->graph, h->stream));
+    return RICK_OK;
+}
+
+rick_status rick_autotune_batch(const rick_params* p, int32_t nchan, const double* w_min, const double* w_max,
+                                const float* vis, const float* u, const float* v, const float* w,
+                                const float* weights, const int64_t* chan_offsets, int32_t* tile_out,
+                                int32_t* plane_group_out, double* ms_out)
+{
+    if (!p || !tile_out || !plane_group_out || !chan_offsets || nchan < 1) return RICK_ERR_ARG;
+    const int64_t m = chan_offsets[nchan];
+    char key[256];
+    snprintf(key, sizeof(key), "batch n=%d nw=%d nchan=%d S=%d kernel=%d flags=%u m_log2=%d", p->n, p->nw, nchan,
+             p->support, p->kernel, p->flags, m > 0 ? (int)std::log2((double)m) : 0);
+    const char* cache = getenv("RICK_AUTOTUNE_CACHE");
+    if (cache && *cache) {
+        FILE* f = fopen(cache, "r");
+        if (f) {
+            char line[512];
+            while (fgets(line, sizeof(line), f)) {
+                int t = 0, g = 0;
+                double ms = 0.0;
+                const size_t kl = strlen(key);
+                if (strncmp(line, key, kl) == 0 && line[kl] == '|' &&
+                    sscanf(line + kl + 1, "%d %d %lf", &t, &g, &ms) == 3) {
+                    *tile_out = t;
+                    *plane_group_out = g;
+                    if (ms_out) *ms_out = ms;
+                    fclose(f);
+                    return RICK_OK;
+                }
+            }
+            fclose(f);
+        }
+    }
+    const size_t img = (size_t)nchan * p->n * p->n * ((p->flags & RICK_REAL_IMAGE) ? 1 : 2) * sizeof(float);
+    float* images = nullptr;
+    if (cudaMalloc(&images, img) != cudaSuccess) return RICK_ERR_OOM;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        cudaFree(images);
+        return RICK_ERR_CUDA;
+    }
+    double best = 1e30;
+    int best_t = 0, best_g = 0;
+    const int tiles[3] = {16, 32, 64};
+    for (int ti = 0; ti < 3; ++ti) {
+        if (tiles[ti] < p->support) continue;
+        for (int half = 0; half < 2; ++half) {
+            rick_params q = *p;
+            q.tile = tiles[ti];
+            q.plane_group = half ? ((nchan / 2 > 0 ? nchan / 2 : 1) * p->nw) : 0;
+            if (half && nchan < 2) continue;
+            rick_handle h = nullptr;
+            if (create_impl(&q, nchan, w_min, w_max, &h) != RICK_OK) continue;
+            rick_set_stream(h, st);
+            float ms = 0.f;
+            bool ok = rick_image_batch(h, vis, u, v, w, weights, chan_offsets, images, 0) == RICK_OK &&
+                      cudaEventRecord(e0, st) == cudaSuccess &&
+                      rick_image_batch(h, vis, u, v, w, weights, chan_offsets, images, 0) == RICK_OK &&
+                      cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                      cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+            const int g = h->G;
+            rick_destroy(h);
+            if (ok && ms < best) {
+                best = ms;
+                best_t = tiles[ti];
+                best_g = g;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    cudaFree(images);
+    if (!best_t) return RICK_ERR_CUDA;
+    *tile_out = best_t;
+    *plane_group_out = best_g;
+    if (ms_out) *ms_out = best;
+    if (cache && *cache) {
+        FILE* f = fopen(cache, "a");
+        if (f) {
+            fprintf(f, "%s|%d %d %.4f\n", key, best_t, best_g, best);
+            fclose(f);
+        }
+    }
     return RICK_OK;
 }
 

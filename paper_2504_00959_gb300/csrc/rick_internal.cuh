@@ -22,7 +22,8 @@ constexpr int kScanTile = kScanBlock * kScanItems;
 
 // Everything a kernel needs to place a measurement, by value.
 struct GridCfg {
-    int n, nw, S, T, log2T, ntu;     // ntu: tiles per side = ceil(n / T)
+    int n, nw, S, T, log2T, ntu;     // nw: planes in total (channels x planes per channel)
+                                     // ntu: tiles per side = ceil(n / T)
     int64_t ntp;                     // tiles per plane = ntu * ntu
     float uvscale;                   // cells per wavelength, binary32
     float half_n, half_s;            // n/2, S/2
@@ -32,6 +33,12 @@ struct GridCfg {
     float kp;                        // Gaussian: 1/(2 sigma^2); KB: beta
     float two_over_s;                // 2 / S
     int uniform;                     // uniform weighting on
+    // batched imaging: nchan channels with nw_chan w-planes each, channel c
+    // owning planes c*nw_chan .. (c+1)*nw_chan-1 and measurements
+    // chan_off[c] .. chan_off[c+1]-1; chan_w[c] = (w_min, 1/dw) in binary32.
+    int nchan, nw_chan;
+    const float2* chan_w;
+    const int64_t* chan_off;
     // tap t of a measurement whose footprint starts at f = floor(p - S/2) + 1
     // is g(t + 1 - S/2 - d), d = frac(p - S/2); as a polynomial in z = 2d - 1:
     // g_t = sum_j coef[t][j] z^j (fitted once per handle, see k_fit_taps)
@@ -46,7 +53,7 @@ struct Place {
     float pu, pv;
 };
 
-__device__ __forceinline__ bool place(const GridCfg& c, float u, float v, float w, Place& p)
+__device__ __forceinline__ bool place(const GridCfg& c, float u, float v, float w, Place& p, int chan = 0)
 {
     if (!(isfinite(u) && isfinite(v) && isfinite(w))) return false;
     float pu = __fmaf_rn(u, c.uvscale, c.half_n);
@@ -56,11 +63,18 @@ __device__ __forceinline__ bool place(const GridCfg& c, float u, float v, float 
     if (!(au >= -1.0f && au <= c.lim && av >= -1.0f && av <= c.lim)) return false;
     p.fu = (int)au + 1;
     p.fv = (int)av + 1;
-    if (c.nw == 1) {
-        p.k = 0;
+    if (c.nw_chan == 1) {
+        p.k = chan;
     } else {
-        float fk = floorf(__fmul_rn(__fsub_rn(w, c.wmin), c.invdw));
-        p.k = (fk < 0.0f) ? 0 : ((fk > (float)(c.nw - 1)) ? c.nw - 1 : (int)fk);
+        float wmin = c.wmin, invdw = c.invdw;
+        if (c.nchan > 1) {
+            const float2 cw = __ldg(c.chan_w + chan);
+            wmin = cw.x;
+            invdw = cw.y;
+        }
+        float fk = floorf(__fmul_rn(__fsub_rn(w, wmin), invdw));
+        const int k = (fk < 0.0f) ? 0 : ((fk > (float)(c.nw_chan - 1)) ? c.nw_chan - 1 : (int)fk);
+        p.k = chan * c.nw_chan + k;
     }
     p.pu = pu;
     p.pv = pv;
@@ -108,6 +122,22 @@ __device__ __forceinline__ void eval_taps(const GridCfg& c, float p, int f, floa
     }
 }
 
+// Sum of the S taps of one axis (same Horner evaluation as eval_taps and the
+// gridder, tap by tap, so normalised taps sum to 1 to binary32 rounding).
+__device__ __forceinline__ float tap_sum(const GridCfg& c, float p, int f)
+{
+    const float d = __fsub_rn(__fsub_rn(p, c.half_s), (float)(f - 1));
+    const float z = __fmaf_rn(2.0f, d, -1.0f);
+    float s = 0.0f;
+    for (int t = 0; t < c.S; ++t) {
+        float a = c.coef[t][kPolyTerms - 1];
+#pragma unroll
+        for (int j = kPolyTerms - 2; j >= 0; --j) a = __fmaf_rn(a, z, c.coef[t][j]);
+        s += a;
+    }
+    return s;
+}
+
 // Whether a measurement with finite placement also has a finite weight and value.
 __device__ __forceinline__ bool finite_value(float wt, float2 vis)
 {
@@ -117,7 +147,8 @@ __device__ __forceinline__ bool finite_value(float wt, float2 vis)
 // One gridding pass: up to kMaxChunksPerPass sorted chunks.
 struct ChunkList {
     const uint32_t* off[kMaxChunksPerPass];  // [ntiles + 1] start offsets
-    const float4* ent[kMaxChunksPerPass];    // (pu, pv, re, im) entries
+    const float4* ent[kMaxChunksPerPass];    // (pu, pv, re, im) entries, re/im already
+                                             // multiplied by weight / (sum of u taps * sum of v taps)
     int count;
 };
 
@@ -136,11 +167,13 @@ cudaError_t launch_count(const GridCfg& c, const float* u, const float* v, const
                          cudaStream_t s);
 cudaError_t launch_scan(const uint32_t* counts, int64_t len, uint32_t* offsets, uint32_t* cursor,
                         uint32_t* block_sums, cudaStream_t s);
+// chan_sw: per-channel weight sums (NULL: ctr->sum_w, single channel)
 cudaError_t launch_scatter(const GridCfg& c, const float* u, const float* v, const float* w,
                            const float* wt, const float2* vis, int64_t m, const uint32_t* density,
-                           uint32_t* cursor, float4* entries, Counters* ctr, cudaStream_t s);
+                           uint32_t* cursor, float4* entries, Counters* ctr, double* chan_sw, cudaStream_t s);
+// heavy: scratch of 1 + nk * ntp uint32 (count + list of tiles with many entries)
 cudaError_t launch_grid(const GridCfg& c, const ChunkList& chunks, int k0, int nk, bool shift_sign,
-                        bool accumulate, const uint32_t* density, float2* planes, cudaStream_t s);
+                        bool accumulate, uint32_t* heavy, float2* planes, cudaStream_t s);
 cudaError_t launch_taper(const GridCfg& c, double kernel_param, float* taper, cudaStream_t s);
 // Fit the tap polynomials (coef: float[S][kPolyTerms]) and report the largest
 // binary32 evaluation error relative to the kernel's peak in *max_err.
@@ -154,10 +187,11 @@ struct StackArgs {
     int first, last;                 // first / last plane group
     unsigned flags;
 };
+// sum_w: the weight sum the image is normalised by (device)
 cudaError_t launch_stack(const StackArgs& a, const float2* planes, float2* acc, const float* taper,
-                         const Counters* ctr, void* image, cudaStream_t s);
+                         const double* sum_w, void* image, cudaStream_t s);
 
-cudaError_t launch_spread(const StackArgs& a, const void* rimg, const float* taper, const Counters* ctr,
+cudaError_t launch_spread(const StackArgs& a, const void* rimg, const float* taper, const double* sum_w,
                           float2* planes, cudaStream_t s);
 // adjoint: sort measurements by the tile of their first footprint cell
 // (no duplication), then gather each measurement's footprint of a plane group
@@ -228,5 +262,20 @@ struct rick_imager {
     size_t img_bytes;
     size_t bytes_held;
     rick::PhaseTimer timer;
+    // batched imaging (rick_create_batch): per-channel w-ranges and sums,
+    // persistent entry buffers, and the captured graph of one batch step
+    bool batch;
+    int nchan;
+    std::vector<double> chan_wmin, chan_wmax;
+    float2* chan_w;                  // device [nchan] (w_min, 1/dw) binary32
+    int64_t* chan_off;               // device [nchan + 1]
+    double* chan_sw;                 // device [nchan] weight sums
+    std::vector<int64_t> chan_off_host;
+    uint32_t* b_off;                 // device [ntiles + 1]
+    float4* b_ent;                   // device entries
+    int64_t b_cap;
+    cudaGraphExec_t graph;
+    const void* graph_key[7];
+    int64_t graph_m;
     char last_error[512];
 };

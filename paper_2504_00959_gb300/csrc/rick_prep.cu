@@ -5,10 +5,12 @@
 //   k_count    entries per tile (a footprint straddling tiles is listed in
 //              every tile it touches)
 //   k_scan_*   exclusive prefix sum of the counts -> tile start offsets
-//   k_scatter  one 16-byte entry (pu, pv, wt*Re V, wt*Im V) per (measurement,
-//              tile), written at its tile's cursor; weight sum and counters.
-// All are grid-stride kernels sized to the SM count; reads of the inputs are
-// coalesced, writes of entries are scattered 16-byte stores.
+//   k_scatter  one 16-byte entry (pu, pv, s*Re V, s*Im V), s = weight / (sum of
+//              u taps * sum of v taps), per (measurement, tile), written at
+//              its tile's cursor; weight sum and counters.
+// Grids are sized to the SM count; each block takes a contiguous range of the
+// measurements (split at channel boundaries in batched imaging) and reads it
+// coalesced; writes of entries are scattered 16-byte stores.
 #include "rick_internal.cuh"
 
 namespace rick {
@@ -46,46 +48,76 @@ struct Inputs {
     const float2* vis;
 };
 
-__device__ __forceinline__ bool load_and_place(const GridCfg& c, const Inputs& in, int64_t i, Place& p,
+__device__ __forceinline__ bool load_and_place(const GridCfg& c, const Inputs& in, int64_t i, int chan, Place& p,
                                                float& wi, float2& V)
 {
     wi = in.wt ? __ldg(in.wt + i) : 1.0f;
     V = __ldg(in.vis + i);
-    return place(c, __ldg(in.u + i), __ldg(in.v + i), __ldg(in.w + i), p) && finite_value(wi, V);
+    return place(c, __ldg(in.u + i), __ldg(in.v + i), __ldg(in.w + i), p, chan) && finite_value(wi, V);
+}
+
+// Each block takes one contiguous range of the m measurements and walks it
+// channel by channel (one segment when there is a single channel): body(chan,
+// i0, i1) is called for every non-empty segment, by all threads of the block.
+template <typename Body>
+__device__ __forceinline__ void for_each_segment(const GridCfg& c, int64_t m, Body&& body)
+{
+    const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+    int64_t r0 = (int64_t)blockIdx.x * per;
+    const int64_t r1 = r0 + per < m ? r0 + per : m;
+    if (r0 >= r1) return;
+    int chan = 0;
+    if (c.nchan > 1) {
+        int lo = 0, hi = c.nchan - 1;  // last channel whose first measurement is <= r0
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(c.chan_off + mid) <= r0) lo = mid; else hi = mid - 1;
+        }
+        chan = lo;
+    }
+    while (r0 < r1) {
+        const int64_t end = (c.nchan > 1) ? min(r1, (int64_t)__ldg(c.chan_off + chan + 1)) : r1;
+        if (end > r0) body(chan, r0, end);
+        r0 = end > r0 ? end : r0;
+        ++chan;
+        if (chan >= c.nchan && r0 < r1) break;  // measurements past the last channel: none by construction
+    }
 }
 
 __global__ void __launch_bounds__(kPrepThreads) k_density(GridCfg c, Inputs in, int64_t m,
                                                           uint32_t* __restrict__ density)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        Place p;
-        float wi;
-        float2 V;
-        if (!load_and_place(c, in, i, p, wi, V)) continue;
-        atomicAdd(density + (int64_t)nearest_cell(c, p.pv) * c.n + nearest_cell(c, p.pu), 1u);
-    }
+    for_each_segment(c, m, [&](int chan, int64_t i0, int64_t i1) {
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            Place p;
+            float wi;
+            float2 V;
+            if (!load_and_place(c, in, i, chan, p, wi, V)) continue;
+            atomicAdd(density + (int64_t)nearest_cell(c, p.pv) * c.n + nearest_cell(c, p.pu), 1u);
+        }
+    });
 }
 
 __global__ void __launch_bounds__(kPrepThreads) k_count(GridCfg c, Inputs in, int64_t m,
                                                         uint32_t* __restrict__ counts)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        Place p;
-        float wi;
-        float2 V;
-        if (!load_and_place(c, in, i, p, wi, V)) continue;
-        const int tu0 = p.fu >> c.log2T, tu1 = (p.fu + c.S - 1) >> c.log2T;
-        const int tv0 = p.fv >> c.log2T, tv1 = (p.fv + c.S - 1) >> c.log2T;
-        uint32_t* base = counts + (int64_t)p.k * c.ntp;
-        atomicAdd(base + tv0 * c.ntu + tu0, 1u);
-        if (tu1 != tu0) atomicAdd(base + tv0 * c.ntu + tu1, 1u);
-        if (tv1 != tv0) {
-            atomicAdd(base + tv1 * c.ntu + tu0, 1u);
-            if (tu1 != tu0) atomicAdd(base + tv1 * c.ntu + tu1, 1u);
+    for_each_segment(c, m, [&](int chan, int64_t i0, int64_t i1) {
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            Place p;
+            float wi;
+            float2 V;
+            if (!load_and_place(c, in, i, chan, p, wi, V)) continue;
+            const int tu0 = p.fu >> c.log2T, tu1 = (p.fu + c.S - 1) >> c.log2T;
+            const int tv0 = p.fv >> c.log2T, tv1 = (p.fv + c.S - 1) >> c.log2T;
+            uint32_t* base = counts + (int64_t)p.k * c.ntp;
+            atomicAdd(base + tv0 * c.ntu + tu0, 1u);
+            if (tu1 != tu0) atomicAdd(base + tv0 * c.ntu + tu1, 1u);
+            if (tv1 != tv0) {
+                atomicAdd(base + tv1 * c.ntu + tu0, 1u);
+                if (tu1 != tu0) atomicAdd(base + tv1 * c.ntu + tu1, 1u);
+            }
         }
-    }
+    });
 }
 
 template <typename T>
@@ -95,72 +127,91 @@ __device__ __forceinline__ T warp_sum(T x)
     return x;
 }
 
+// Sum of one float over the block (all threads call it); result valid in thread 0.
+__device__ __forceinline__ float block_sum(float x)
+{
+    __shared__ float s[kPrepThreads / 32];
+    x = warp_sum(x);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) s[wid] = x;
+    __syncthreads();
+    float t = 0.0f;
+    if (threadIdx.x == 0)
+        for (int j = 0; j < kPrepThreads / 32; ++j) t += s[j];
+    return t;
+}
+
+// chan_sw[chan] accumulates the weight sum of each channel (one entry when
+// there is a single channel).
 __global__ void __launch_bounds__(kPrepThreads) k_scatter(GridCfg c, Inputs in, int64_t m,
                                                           const uint32_t* __restrict__ density,
                                                           uint32_t* __restrict__ cursor,
-                                                          float4* __restrict__ entries, Counters* ctr)
+                                                          float4* __restrict__ entries, Counters* ctr,
+                                                          double* __restrict__ chan_sw)
 {
-    float sw = 0.0f;
     unsigned gridded = 0, dropped = 0, nent = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        Place p;
-        float wi;
-        float2 V;
-        if (!load_and_place(c, in, i, p, wi, V)) {
-            ++dropped;
-            continue;
-        }
-        if (c.uniform) {
-            uint32_t cnt = __ldg(density + (int64_t)nearest_cell(c, p.pv) * c.n + nearest_cell(c, p.pu));
-            wi = wi / (float)cnt;
-        }
-        const float4 rec = make_float4(p.pu, p.pv, wi * V.x, wi * V.y);
-        sw += wi;
-        ++gridded;
-        const int tu0 = p.fu >> c.log2T, tu1 = (p.fu + c.S - 1) >> c.log2T;
-        const int tv0 = p.fv >> c.log2T, tv1 = (p.fv + c.S - 1) >> c.log2T;
-        uint32_t* base = cursor + (int64_t)p.k * c.ntp;
-        entries[atomicAdd(base + tv0 * c.ntu + tu0, 1u)] = rec;
-        ++nent;
-        if (tu1 != tu0) {
-            entries[atomicAdd(base + tv0 * c.ntu + tu1, 1u)] = rec;
-            ++nent;
-        }
-        if (tv1 != tv0) {
-            entries[atomicAdd(base + tv1 * c.ntu + tu0, 1u)] = rec;
+    for_each_segment(c, m, [&](int chan, int64_t i0, int64_t i1) {
+        float sw = 0.0f;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            Place p;
+            float wi;
+            float2 V;
+            if (!load_and_place(c, in, i, chan, p, wi, V)) {
+                ++dropped;
+                continue;
+            }
+            if (c.uniform) {
+                uint32_t cnt = __ldg(density + (int64_t)nearest_cell(c, p.pv) * c.n + nearest_cell(c, p.pu));
+                wi = wi / (float)cnt;
+            }
+            // the gridder reads the visibility already weighted and divided by the
+            // two tap sums (normalised taps), once per measurement here instead of
+            // once per (measurement, tile) entry there
+            const float scale = wi / (tap_sum(c, p.pu, p.fu) * tap_sum(c, p.pv, p.fv));
+            const float4 rec = make_float4(p.pu, p.pv, scale * V.x, scale * V.y);
+            sw += wi;
+            ++gridded;
+            const int tu0 = p.fu >> c.log2T, tu1 = (p.fu + c.S - 1) >> c.log2T;
+            const int tv0 = p.fv >> c.log2T, tv1 = (p.fv + c.S - 1) >> c.log2T;
+            uint32_t* base = cursor + (int64_t)p.k * c.ntp;
+            entries[atomicAdd(base + tv0 * c.ntu + tu0, 1u)] = rec;
             ++nent;
             if (tu1 != tu0) {
-                entries[atomicAdd(base + tv1 * c.ntu + tu1, 1u)] = rec;
+                entries[atomicAdd(base + tv0 * c.ntu + tu1, 1u)] = rec;
                 ++nent;
             }
+            if (tv1 != tv0) {
+                entries[atomicAdd(base + tv1 * c.ntu + tu0, 1u)] = rec;
+                ++nent;
+                if (tu1 != tu0) {
+                    entries[atomicAdd(base + tv1 * c.ntu + tu1, 1u)] = rec;
+                    ++nent;
+                }
+            }
         }
-    }
-    // block reduction of the counters, one set of atomics per block
-    __shared__ float s_sw[kPrepThreads / 32];
+        const float tot = block_sum(sw);
+        if (threadIdx.x == 0 && tot != 0.0f) atomicAdd(chan_sw + chan, (double)tot);
+    });
+    // counters: one set of atomics per block
     __shared__ unsigned s_g[kPrepThreads / 32], s_d[kPrepThreads / 32], s_e[kPrepThreads / 32];
-    sw = warp_sum(sw);
     gridded = warp_sum(gridded);
     dropped = warp_sum(dropped);
     nent = warp_sum(nent);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
-        s_sw[wid] = sw;
         s_g[wid] = gridded;
         s_d[wid] = dropped;
         s_e[wid] = nent;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float a = 0.0f;
         unsigned long long g = 0, d = 0, e = 0;
         for (int j = 0; j < kPrepThreads / 32; ++j) {
-            a += s_sw[j];
             g += s_g[j];
             d += s_d[j];
             e += s_e[j];
         }
-        atomicAdd(&ctr->sum_w, (double)a);
         if (g) atomicAdd(&ctr->gridded, g);
         if (d) atomicAdd(&ctr->dropped, d);
         if (e) atomicAdd(&ctr->entries, e);
@@ -173,7 +224,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_scatter(GridCfg c, Inputs in, 
 __device__ __forceinline__ bool place_coords(const GridCfg& c, const Inputs& in, int64_t i, Place& p, float& wi)
 {
     wi = in.wt ? __ldg(in.wt + i) : 1.0f;
-    return place(c, __ldg(in.u + i), __ldg(in.v + i), __ldg(in.w + i), p) && isfinite(wi);
+    return place(c, __ldg(in.u + i), __ldg(in.v + i), __ldg(in.w + i), p, 0) && isfinite(wi);
 }
 
 __device__ __forceinline__ int64_t primary_tile(const GridCfg& c, const Place& p)
@@ -425,11 +476,11 @@ cudaError_t launch_scan(const uint32_t* counts, int64_t len, uint32_t* offsets, 
 
 cudaError_t launch_scatter(const GridCfg& c, const float* u, const float* v, const float* w,
                            const float* wt, const float2* vis, int64_t m, const uint32_t* density,
-                           uint32_t* cursor, float4* entries, Counters* ctr, cudaStream_t s)
+                           uint32_t* cursor, float4* entries, Counters* ctr, double* chan_sw, cudaStream_t s)
 {
     if (m <= 0) return cudaSuccess;
     k_scatter<<<prep_blocks(m), kPrepThreads, 0, s>>>(c, Inputs{u, v, w, wt, vis}, m, density, cursor,
-                                                      entries, ctr);
+                                                      entries, ctr, chan_sw ? chan_sw : &ctr->sum_w);
     return cudaGetLastError();
 }
 

@@ -86,7 +86,7 @@ __device__ __forceinline__ PixelScreen pixel_screen(const StackArgs& a, int x, i
 __global__ void __launch_bounds__(kStackThreads) k_stack(StackArgs a, const float2* __restrict__ planes,
                                                          float2* __restrict__ acc,
                                                          const float* __restrict__ taper,
-                                                         const Counters* __restrict__ ctr, void* image)
+                                                         const double* __restrict__ sum_w, void* image)
 {
     const int halfn = a.n >> 1;
     const int64_t idx = blockIdx.x * (int64_t)kStackThreads + threadIdx.x;
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kStackThreads) k_stack(StackArgs a, const floa
         *reinterpret_cast<float4*>(acc + pix) = make_float4(a0.x, a0.y, a1.x, a1.y);
         return;
     }
-    const double sw = ctr->sum_w;
+    const double sw = *sum_w;
     const float inv_sw = (sw != 0.0) ? (float)(1.0 / sw) : 0.0f;
     float f0 = inv_sw, f1 = inv_sw;
     if (a.flags & RICK_GRID_CORRECT) {
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kStackThreads) k_stack(StackArgs a, const floa
 // R = r / sum_w / taper(x) taper(y) * n  (per flags), ready for a forward FFT.
 __global__ void __launch_bounds__(kStackThreads) k_spread(StackArgs a, const void* __restrict__ rimg,
                                                           const float* __restrict__ taper,
-                                                          const Counters* __restrict__ ctr,
+                                                          const double* __restrict__ sum_w,
                                                           float2* __restrict__ planes)
 {
     const int halfn = a.n >> 1;
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kStackThreads) k_spread(StackArgs a, const voi
         r0 = make_float2(rr.x, rr.y);
         r1 = make_float2(rr.z, rr.w);
     }
-    const double sw = ctr->sum_w;
+    const double sw = *sum_w;
     const float inv_sw = (sw != 0.0) ? (float)(1.0 / sw) : 0.0f;
     float f0 = inv_sw, f1 = inv_sw;
     if (a.flags & RICK_GRID_CORRECT) {
@@ -227,23 +227,23 @@ __global__ void __launch_bounds__(kStackThreads) k_spread(StackArgs a, const voi
 
 }  // namespace
 
-cudaError_t launch_spread(const StackArgs& a, const void* rimg, const float* taper, const Counters* ctr,
+cudaError_t launch_spread(const StackArgs& a, const void* rimg, const float* taper, const double* sum_w,
                           float2* planes, cudaStream_t s)
 {
     const int64_t threads = (int64_t)a.n * (a.n / 2);
     const int64_t blocks = (threads + kStackThreads - 1) / kStackThreads;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_spread<<<(unsigned)blocks, kStackThreads, 0, s>>>(a, rimg, taper, ctr, planes);
+    k_spread<<<(unsigned)blocks, kStackThreads, 0, s>>>(a, rimg, taper, sum_w, planes);
     return cudaGetLastError();
 }
 
 cudaError_t launch_stack(const StackArgs& a, const float2* planes, float2* acc, const float* taper,
-                         const Counters* ctr, void* image, cudaStream_t s)
+                         const double* sum_w, void* image, cudaStream_t s)
 {
     const int64_t threads = (int64_t)a.n * (a.n / 2);
     const int64_t blocks = (threads + kStackThreads - 1) / kStackThreads;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    k_stack<<<(unsigned)blocks, kStackThreads, 0, s>>>(a, planes, acc, taper, ctr, image);
+    k_stack<<<(unsigned)blocks, kStackThreads, 0, s>>>(a, planes, acc, taper, sum_w, image);
     return cudaGetLastError();
 }
 

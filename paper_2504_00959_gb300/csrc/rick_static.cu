@@ -88,14 +88,14 @@ extern "C" rick_status rick_grid_planes_static(const rick_params* p, const float
     }
     cudaStream_t stream = (cudaStream_t)cuda_stream;
 
-    // scratch layout: counters | coefficients | cursor | offsets | scan sums | density | entries
+    // scratch layout: counters | coefficients | cursor (+1 word) | offsets | scan sums | density | entries
     const int64_t ntiles = (int64_t)c.nw * c.ntp;
     const int64_t cap = nvis * (c.S > 1 ? 4 : 1);
     const size_t o_ctr = 0;
     const size_t o_coef = o_ctr + align256(sizeof(Counters));
     const size_t o_err = o_coef + align256(sizeof(float) * kMaxSupport * kPolyTerms);
     const size_t o_cursor = o_err + align256(sizeof(double) * kMaxSupport);
-    const size_t o_off = o_cursor + align256((size_t)ntiles * sizeof(uint32_t));
+    const size_t o_off = o_cursor + align256((size_t)(ntiles + 1) * sizeof(uint32_t));
     const size_t o_sums = o_off + align256((size_t)(ntiles + 1) * sizeof(uint32_t));
     const size_t o_dens = o_sums + align256(scan_block_sums_len(ntiles) * sizeof(uint32_t));
     const size_t dens_bytes = c.uniform ? (size_t)c.n * c.n * sizeof(uint32_t) : 0;
@@ -173,13 +173,14 @@ extern "C" rick_status rick_grid_planes_static(const rick_params* p, const float
     if (e == cudaSuccess && density) e = launch_density(c, u, v, w, weights, vis2, nvis, density, stream);
     if (e == cudaSuccess) e = launch_count(c, u, v, w, weights, vis2, nvis, cursor, stream);
     if (e == cudaSuccess) e = launch_scan(cursor, ntiles, off, cursor, sums, stream);
-    if (e == cudaSuccess) e = launch_scatter(c, u, v, w, weights, vis2, nvis, density, cursor, ent, ctr, stream);
+    if (e == cudaSuccess) e = launch_scatter(c, u, v, w, weights, vis2, nvis, density, cursor, ent, ctr, nullptr, stream);
     if (e == cudaSuccess) {
         ChunkList cl{};
         cl.off[0] = off;
         cl.ent[0] = ent;
         cl.count = 1;
-        e = launch_grid(c, cl, 0, c.nw, false, false, density, reinterpret_cast<float2*>(planes), stream);
+        // the scatter cursors are free again: they hold the gridder's heavy-tile list
+        e = launch_grid(c, cl, 0, c.nw, false, false, cursor, reinterpret_cast<float2*>(planes), stream);
     }
     if (e != cudaSuccess) {
         set_msg(err, err_len, "rick_grid_planes_static launch: %s", cudaGetErrorString(e));

@@ -217,6 +217,92 @@ def config2(device="cpu", m=10_000_000, n=4096, nw=32, seed=BASE_SEED + 2):
                                   -30.0, seed, device=device)
 
 
+def config3(device="cpu", m=200_000_000, n=16384, nw=128, fov_deg=5.0, support=8, seed=BASE_SEED + 3,
+            n_ant=512, diameter_m=60_000.0, hours=8.0, dt_s=2.0, freq_hz=1.4e9, dec_deg=-45.0,
+            flags=FLAG_CORRECT | FLAG_REAL | FLAG_UNIFORM, batch=50_000_000):
+    """SKA-like scale: 16384^2 grid over a 5 degree field (du = 11.46 wavelengths),
+    128 w-planes, 2e8 in-grid rows of an Earth-rotation synthesis of 512
+    antennas in a 60 km disk over 8 h at dec -45, 1.4 GHz (rows whose
+    footprint would leave the grid are re-drawn; the integration step is 2 s
+    so that enough in-grid rows exist), Kaiser-Bessel support 8 (beta 18.72),
+    uniform weighting.  Visibilities: N(0,1) + i N(0,1) plus a unit source at
+    the phase centre."""
+    pixel_rad = math.radians(fov_deg) / n
+    du = 1.0 / (n * pixel_rad)
+    lim = (n / 2 - support / 2 - 1) * du
+    us, vs, ws = [], [], []
+    kept, it = 0, 0
+    while kept < m:
+        Lx, Ly, Lz, H, dec = earth_rotation_rows(n_ant, diameter_m, hours, dt_s, dec_deg, -30.0, batch,
+                                                 seed * 1000 + it, device)
+        u, v, w = rows_to_uvw(Lx, Ly, Lz, H, dec, freq_hz)
+        del Lx, Ly, Lz, H
+        ok = (u.abs() <= lim) & (v.abs() <= lim)
+        take = min(int(ok.sum()), m - kept)
+        idx = torch.nonzero(ok).flatten()[:take]
+        us.append(u[idx].to(torch.float32))
+        vs.append(v[idx].to(torch.float32))
+        ws.append(w[idx].to(torch.float32))
+        kept += take
+        it += 1
+        del u, v, w, ok, idx
+    u = torch.cat(us)
+    v = torch.cat(vs)
+    w = torch.cat(ws)
+    del us, vs, ws
+    gen = _gen(seed + 7)
+    vis = torch.empty(m, dtype=torch.complex64, device=u.device)
+    step = 1 << 24
+    for s0 in range(0, m, step):
+        e0 = min(m, s0 + step)
+        vis[s0:e0] = (complex_noise(e0 - s0, 1.0, gen) + 1.0).to(u.device)
+    params = make_params(n, nw, pixel_rad, float(w.min()), float(w.max()), KERNEL_KB, support, 0.0, flags)
+    return dict(params=params, u=u, v=v, w=w, wt=torch.ones(m, dtype=torch.float32, device=u.device), vis=vis)
+
+
+def channels_problem(nchan=64, n=2048, nw=16, f_lo=0.95e9, f_hi=1.75e9, m_lo=1_000_000, m_hi=20_000_000,
+                     n_ant=256, diameter_m=20_000.0, hours=6.0, dt_s=10.0, dec_deg=-30.0, support=7,
+                     kernel=KERNEL_KB, seed=BASE_SEED + 4, flags=FLAG_CORRECT | FLAG_REAL, device="cpu",
+                     lat_deg=-30.0):
+    """Multi-channel problem: nchan frequencies f_c = f_lo + c (f_hi - f_lo)/(nchan-1),
+    each with floor(exp(U(ln m_lo, ln m_hi))) rows of the same Earth-rotation
+    track (a simulated flagging of uneven depth), its own w-range, and a uv
+    cell fixed for all channels by the longest |u|, |v| at f_hi placed at
+    0.45 n cells.  Visibilities are N(0,1) + i N(0,1) plus a unit source at
+    the phase centre.  The 64-channel, 2048^2, 16-plane configuration is the
+    default.  Returns params, channel (w_min, w_max) ranges, offsets and the
+    concatenated float32 / complex64 tensors on ``device``."""
+    gen = _gen(seed)
+    lnm = torch.empty(nchan, dtype=torch.float64).uniform_(math.log(m_lo), math.log(m_hi), generator=gen)
+    counts = [int(math.floor(math.exp(float(x)))) for x in lnm]
+    freqs = [f_lo + c * (f_hi - f_lo) / max(nchan - 1, 1) for c in range(nchan)]
+    parts = []
+    umax = 0.0
+    for c in range(nchan):
+        Lx, Ly, Lz, H, dec = earth_rotation_rows(n_ant, diameter_m, hours, dt_s, dec_deg, lat_deg, counts[c],
+                                                 seed * 1000 + c, device)
+        u, v, w = rows_to_uvw(Lx, Ly, Lz, H, dec, freqs[c])
+        del Lx, Ly, Lz, H
+        if counts[c] > 0:
+            umax = max(umax, float(torch.maximum(u.abs().max(), v.abs().max())) * f_hi / freqs[c])
+        parts.append((u.to(torch.float32), v.to(torch.float32), w.to(torch.float32)))
+    du = umax / (0.45 * n)
+    pixel_rad = 1.0 / (n * du)
+    u = torch.cat([p[0] for p in parts])
+    v = torch.cat([p[1] for p in parts])
+    w = torch.cat([p[2] for p in parts])
+    ranges = [(float(p[2].min()), float(p[2].max())) if p[2].numel() else (-1.0, 1.0) for p in parts]
+    ranges = [(a, b) if b > a else (a - 1.0, a + 1.0) for a, b in ranges]
+    m = u.numel()
+    vis = (complex_noise(m, 1.0, gen) + 1.0).to(torch.complex64).to(u.device)
+    offsets = [0]
+    for cnt in counts:
+        offsets.append(offsets[-1] + cnt)
+    params = make_params(n, nw, pixel_rad, 0.0, 1.0, kernel, support, 0.0, flags)
+    return dict(params=params, ranges=ranges, offsets=offsets, freqs=freqs, u=u, v=v, w=w,
+                wt=torch.ones(m, dtype=torch.float32, device=u.device), vis=vis)
+
+
 def to_numpy(prob):
     """The same problem as numpy arrays on the host (for the oracle)."""
     return dict(params=dict(prob["params"]),

@@ -1,0 +1,124 @@
+"""Batched multi-channel imaging on the GPU: each channel's image equals the
+one a single-channel imager makes of that channel alone (FP32 reordering
+only: 1e-6 of the peak, uncorrected), equals the FP64 oracle (1e-4), is the
+same whether the step runs directly or as a replayed CUDA graph, and the
+autotuner returns a valid, cached configuration."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+CORRECT, REAL = synth.FLAG_CORRECT, synth.FLAG_REAL
+
+
+@pytest.fixture(scope="module")
+def rick():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_00959_gb300 import build
+    build.build()
+    import paper_2504_00959_gb300 as r
+    r.load()
+    return r
+
+
+@pytest.fixture(scope="module")
+def chans():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    prob = synth.channels_problem(nchan=6, n=256, nw=4, m_lo=2_000, m_hi=60_000, device="cuda", seed=77)
+    # an empty channel and a single-measurement channel at the end
+    u, v, w, wt, vis = (prob[k] for k in ("u", "v", "w", "wt", "vis"))
+    prob["offsets"] = prob["offsets"] + [prob["offsets"][-1], prob["offsets"][-1] + 1]
+    for k, extra in (("u", u[:1]), ("v", v[:1]), ("w", w[:1]), ("wt", wt[:1]), ("vis", vis[:1])):
+        prob[k] = torch.cat([prob[k], extra])
+    prob["ranges"] = prob["ranges"] + [(-1.0, 1.0), (float(w[0]) - 5.0, float(w[0]) + 5.0)]
+    return prob
+
+
+def _single(rick, prob, c, flags):
+    a, b = prob["offsets"][c], prob["offsets"][c + 1]
+    lo, hi = prob["ranges"][c]
+    im = rick.Imager(dict(prob["params"], flags=flags, w_min=lo, w_max=hi))
+    im.grid(prob["vis"][a:b], prob["u"][a:b], prob["v"][a:b], prob["w"][a:b], prob["wt"][a:b])
+    img = im.image()
+    torch.cuda.synchronize()
+    im.close()
+    return img
+
+
+@pytest.mark.parametrize("flags", [REAL, CORRECT | REAL])
+def test_batch_equals_single_channel_imaging(rick, chans, flags):
+    prob = chans
+    bi = rick.BatchImager(dict(prob["params"], flags=flags), prob["ranges"])
+    imgs = bi.images(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"], prob["offsets"])
+    torch.cuda.synchronize()
+    st = bi.stats()
+    bi.close()
+    assert st["n_gridded"] + st["n_dropped"] == prob["u"].numel()
+    n = prob["params"]["n"]
+    x = torch.arange(n, dtype=torch.float64)
+    for c in range(len(prob["ranges"])):
+        ref = _single(rick, prob, c, flags)
+        diff = (imgs[c] - ref).abs().double()
+        scale = ref.abs().max().item()
+        if c == len(prob["ranges"]) - 2:  # the empty channel images to zero
+            assert torch.all(imgs[c] == 0)
+            continue
+        if flags & CORRECT:  # compare before the taper division (see test_gpu_parity)
+            import oracle
+            q = prob["params"]
+            t = torch.from_numpy(oracle.taper(n, q["kernel"], q["support"], 0.0)).to(diff.device)
+            cc = torch.outer(t, t)
+            assert (diff * cc).max().item() <= 1e-6 * (ref.abs().double() * cc).max().item()
+        else:
+            assert diff.max().item() <= 1e-6 * scale, (c, diff.max().item(), scale)
+    del x
+
+
+def test_batch_channel_matches_oracle(rick, oracle_mod, chans):
+    prob = chans
+    bi = rick.BatchImager(dict(prob["params"], flags=REAL), prob["ranges"])
+    imgs = bi.images(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"], prob["offsets"]).cpu().numpy()
+    bi.close()
+    c = 2
+    a, b = prob["offsets"][c], prob["offsets"][c + 1]
+    lo, hi = prob["ranges"][c]
+    params = dict(prob["params"], w_min=lo, w_max=hi)
+    sl = {k: prob[k][a:b].cpu().numpy() for k in ("u", "v", "w", "wt", "vis")}
+    ref, _, _ = oracle_mod.dirty_image(params, sl["u"], sl["v"], sl["w"], sl["wt"], sl["vis"], flags=0)
+    assert np.max(np.abs(imgs[c] - ref.real)) <= 1e-4 * np.max(np.abs(ref.real))
+
+
+def test_batch_graph_replay_equals_direct(rick, chans):
+    prob = chans
+    bi = rick.BatchImager(dict(prob["params"], flags=REAL), prob["ranges"])
+    direct = bi.images(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"], prob["offsets"]).clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    out = torch.empty_like(direct)
+    with torch.cuda.stream(s):
+        for _ in range(3):  # capture, then replay twice
+            bi.images(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"], prob["offsets"], out=out,
+                      use_graph=True)
+    torch.cuda.synchronize()
+    bi.close()
+    assert (out - direct).abs().max().item() <= 1e-6 * direct.abs().max().item()
+
+
+def test_autotune_batch_and_cache(rick, chans, tmp_path, monkeypatch):
+    prob = chans
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("RICK_AUTOTUNE_CACHE", str(cache))
+    t, g, ms = rick.autotune_batch(dict(prob["params"], flags=REAL), prob["ranges"], prob["vis"], prob["u"],
+                                   prob["v"], prob["w"], prob["wt"], prob["offsets"])
+    nw = prob["params"]["nw"]
+    assert t in (16, 32, 64) and t >= prob["params"]["support"]
+    assert g % nw == 0 and g > 0 and ms > 0
+    assert cache.exists() and str(t) in cache.read_text()
+    t2, g2, ms2 = rick.autotune_batch(dict(prob["params"], flags=REAL), prob["ranges"], prob["vis"], prob["u"],
+                                      prob["v"], prob["w"], prob["wt"], prob["offsets"])
+    assert (t2, g2) == (t, g) and abs(ms2 - ms) < 1e-3

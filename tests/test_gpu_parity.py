@@ -261,6 +261,22 @@ def test_hot_tile(rick, oracle_mod):
     _compare(rick, oracle_mod, dict(params=prob["params"], u=u, v=v, w=w, wt=wt, vis=vis), CORRECT | REAL)
 
 
+def test_hot_tile_in_chunks(rick, oracle_mod):
+    """A tile with ~2e4 entries on a grid large enough for the chunk list:
+    gridded as chunks by separate warps that add into the plane."""
+    n = 512
+    prob = synth.disk_problem(n, 2, 20000, KB, 7, 3.0, 50.0, 13)
+    du = 1 / (n * prob["params"]["pixel_rad"])
+    g = torch.Generator().manual_seed(6)
+    hot = 20000
+    u = torch.cat([prob["u"], (40.2 + 3.0 * torch.rand(hot, generator=g)) * du])
+    v = torch.cat([prob["v"], (-21.7 + 3.0 * torch.rand(hot, generator=g)) * du])
+    w = torch.cat([prob["w"], torch.full((hot,), -10.0)])
+    wt = torch.ones(u.numel())
+    vis = torch.cat([prob["vis"], torch.complex(torch.randn(hot, generator=g), torch.randn(hot, generator=g))])
+    _compare(rick, oracle_mod, dict(params=prob["params"], u=u, v=v, w=w, wt=wt, vis=vis), REAL)
+
+
 def test_repeatable_and_stream_ordered(rick):
     """Two images of the same problem, the second on a side stream, agree to
     FP32 reordering (uncorrected images, so no taper amplification)."""

@@ -175,6 +175,20 @@ def oracle_sample(prob_np, planes):
 
 
 # ------------------------------------------------------------------ main
+def aggregate(ms_local, units_per_step, steps, world, device):
+    """Slowest rank's timed-region milliseconds and the whole-job throughput:
+    every rank processes units_per_step units per step (replicas, weak
+    scaling), value = world * units_per_step * steps / slowest time."""
+    import torch
+    import torch.distributed as dist
+    ms = float(ms_local)
+    if world > 1:
+        t = torch.tensor([ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_step * steps / (ms / 1e3)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -252,12 +266,8 @@ def main():
     clk = clocks.stop()
     ms = start.elapsed_time(end)
     tm = im.timing()
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, value = aggregate(ms, m, args.steps, world, dev)
     ms_step = ms / max(args.steps, 1)
-    value = world * m * args.steps / (ms / 1e3)
 
     # ------------------------------------------------ roofline (gridder)
     peak, peak_kind = _peaks()

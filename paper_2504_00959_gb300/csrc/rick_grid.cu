@@ -8,23 +8,24 @@
 // tile in shared memory and writes the whole tile once with coalesced 16-byte
 // stores -- also when it is empty, so the planes need no memset and HBM sees
 // each plane byte once.  No atomics, global or shared:
-//   * lanes 0..15 evaluate the u taps and lanes 16..31 the v taps of one
-//     entry (degree-10 polynomials, coefficients held in registers), then
-//     every lane takes the (row, column) taps of its footprint cells by
-//     shuffle, so one entry's S^2 cells are spread over the 32 lanes;
-//   * a warp's cells for one entry are distinct, and the tile's row pitch P
-//     is chosen with P = S (mod 16), which puts the 16 cells of each
-//     half-warp in 16 different 8-byte bank pairs: read-modify-write of the
-//     footprint is conflict-free;
+//   * entries are taken 32 at a time: each lane loads one (a coalesced
+//     512-byte load per warp) and evaluates its 2S taps (degree-10
+//     polynomials) into a per-warp stage in shared memory;
+//   * the warp then walks the 32 staged entries; the S x S footprint is cut
+//     into S rows of S/2 + 1 pairs of horizontally adjacent cells aligned to
+//     even columns, and every lane owns fixed (row, pair) slots, read and
+//     written as one 16-byte value (4 FMAs per slot);
+//   * the tile's pitch in pairs is 4 (mod 8), so the 8 lanes of every phase
+//     of a 128-bit access (2 rows x 4 pairs) hit 8 different 16-byte bank
+//     groups: the read-modify-write of a footprint is conflict-free;
 //   * a __syncwarp between entries orders one entry's stores before the next
 //     entry's loads.
 // Tiles with more than kHeavyEntries entries (the dense centre of the uv
 // plane) would serialise on one warp: k_grid_tiles writes them as zeros and
 // lists them as chunks of at most kHeavyEntries entries, and k_grid_chunks
 // gives every chunk to a warp, which adds its private tile into the plane
-// with vector atomic adds.  Entries are loaded 32 at a time (one coalesced
-// 512-byte load per warp) and broadcast by shuffle.  The fftshift
-// checkerboard (-1)^(ju+jv) is folded into the tap signs.
+// with vector atomic adds.  The fftshift checkerboard (-1)^(ju+jv) is folded
+// into the tap signs.
 #include "rick_internal.cuh"
 
 namespace rick {
@@ -46,62 +47,136 @@ int sm_count_grid()
     return cached[dev];
 }
 
-// Row pitch (in cells) of a shared-memory tile: >= T and = S (mod 16).
-__host__ __device__ __forceinline__ int tile_pitch(int T, int S) { return T + (((S - T) % 16) + 16) % 16; }
+// A shared-memory tile is T rows of T/2 cell pairs (16-byte float4 units),
+// unpadded; pair pr of row r sits at r (T/2) + (pr ^ 4 (r & 1)).  With this
+// swizzle the 8 lanes of each phase of a 128-bit access (2 footprint rows x
+// 4 pairs, or 8 pairs of one row in whole-tile passes) fall in 8 different
+// 16-byte bank groups.  T >= 16, so a row holds at least 8 pairs.
+__device__ __forceinline__ int pair_index(int row, int pr, int log2tp)
+{
+    return (row << log2tp) + (pr ^ ((row & 1) << 2));
+}
 
 int light_warps(int T) { return T <= 16 ? 8 : (T <= 32 ? 4 : 1); }
 
-// Per-lane constants: the footprint cells (slots) this lane updates for
-// every entry: slot s is tap index lane + 32 s, at footprint row sr, column sc.
+// Per-lane constants: the footprint cells this lane updates for every entry,
+// as (row, pair) slots.  A footprint row of S cells starting at column lu
+// spans kPairs cell pairs aligned to even tile columns (the first or last
+// pair holds one zero tap); slot s of a lane is pair index lane + 32 s of the
+// row-major list of (row, pair).  roff is the slot row's byte offset in the
+// tile and xm its part of the swizzle (pair_index).
 template <int S>
 struct LaneSlots {
-    static constexpr int kSlots = (S * S + 31) / 32;
-    int sr[kSlots], sc[kSlots];
+    static constexpr int kPairs = S / 2 + 1;
+    static constexpr int kSlots = (S * kPairs + 31) / 32;
+    int sr[kSlots], sp[kSlots];
+    uint32_t roff[kSlots], xm[kSlots];
     bool ok[kSlots];
 
-    __device__ __forceinline__ void init(int lane)
+    __device__ __forceinline__ void init(int lane, int ltp)
     {
 #pragma unroll
         for (int s = 0; s < kSlots; ++s) {
             const int i = lane + 32 * s;
-            ok[s] = i < S * S;
-            sr[s] = ok[s] ? i / S : 0;
-            sc[s] = ok[s] ? i % S : 0;
+            ok[s] = i < S * kPairs;
+            sr[s] = ok[s] ? i / kPairs : 0;
+            sp[s] = ok[s] ? i % kPairs : 0;
+            roff[s] = (uint32_t)sr[s] << (ltp + 4);
+            xm[s] = (uint32_t)(sr[s] & 1) << 2;
         }
     }
 };
 
-// Per-warp staging of 32 entries in shared memory: their signed taps and a
-// header (first cell relative to the tile origin, weighted visibility).
+// Predicated read-modify-write of one tile pair at shared address addr:
+// (c0, c1) += (ga, gb) x (vr + i vi).  Shared-window addressing keeps the
+// address arithmetic 32-bit; the predicate replaces a branch.
+__device__ __forceinline__ void rmw_pair(uint32_t addr, bool on, float ga, float gb, float vr, float vi)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .f32 a, b, c, d;\n\t"
+        "setp.ne.u32 p, %0, 0;\n\t"
+        "@p ld.shared.v4.f32 {a, b, c, d}, [%1];\n\t"
+        "@p fma.rn.f32 a, %2, %4, a;\n\t"
+        "@p fma.rn.f32 b, %2, %5, b;\n\t"
+        "@p fma.rn.f32 c, %3, %4, c;\n\t"
+        "@p fma.rn.f32 d, %3, %5, d;\n\t"
+        "@p st.shared.v4.f32 [%1], {a, b, c, d};\n\t}"
+        :
+        : "r"((uint32_t)on), "r"(addr), "f"(ga), "f"(gb), "f"(vr), "f"(vi)
+        : "memory");
+}
+
+// Per-warp staging of 32 entries in shared memory: each entry's u taps laid
+// out on its pair grid (kPairs pairs, zero-padded on the side of the odd
+// start column), its v taps times the weighted visibility (complex), and a
+// header (first row and first pair relative to the tile).
 template <int S>
 struct Stage {
-    static constexpr int kStride = S <= 8 ? 8 : 16;
-    float gu[32 * kStride];
-    float gv[32 * kStride];
-    float4 head[32];
+    static constexpr int kPairs = LaneSlots<S>::kPairs;
+    float2 gu[32 * kPairs];
+    float2 gvv[32 * S];
+    int2 head[32];
 };
 
-// Shared memory of one warp: its tile (T rows of pitch P cells) and its stage.
+// Shared memory of one warp: its tile (T rows of T/2 pairs) and its stage.
 template <int S>
 __host__ __device__ __forceinline__ size_t warp_smem_bytes(int T)
 {
-    return (size_t)T * tile_pitch(T, S) * sizeof(float2) + sizeof(Stage<S>);
+    return (size_t)T * T * sizeof(float2) + sizeof(Stage<S>);
 }
+
+// One staged entry in registers: its first row and pair, and for each of the
+// lane's slots the u tap pair and the complex v tap x visibility.
+template <int S>
+struct Staged {
+    static constexpr int NS = LaneSlots<S>::kSlots;
+    int2 h;
+    float2 g2[NS], gq[NS];
+
+    __device__ __forceinline__ void load(const Stage<S>& st, const LaneSlots<S>& ls, int q)
+    {
+        h = st.head[q];
+#pragma unroll
+        for (int sl = 0; sl < NS; ++sl) {
+            g2[sl] = st.gu[q * Stage<S>::kPairs + ls.sp[sl]];
+            gq[sl] = st.gvv[q * S + ls.sr[sl]];
+        }
+    }
+
+    __device__ __forceinline__ void apply(uint32_t tile_s, const LaneSlots<S>& ls, unsigned T, unsigned TP,
+                                          int ltp) const
+    {
+        const uint32_t base = tile_s + ((uint32_t)h.x << (ltp + 4));
+        const uint32_t px = ((uint32_t)h.x & 1u) << 2;
+#pragma unroll
+        for (int sl = 0; sl < NS; ++sl) {
+            const unsigned row = (unsigned)(h.x + ls.sr[sl]), pr = (unsigned)(h.y + ls.sp[sl]);
+            const bool on = ls.ok[sl] && row < T && pr < TP;
+            const uint32_t addr = base + ls.roff[sl] + ((pr ^ ls.xm[sl] ^ px) << 4);
+            rmw_pair(addr, on, g2[sl].x, g2[sl].y, gq[sl].x, gq[sl].y);
+        }
+    }
+};
 
 // Accumulate entries [b, e) of one sorted list into the warp's tile.  Rounds
 // of 32 entries: (1) each lane takes one entry (coalesced 16-byte loads) and
 // evaluates its 2S taps (degree-10 polynomials with uniform coefficients from
 // the constant bank) with the checkerboard signs folded in, into the stage;
-// (2) the warp walks the 32 entries, every lane updating its slots' cells.
-// Within one entry the lanes' cells are distinct and, with pitch P = S
-// (mod 16), in distinct bank pairs; a __syncwarp orders consecutive entries.
+// (2) the warp walks the 32 entries; every lane updates its slots, each a
+// pair of horizontally adjacent cells read and written as one 16-byte value
+// (4 FMAs: u tap pair x complex v tap-visibility product).  Within one entry
+// the lanes' pairs are distinct and conflict-free; a __syncwarp orders
+// consecutive entries.  The stage is read-only during the walk, so the next
+// entry's header and taps are loaded before this entry's read-modify-write.
 template <int S>
 __device__ __forceinline__ void warp_grid_range(const GridCfg& c, const float4* __restrict__ ent, uint32_t b,
-                                                uint32_t e, int u0, int v0, float2* tile, Stage<S>& st, int P,
+                                                uint32_t e, int u0, int v0, float4* tile4, Stage<S>& st,
                                                 const LaneSlots<S>& ls, int lane, int shift)
 {
-    constexpr int K = Stage<S>::kStride;
-    const unsigned T = (unsigned)c.T;
+    constexpr int KP = Stage<S>::kPairs;
+    const unsigned T = (unsigned)c.T, TP = (unsigned)(c.T / 2);
+    const int ltp = c.log2T - 1;
+    const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile4);
     for (uint32_t j0 = b; j0 < e; j0 += 32) {
         const uint32_t j = j0 + lane;
         if (j < e) {
@@ -109,6 +184,9 @@ __device__ __forceinline__ void warp_grid_range(const GridCfg& c, const float4* 
             const int fu = first_cell(c, r.x), fv = first_cell(c, r.y);
             const float zu = __fmaf_rn(2.0f, __fsub_rn(__fsub_rn(r.x, c.half_s), (float)(fu - 1)), -1.0f);
             const float zv = __fmaf_rn(2.0f, __fsub_rn(__fsub_rn(r.y, c.half_s), (float)(fv - 1)), -1.0f);
+            const int lu = fu - u0;
+            const int odd = lu & 1;  // u0 is even: the parity of the tile column
+            float gu[S];
 #pragma unroll
             for (int t = 0; t < S; ++t) {
                 float a = c.coef[t][kPolyTerms - 1], bb = c.coef[t][kPolyTerms - 1];
@@ -121,29 +199,35 @@ __device__ __forceinline__ void warp_grid_range(const GridCfg& c, const float4* 
                     if ((fu + t) & 1) a = -a;
                     if ((fv + t) & 1) bb = -bb;
                 }
-                st.gu[lane * K + t] = a;
-                st.gv[lane * K + t] = bb;
+                gu[t] = a;
+                st.gvv[lane * S + t] = make_float2(bb * r.z, bb * r.w);
             }
-            st.head[lane] = make_float4(__int_as_float(fu - u0), __int_as_float(fv - v0), r.z, r.w);
+            // pair t holds tile columns 2 (pu + t) and 2 (pu + t) + 1: taps
+            // (2t, 2t+1) for an even start column, (2t-1, 2t) for an odd one
+#pragma unroll
+            for (int t = 0; t < KP; ++t) {
+                const float e0 = 2 * t < S ? gu[2 * t < S ? 2 * t : 0] : 0.0f;
+                const float e1 = 2 * t + 1 < S ? gu[2 * t + 1 < S ? 2 * t + 1 : 0] : 0.0f;
+                const float o0 = 2 * t - 1 >= 0 ? gu[2 * t - 1 >= 0 ? 2 * t - 1 : 0] : 0.0f;
+                st.gu[lane * KP + t] = odd ? make_float2(o0, e0) : make_float2(e0, e1);
+            }
+            st.head[lane] = make_int2(fv - v0, (lu - odd) / 2);
         }
         __syncwarp();
         const int cnt = (e - j0 < 32u) ? (int)(e - j0) : 32;
-        for (int q = 0; q < cnt; ++q) {
-            const float4 h = st.head[q];
-            const int lu = __float_as_int(h.x), lv = __float_as_int(h.y);
-#pragma unroll
-            for (int sl = 0; sl < LaneSlots<S>::kSlots; ++sl) {
-                const unsigned row = (unsigned)(lv + ls.sr[sl]), col = (unsigned)(lu + ls.sc[sl]);
-                if (ls.ok[sl] && row < T && col < T) {
-                    const float wgt = st.gu[q * K + ls.sc[sl]] * st.gv[q * K + ls.sr[sl]];
-                    float2* cell = tile + row * P + col;
-                    float2 x = *cell;
-                    x.x = __fmaf_rn(h.z, wgt, x.x);
-                    x.y = __fmaf_rn(h.w, wgt, x.y);
-                    *cell = x;
-                }
-            }
+        // two register sets, alternating: the next entry's stage values load
+        // while this entry's pairs are updated
+        Staged<S> A, B;
+        A.load(st, ls, 0);
+        for (int q = 0;; q += 2) {
+            if (q + 1 < cnt) B.load(st, ls, q + 1);
+            A.apply(tile_s, ls, T, TP, ltp);
             __syncwarp();
+            if (q + 1 >= cnt) break;
+            if (q + 2 < cnt) A.load(st, ls, q + 2);
+            B.apply(tile_s, ls, T, TP, ltp);
+            __syncwarp();
+            if (q + 2 >= cnt) break;
         }
     }
 }
@@ -168,39 +252,51 @@ __device__ __forceinline__ TileGeom tile_geom(const GridCfg& c, int k0, int64_t 
     return g;
 }
 
-// Write (or zero) the valid part of a tile: 16 lanes per 256-byte row segment.
-template <bool kZero>
-__device__ __forceinline__ void store_tile(const GridCfg& c, const TileGeom& g, float2* P0, const float2* tile,
-                                           int P, int tid, int nthreads)
+// Whole-tile passes of one warp: lane L keeps the pair column L mod (T/2)
+// and starts at row L / (T/2), stepping 32 / (T/2) rows, so every pass is a
+// run of 16-byte accesses with no division.  The plane row of the pair is
+// (v0 + row) n + u0 + 2 pr, 16-byte aligned because n and u0 are even.
+struct TileWalk {
+    int pr, r0, dr, ltp;
+};
+
+__device__ __forceinline__ TileWalk tile_walk(const GridCfg& c, int lane)
 {
-    const int half = c.T >> 1;
-    for (int i = tid; i < c.T * half; i += nthreads) {
-        const int row = i / half, col = (i - row * half) * 2;
-        if (row < g.wv && col < g.wu) {
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (!kZero) {
-                const float2 a = tile[row * P + col], b = tile[row * P + col + 1];
-                v = make_float4(a.x, a.y, b.x, b.y);
-            }
-            *reinterpret_cast<float4*>(P0 + (int64_t)(g.v0 + row) * c.n + g.u0 + col) = v;
-        }
-    }
+    TileWalk w;
+    w.ltp = c.log2T - 1;
+    w.pr = lane & ((1 << w.ltp) - 1);
+    w.r0 = lane >> w.ltp;
+    w.dr = 32 >> w.ltp;
+    return w;
 }
 
-// Initialise a tile copy: zeros, or the plane's current values (accumulating pass).
-__device__ __forceinline__ void init_tile(const GridCfg& c, const TileGeom& g, const float2* P0, float2* tile, int P,
-                                          bool from_plane, int tid, int nthreads)
+// Write the valid part of a tile to the plane (or zeros): coalesced 16-byte
+// stores, 256 contiguous bytes per row segment for T = 32.
+template <bool kZero>
+__device__ __forceinline__ void store_tile(const GridCfg& c, const TileGeom& g, float2* P0, const float4* tile4,
+                                           int lane)
 {
-    if (!from_plane) {
-        float4* t4 = reinterpret_cast<float4*>(tile);
-        for (int i = tid; i < (c.T * P) / 2; i += nthreads) t4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
-    }
-    for (int i = tid; i < c.T * P; i += nthreads) {
-        const int row = i / P, col = i - row * P;
-        float2 x = make_float2(0.f, 0.f);
-        if (row < g.wv && col < g.wu) x = P0[(int64_t)(g.v0 + row) * c.n + g.u0 + col];
-        tile[i] = x;
+    const TileWalk w = tile_walk(c, lane);
+    if (2 * w.pr >= g.wu) return;
+    float4* dst = reinterpret_cast<float4*>(P0 + (int64_t)(g.v0 + w.r0) * c.n + g.u0 + 2 * w.pr);
+    const int64_t step = (int64_t)w.dr * (c.n / 2);
+    for (int row = w.r0; row < g.wv; row += w.dr, dst += step)
+        *dst = kZero ? make_float4(0.f, 0.f, 0.f, 0.f) : tile4[pair_index(row, w.pr, w.ltp)];
+}
+
+// Initialise a tile copy: zeros, or the plane's current values (accumulating
+// pass; cells outside the grid start at zero).
+__device__ __forceinline__ void init_tile(const GridCfg& c, const TileGeom& g, const float2* P0, float4* tile4,
+                                          bool from_plane, int lane)
+{
+    const TileWalk w = tile_walk(c, lane);
+    const float4* src = reinterpret_cast<const float4*>(P0 + (int64_t)(g.v0 + w.r0) * c.n + g.u0 + 2 * w.pr);
+    const int64_t step = (int64_t)w.dr * (c.n / 2);
+    const bool col_ok = from_plane && 2 * w.pr < g.wu;
+    for (int row = w.r0; row < c.T; row += w.dr, src += step) {
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (col_ok && row < g.wv) x = *src;
+        tile4[pair_index(row, w.pr, w.ltp)] = x;
     }
 }
 
@@ -213,10 +309,9 @@ __global__ void __launch_bounds__(256) k_grid_tiles(GridCfg c, ChunkList ch, int
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t tl = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
     if (tl >= ntl) return;
-    const int P = tile_pitch(c.T, S);
     unsigned char* mine = reinterpret_cast<unsigned char*>(smem4) + (size_t)wid * warp_smem_bytes<S>(c.T);
-    float2* tile = reinterpret_cast<float2*>(mine);
-    Stage<S>& st = *reinterpret_cast<Stage<S>*>(mine + (size_t)c.T * P * sizeof(float2));
+    float4* tile4 = reinterpret_cast<float4*>(mine);
+    Stage<S>& st = *reinterpret_cast<Stage<S>*>(mine + (size_t)c.T * c.T * sizeof(float2));
     const TileGeom g = tile_geom(c, k0, tl);
     float2* P0 = planes + (int64_t)g.kl * c.n * c.n;
 
@@ -235,7 +330,7 @@ __global__ void __launch_bounds__(256) k_grid_tiles(GridCfg c, ChunkList ch, int
                 heavy[1 + 2 * (base + k)] = (uint32_t)tl;
                 heavy[2 + 2 * (base + k)] = k;
             }
-            if (!accumulate) store_tile<true>(c, g, P0, nullptr, P, lane, 32);
+            if (!accumulate) store_tile<true>(c, g, P0, nullptr, lane);
             return;
         }
         // no room in the chunk list: mark the reserved slots that do exist as
@@ -243,23 +338,24 @@ __global__ void __launch_bounds__(256) k_grid_tiles(GridCfg c, ChunkList ch, int
         for (uint32_t k = base + lane; k < heavy_cap; k += 32) heavy[1 + 2 * k] = 0xffffffffu;
     }
     if (nent == 0 && !accumulate) {
-        store_tile<true>(c, g, P0, nullptr, P, lane, 32);
+        store_tile<true>(c, g, P0, nullptr, lane);
         return;
     }
-    init_tile(c, g, P0, tile, P, accumulate != 0, lane, 32);
+    init_tile(c, g, P0, tile4, accumulate != 0, lane);
     __syncwarp();
     LaneSlots<S> ls;
-    ls.init(lane);
+    ls.init(lane, c.log2T - 1);
     for (int q = 0; q < ch.count; ++q)
-        warp_grid_range<S>(c, ch.ent[q], ch.off[q][g.tg], ch.off[q][g.tg + 1], g.u0, g.v0, tile, st, P, ls, lane,
+        warp_grid_range<S>(c, ch.ent[q], ch.off[q][g.tg], ch.off[q][g.tg + 1], g.u0, g.v0, tile4, st, ls, lane,
                            shift);
     __syncwarp();
-    store_tile<false>(c, g, P0, tile, P, lane, 32);
+    store_tile<false>(c, g, P0, tile4, lane);
 }
 
 // Chunks of the tiles with many entries: one warp per chunk, private tile in
-// shared memory, flushed into the plane with vector atomic adds (the tile's
-// cells were zeroed by k_grid_tiles, which ran before on the same stream).
+// shared memory, flushed into the plane with 16-byte vector atomic adds of
+// the non-zero cell pairs (the tile's cells were zeroed by k_grid_tiles,
+// which ran before on the same stream).
 template <int S>
 __global__ void __launch_bounds__(256) k_grid_chunks(GridCfg c, ChunkList ch, int k0, int shift,
                                                      float2* __restrict__ planes, const uint32_t* __restrict__ heavy,
@@ -267,12 +363,11 @@ __global__ void __launch_bounds__(256) k_grid_chunks(GridCfg c, ChunkList ch, in
 {
     extern __shared__ float4 smem4[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int P = tile_pitch(c.T, S);
     unsigned char* mine = reinterpret_cast<unsigned char*>(smem4) + (size_t)wid * warp_smem_bytes<S>(c.T);
-    float2* tile = reinterpret_cast<float2*>(mine);
-    Stage<S>& st = *reinterpret_cast<Stage<S>*>(mine + (size_t)c.T * P * sizeof(float2));
+    float4* tile4 = reinterpret_cast<float4*>(mine);
+    Stage<S>& st = *reinterpret_cast<Stage<S>*>(mine + (size_t)c.T * c.T * sizeof(float2));
     LaneSlots<S> ls;
-    ls.init(lane);
+    ls.init(lane, c.log2T - 1);
     const uint32_t count = min(heavy[0], heavy_cap);
     const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
     for (uint32_t it = blockIdx.x * (blockDim.x >> 5) + wid; it < count; it += nwarps) {
@@ -285,15 +380,17 @@ __global__ void __launch_bounds__(256) k_grid_chunks(GridCfg c, ChunkList ch, in
         const uint32_t b0 = ch.off[0][g.tg], e0 = ch.off[0][g.tg + 1];
         const uint32_t b = b0 + k * kHeavyEntries;
         const uint32_t e = min(e0, b + kHeavyEntries);
-        init_tile(c, g, P0, tile, P, false, lane, 32);
+        init_tile(c, g, P0, tile4, false, lane);
         __syncwarp();
-        warp_grid_range<S>(c, ch.ent[0], b, e, g.u0, g.v0, tile, st, P, ls, lane, shift);
+        warp_grid_range<S>(c, ch.ent[0], b, e, g.u0, g.v0, tile4, st, ls, lane, shift);
         __syncwarp();
-        for (int i = lane; i < c.T * c.T; i += 32) {
-            const int row = i / c.T, col = i - row * c.T;
-            if (row < g.wv && col < g.wu) {
-                const float2 x = tile[row * P + col];
-                if (x.x != 0.f || x.y != 0.f) atomicAdd(P0 + (int64_t)(g.v0 + row) * c.n + g.u0 + col, x);
+        const TileWalk w = tile_walk(c, lane);
+        if (2 * w.pr < g.wu) {
+            float4* dst = reinterpret_cast<float4*>(P0 + (int64_t)(g.v0 + w.r0) * c.n + g.u0 + 2 * w.pr);
+            const int64_t step = (int64_t)w.dr * (c.n / 2);
+            for (int row = w.r0; row < g.wv; row += w.dr, dst += step) {
+                const float4 x = tile4[pair_index(row, w.pr, w.ltp)];
+                if (x.x != 0.f || x.y != 0.f || x.z != 0.f || x.w != 0.f) atomicAdd(dst, x);
             }
         }
         __syncwarp();
@@ -326,8 +423,12 @@ cudaError_t launch_grid_s(const GridCfg& c, const ChunkList& ch, int k0, int nk,
     k_grid_tiles<S><<<(unsigned)nblocks, 32 * wl, tile_bytes * wl, s>>>(c, ch, k0, ntl, shift ? 1 : 0,
                                                                        accumulate ? 1 : 0, planes, heavy, cap);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    k_grid_chunks<S><<<(unsigned)(4 * sm_count_grid()), 32 * wl, tile_bytes * wl, s>>>(c, ch, k0, shift ? 1 : 0,
-                                                                                        planes, heavy, cap);
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_chunks<S>, 32 * wl, tile_bytes * wl)) !=
+        cudaSuccess)
+        return e;
+    const unsigned nchunk_blocks = (unsigned)(max(per_sm, 1) * sm_count_grid());
+    k_grid_chunks<S><<<nchunk_blocks, 32 * wl, tile_bytes * wl, s>>>(c, ch, k0, shift ? 1 : 0, planes, heavy, cap);
     return cudaGetLastError();
 }
 

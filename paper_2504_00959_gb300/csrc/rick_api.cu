@@ -261,8 +261,14 @@ rick_status grid_pass(rick_handle h, int k0, int nk, bool shift, float2* planes)
             cl.off[cl.count] = h->chunks[q].off;
             cl.ent[cl.count] = h->chunks[q].ent;
         }
-        // the scatter cursors are idle here: they hold the list of heavy tiles
-        RICK_CU(h, launch_grid(h->cfg, cl, k0, nk, shift, c0 > 0, h->cursor, planes, h->stream));
+        // the heavy-chunk list (used when the pass has one chunk) is sized
+        // for that chunk's entry bound, stream-ordered from the pool
+        const size_t words = cl.count == 1 ? heavy_words_for(h->chunks[c0].cap) : 1;
+        uint32_t* heavy = nullptr;
+        RICK_CU(h, cudaMallocFromPoolAsync((void**)&heavy, words * sizeof(uint32_t), h->pool, h->stream));
+        const cudaError_t e = launch_grid(h->cfg, cl, k0, nk, shift, c0 > 0, heavy, words, planes, h->stream);
+        cudaFreeAsync(heavy, h->stream);
+        RICK_CU(h, e);
         count_launches(h, 2);
         c0 += kMaxChunksPerPass;
     } while (c0 < nch);
@@ -327,6 +333,7 @@ rick_status rick_workspace_size(const rick_params* p, int64_t max_vis, size_t* b
     b += (size_t)ntiles * sizeof(uint32_t) * 2 + sizeof(uint32_t);   // cursor + offsets
     b += scan_block_sums_len(ntiles) * sizeof(uint32_t);
     b += (size_t)entries_bound(c, max_vis) * sizeof(float4);         // entries
+    b += heavy_words_for(entries_bound(c, max_vis)) * sizeof(uint32_t);  // gridder's heavy-chunk list
     if (p->flags & RICK_UNIFORM_WEIGHT) b += (size_t)c.n * c.n * sizeof(uint32_t);
     b += plane_bytes(p);                                             // cuFFT work area (estimate)
     *bytes = b;
@@ -520,6 +527,7 @@ rick_status rick_destroy(rick_handle h)
     cudaFree(h->chan_sw);
     cudaFree(h->b_off);
     cudaFree(h->b_ent);
+    cudaFree(h->b_heavy);
     if (h->pool) cudaMemPoolDestroy(h->pool);
     delete h;
     return RICK_OK;
@@ -858,7 +866,7 @@ static rick_status batch_body(rick_handle h, const float* vis, const float* u, c
             cl.off[0] = h->b_off;
             cl.ent[0] = h->b_ent;
             cl.count = 1;
-            RICK_CU(h, launch_grid(c, cl, k0, nk, true, false, h->cursor, h->planes, h->stream));
+            RICK_CU(h, launch_grid(c, cl, k0, nk, true, false, h->b_heavy, h->b_heavy_words, h->planes, h->stream));
             count_launches(h, 2);
         }
         cufftHandle plan;
@@ -927,8 +935,16 @@ rick_status rick_image_batch(rick_handle h, const float* vis, const float* u, co
         h->b_ent = nullptr;
         h->bytes_held -= (size_t)h->b_cap * sizeof(float4);
         h->b_cap = 0;
+        cudaFree(h->b_heavy);
+        h->b_heavy = nullptr;
+        h->bytes_held -= h->b_heavy_words * sizeof(uint32_t);
+        h->b_heavy_words = 0;
         RICK_CU(h, cudaMalloc((void**)&h->b_ent, (size_t)cap * sizeof(float4)));
         h->b_cap = cap;
+        const size_t hw = heavy_words_for(cap);
+        RICK_CU(h, cudaMalloc((void**)&h->b_heavy, hw * sizeof(uint32_t)));
+        h->b_heavy_words = hw;
+        h->bytes_held += hw * sizeof(uint32_t);
         h->bytes_held += (size_t)cap * sizeof(float4);
         stale = true;
     }

@@ -32,6 +32,7 @@ namespace rick {
 namespace {
 
 constexpr int kHeavyEntries = 256;
+constexpr int kTilesPerWarp = 4;
 
 int sm_count_grid()
 {
@@ -47,14 +48,16 @@ int sm_count_grid()
     return cached[dev];
 }
 
-// A shared-memory tile is T rows of T/2 cell pairs (16-byte float4 units),
-// unpadded; pair pr of row r sits at r (T/2) + (pr ^ 4 (r & 1)).  With this
-// swizzle the 8 lanes of each phase of a 128-bit access (2 footprint rows x
-// 4 pairs, or 8 pairs of one row in whole-tile passes) fall in 8 different
-// 16-byte bank groups.  T >= 16, so a row holds at least 8 pairs.
-__device__ __forceinline__ int pair_index(int row, int pr, int log2tp)
+// A shared-memory tile is T rows of cell pairs (16-byte float4 units) with a
+// row pitch of P2 >= T/2 pairs, P2 = 4 (mod 8): the 8 lanes of each phase of
+// a 128-bit access (2 footprint rows x 4 pairs, or 8 pairs of one row in
+// whole-tile passes) then fall in 8 different 16-byte bank groups, and the
+// address of footprint slot (sr, sp) of an entry is the entry's base plus a
+// per-lane constant.
+__host__ __device__ __forceinline__ int pair_pitch(int T)
 {
-    return (row << log2tp) + (pr ^ ((row & 1) << 2));
+    const int h = T / 2;
+    return h + ((4 - h % 8) % 8 + 8) % 8;
 }
 
 int light_warps(int T) { return T <= 16 ? 8 : (T <= 32 ? 4 : 1); }
@@ -63,79 +66,98 @@ int light_warps(int T) { return T <= 16 ? 8 : (T <= 32 ? 4 : 1); }
 // as (row, pair) slots.  A footprint row of S cells starting at column lu
 // spans kPairs cell pairs aligned to even tile columns (the first or last
 // pair holds one zero tap); slot s of a lane is pair index lane + 32 s of the
-// row-major list of (row, pair).  roff is the slot row's byte offset in the
-// tile and xm its part of the swizzle (pair_index).
+// row-major list of (row, pair).  loff is the slot's byte offset from the
+// footprint's first pair in the tile.
 template <int S>
 struct LaneSlots {
     static constexpr int kPairs = S / 2 + 1;
     static constexpr int kSlots = (S * kPairs + 31) / 32;
     int sr[kSlots], sp[kSlots];
-    uint32_t roff[kSlots], xm[kSlots];
-    bool ok[kSlots];
+    uint32_t loff[kSlots];
+    uint32_t lanebit;
 
-    __device__ __forceinline__ void init(int lane, int ltp)
+    __device__ __forceinline__ void init(int lane, int p2)
     {
+        lanebit = 1u << lane;
 #pragma unroll
         for (int s = 0; s < kSlots; ++s) {
             const int i = lane + 32 * s;
-            ok[s] = i < S * kPairs;
-            sr[s] = ok[s] ? i / kPairs : 0;
-            sp[s] = ok[s] ? i % kPairs : 0;
-            roff[s] = (uint32_t)sr[s] << (ltp + 4);
-            xm[s] = (uint32_t)(sr[s] & 1) << 2;
+            sr[s] = i < S * kPairs ? i / kPairs : 0;
+            sp[s] = i < S * kPairs ? i % kPairs : 0;
+            loff[s] = (uint32_t)(sr[s] * p2 + sp[s]) * 16u;
         }
     }
 };
 
-// Predicated read-modify-write of one tile pair at shared address addr:
-// (c0, c1) += (ga, gb) x (vr + i vi).  Shared-window addressing keeps the
-// address arithmetic 32-bit; the predicate replaces a branch.
-__device__ __forceinline__ void rmw_pair(uint32_t addr, bool on, float ga, float gb, float vr, float vi)
+// Read-modify-write of one tile pair at shared address addr when this lane's
+// bit is set in mask: (c0, c1) += (ga, gb) x (vr + i vi).  Shared-window
+// addressing keeps the address arithmetic 32-bit; the predicate replaces a
+// branch.
+__device__ __forceinline__ void rmw_pair(uint32_t addr, uint32_t mask, uint32_t lanebit, float ga, float gb,
+                                         float vr, float vi)
 {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t.reg .f32 a, b, c, d;\n\t"
-        "setp.ne.u32 p, %0, 0;\n\t"
-        "@p ld.shared.v4.f32 {a, b, c, d}, [%1];\n\t"
-        "@p fma.rn.f32 a, %2, %4, a;\n\t"
-        "@p fma.rn.f32 b, %2, %5, b;\n\t"
-        "@p fma.rn.f32 c, %3, %4, c;\n\t"
-        "@p fma.rn.f32 d, %3, %5, d;\n\t"
-        "@p st.shared.v4.f32 [%1], {a, b, c, d};\n\t}"
+        "{\n\t.reg .pred p;\n\t.reg .b32 t;\n\t.reg .f32 a, b, c, d;\n\t"
+        "and.b32 t, %0, %1;\n\t"
+        "setp.ne.u32 p, t, 0;\n\t"
+        "@p ld.shared.v4.f32 {a, b, c, d}, [%2];\n\t"
+        "@p fma.rn.f32 a, %3, %5, a;\n\t"
+        "@p fma.rn.f32 b, %3, %6, b;\n\t"
+        "@p fma.rn.f32 c, %4, %5, c;\n\t"
+        "@p fma.rn.f32 d, %4, %6, d;\n\t"
+        "@p st.shared.v4.f32 [%2], {a, b, c, d};\n\t}"
         :
-        : "r"((uint32_t)on), "r"(addr), "f"(ga), "f"(gb), "f"(vr), "f"(vi)
+        : "r"(mask), "r"(lanebit), "r"(addr), "f"(ga), "f"(gb), "f"(vr), "f"(vi)
         : "memory");
 }
 
 // Per-warp staging of 32 entries in shared memory: each entry's u taps laid
 // out on its pair grid (kPairs pairs, zero-padded on the side of the odd
 // start column), its v taps times the weighted visibility (complex), and a
-// header (first row and first pair relative to the tile).
+// header: the shared address of its first pair, then one word per slot of
+// lane bits saying which lanes' pairs lie inside the tile.
 template <int S>
 struct Stage {
     static constexpr int kPairs = LaneSlots<S>::kPairs;
+    static constexpr int kSlots = LaneSlots<S>::kSlots;
+    static constexpr int kHead = kSlots + 1 <= 2 ? 2 : (kSlots + 1 <= 4 ? 4 : 8);
     float2 gu[32 * kPairs];
     float2 gvv[32 * S];
-    int2 head[32];
+    uint32_t head[32 * kHead];
 };
 
-// Shared memory of one warp: its tile (T rows of T/2 pairs) and its stage.
+// Shared memory of one warp: its tile (T rows of pitch P2 pairs) and its stage.
 template <int S>
 __host__ __device__ __forceinline__ size_t warp_smem_bytes(int T)
 {
-    return (size_t)T * T * sizeof(float2) + sizeof(Stage<S>);
+    return (size_t)T * pair_pitch(T) * sizeof(float4) + sizeof(Stage<S>);
 }
 
-// One staged entry in registers: its first row and pair, and for each of the
-// lane's slots the u tap pair and the complex v tap x visibility.
+// One staged entry in registers: its header, and for each of the lane's
+// slots the u tap pair and the complex v tap x visibility.
 template <int S>
 struct Staged {
-    static constexpr int NS = LaneSlots<S>::kSlots;
-    int2 h;
+    static constexpr int NS = LaneSlots<S>::kSlots, NH = Stage<S>::kHead;
+    uint32_t h[NH];
     float2 g2[NS], gq[NS];
 
     __device__ __forceinline__ void load(const Stage<S>& st, const LaneSlots<S>& ls, int q)
     {
-        h = st.head[q];
+        const uint4* hp = reinterpret_cast<const uint4*>(st.head + q * NH);
+        if (NH == 2) {
+            const uint2 x = *reinterpret_cast<const uint2*>(st.head + q * NH);
+            h[0] = x.x;
+            h[1] = x.y;
+        } else {
+#pragma unroll
+            for (int k = 0; k < NH / 4; ++k) {
+                const uint4 x = hp[k];
+                h[4 * k] = x.x;
+                h[4 * k + 1] = x.y;
+                h[4 * k + 2] = x.z;
+                h[4 * k + 3] = x.w;
+            }
+        }
 #pragma unroll
         for (int sl = 0; sl < NS; ++sl) {
             g2[sl] = st.gu[q * Stage<S>::kPairs + ls.sp[sl]];
@@ -143,49 +165,47 @@ struct Staged {
         }
     }
 
-    __device__ __forceinline__ void apply(uint32_t tile_s, const LaneSlots<S>& ls, unsigned T, unsigned TP,
-                                          int ltp) const
+    __device__ __forceinline__ void apply(const LaneSlots<S>& ls) const
     {
-        const uint32_t base = tile_s + ((uint32_t)h.x << (ltp + 4));
-        const uint32_t px = ((uint32_t)h.x & 1u) << 2;
 #pragma unroll
-        for (int sl = 0; sl < NS; ++sl) {
-            const unsigned row = (unsigned)(h.x + ls.sr[sl]), pr = (unsigned)(h.y + ls.sp[sl]);
-            const bool on = ls.ok[sl] && row < T && pr < TP;
-            const uint32_t addr = base + ls.roff[sl] + ((pr ^ ls.xm[sl] ^ px) << 4);
-            rmw_pair(addr, on, g2[sl].x, g2[sl].y, gq[sl].x, gq[sl].y);
-        }
+        for (int sl = 0; sl < NS; ++sl)
+            rmw_pair(h[0] + ls.loff[sl], h[1 + sl], ls.lanebit, g2[sl].x, g2[sl].y, gq[sl].x, gq[sl].y);
     }
 };
 
 // Accumulate entries [b, e) of one sorted list into the warp's tile.  Rounds
 // of 32 entries: (1) each lane takes one entry (coalesced 16-byte loads) and
 // evaluates its 2S taps (degree-10 polynomials with uniform coefficients from
-// the constant bank) with the checkerboard signs folded in, into the stage;
-// (2) the warp walks the 32 entries; every lane updates its slots, each a
-// pair of horizontally adjacent cells read and written as one 16-byte value
-// (4 FMAs: u tap pair x complex v tap-visibility product).  Within one entry
-// the lanes' pairs are distinct and conflict-free; a __syncwarp orders
-// consecutive entries.  The stage is read-only during the walk, so the next
-// entry's header and taps are loaded before this entry's read-modify-write.
+// the constant bank) with the checkerboard signs folded in, and its header,
+// into the stage; (2) the warp walks the 32 entries; every lane updates its
+// slots, each a pair of horizontally adjacent cells read and written as one
+// 16-byte value (4 FMAs: u tap pair x complex v tap-visibility product).
+// Within one entry the lanes' pairs are distinct and conflict-free; a
+// __syncwarp orders consecutive entries.  The stage is read-only during the
+// walk, so the next entry's header and taps are loaded before this entry's
+// read-modify-write (two register sets, alternating).
 template <int S>
 __device__ __forceinline__ void warp_grid_range(const GridCfg& c, const float4* __restrict__ ent, uint32_t b,
                                                 uint32_t e, int u0, int v0, float4* tile4, Stage<S>& st,
                                                 const LaneSlots<S>& ls, int lane, int shift)
 {
-    constexpr int KP = Stage<S>::kPairs;
-    const unsigned T = (unsigned)c.T, TP = (unsigned)(c.T / 2);
-    const int ltp = c.log2T - 1;
+    constexpr int KP = Stage<S>::kPairs, NS = Stage<S>::kSlots, NH = Stage<S>::kHead;
+    const int TP = c.T / 2, P2 = pair_pitch(c.T);
     const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile4);
+    // each round's entries are loaded one round ahead
+    float4 r_next = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (b + lane < e) r_next = __ldg(ent + b + lane);
     for (uint32_t j0 = b; j0 < e; j0 += 32) {
         const uint32_t j = j0 + lane;
+        const float4 r = r_next;
+        if (j + 32 < e) r_next = __ldg(ent + j + 32);
         if (j < e) {
-            const float4 r = __ldg(ent + j);
             const int fu = first_cell(c, r.x), fv = first_cell(c, r.y);
             const float zu = __fmaf_rn(2.0f, __fsub_rn(__fsub_rn(r.x, c.half_s), (float)(fu - 1)), -1.0f);
             const float zv = __fmaf_rn(2.0f, __fsub_rn(__fsub_rn(r.y, c.half_s), (float)(fv - 1)), -1.0f);
-            const int lu = fu - u0;
+            const int lu = fu - u0, lv = fv - v0;
             const int odd = lu & 1;  // u0 is even: the parity of the tile column
+            const int pu = (lu - odd) / 2;
             float gu[S];
 #pragma unroll
             for (int t = 0; t < S; ++t) {
@@ -211,21 +231,38 @@ __device__ __forceinline__ void warp_grid_range(const GridCfg& c, const float4* 
                 const float o0 = 2 * t - 1 >= 0 ? gu[2 * t - 1 >= 0 ? 2 * t - 1 : 0] : 0.0f;
                 st.gu[lane * KP + t] = odd ? make_float2(o0, e0) : make_float2(e0, e1);
             }
-            st.head[lane] = make_int2(fv - v0, (lu - odd) / 2);
+            // header: first pair's shared address (wraps for footprints that
+            // start left of or above the tile; only in-tile pairs are used)
+            // and the in-tile lane bits of every slot: footprint rows
+            // [rlo, rhi) and pairs [plo, phi) lie inside the tile
+            const int rlo = max(0, -lv), rhi = min(S, c.T - lv);
+            const int plo = max(0, -pu), phi = min(KP, TP - pu);
+            const uint32_t pm = phi > plo ? (((1u << phi) - 1u) & ~((1u << plo) - 1u)) : 0u;
+            uint32_t wm[NH - 1];
+#pragma unroll
+            for (int k = 0; k < NH - 1; ++k) wm[k] = 0u;
+#pragma unroll
+            for (int sr = 0; sr < S; ++sr) {
+                const uint32_t rowbits = (sr >= rlo && sr < rhi) ? pm : 0u;
+                const int bit = sr * KP, wd = bit / 32, sh = bit % 32;
+                wm[wd] |= rowbits << sh;
+                if (sh + KP > 32 && wd + 1 < NS) wm[wd + 1] |= rowbits >> (32 - sh);
+            }
+            st.head[lane * NH] = tile_s + (uint32_t)(lv * P2 + pu) * 16u;
+#pragma unroll
+            for (int k = 0; k < NH - 1; ++k) st.head[lane * NH + 1 + k] = wm[k];
         }
         __syncwarp();
         const int cnt = (e - j0 < 32u) ? (int)(e - j0) : 32;
-        // two register sets, alternating: the next entry's stage values load
-        // while this entry's pairs are updated
         Staged<S> A, B;
         A.load(st, ls, 0);
         for (int q = 0;; q += 2) {
             if (q + 1 < cnt) B.load(st, ls, q + 1);
-            A.apply(tile_s, ls, T, TP, ltp);
+            A.apply(ls);
             __syncwarp();
             if (q + 1 >= cnt) break;
             if (q + 2 < cnt) A.load(st, ls, q + 2);
-            B.apply(tile_s, ls, T, TP, ltp);
+            B.apply(ls);
             __syncwarp();
             if (q + 2 >= cnt) break;
         }
@@ -257,16 +294,17 @@ __device__ __forceinline__ TileGeom tile_geom(const GridCfg& c, int k0, int64_t 
 // run of 16-byte accesses with no division.  The plane row of the pair is
 // (v0 + row) n + u0 + 2 pr, 16-byte aligned because n and u0 are even.
 struct TileWalk {
-    int pr, r0, dr, ltp;
+    int pr, r0, dr, p2;
 };
 
 __device__ __forceinline__ TileWalk tile_walk(const GridCfg& c, int lane)
 {
     TileWalk w;
-    w.ltp = c.log2T - 1;
-    w.pr = lane & ((1 << w.ltp) - 1);
-    w.r0 = lane >> w.ltp;
-    w.dr = 32 >> w.ltp;
+    const int ltp = c.log2T - 1;
+    w.p2 = pair_pitch(c.T);
+    w.pr = lane & ((1 << ltp) - 1);
+    w.r0 = lane >> ltp;
+    w.dr = 32 >> ltp;
     return w;
 }
 
@@ -281,7 +319,7 @@ __device__ __forceinline__ void store_tile(const GridCfg& c, const TileGeom& g, 
     float4* dst = reinterpret_cast<float4*>(P0 + (int64_t)(g.v0 + w.r0) * c.n + g.u0 + 2 * w.pr);
     const int64_t step = (int64_t)w.dr * (c.n / 2);
     for (int row = w.r0; row < g.wv; row += w.dr, dst += step)
-        *dst = kZero ? make_float4(0.f, 0.f, 0.f, 0.f) : tile4[pair_index(row, w.pr, w.ltp)];
+        *dst = kZero ? make_float4(0.f, 0.f, 0.f, 0.f) : tile4[row * w.p2 + w.pr];
 }
 
 // Initialise a tile copy: zeros, or the plane's current values (accumulating
@@ -296,10 +334,15 @@ __device__ __forceinline__ void init_tile(const GridCfg& c, const TileGeom& g, c
     for (int row = w.r0; row < c.T; row += w.dr, src += step) {
         float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
         if (col_ok && row < g.wv) x = *src;
-        tile4[pair_index(row, w.pr, w.ltp)] = x;
+        tile4[row * w.p2 + w.pr] = x;
     }
 }
 
+// Each CTA of W warps takes kTilesPerWarp * W consecutive tiles of the pass,
+// warp w the tiles w, w + W, ... of them (neighbours, so similar loads), and
+// loads the next tile's list ranges while it grids the current one; the
+// hardware hands CTAs out dynamically, which balances the uneven tiles.
+// Lane q < ch.count holds the range of list q for the tile.
 template <int S>
 __global__ void __launch_bounds__(256) k_grid_tiles(GridCfg c, ChunkList ch, int k0, int64_t ntl, int shift,
                                                     int accumulate, float2* __restrict__ planes,
@@ -307,49 +350,70 @@ __global__ void __launch_bounds__(256) k_grid_tiles(GridCfg c, ChunkList ch, int
 {
     extern __shared__ float4 smem4[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t tl = (int64_t)blockIdx.x * (blockDim.x >> 5) + wid;
-    if (tl >= ntl) return;
+    const int64_t nwt = blockDim.x >> 5;
+    const int64_t first = (int64_t)blockIdx.x * nwt * kTilesPerWarp;
+    const int64_t last = min(ntl, first + nwt * kTilesPerWarp);
+    int64_t tl = first + wid;
+    if (tl >= last) return;
     unsigned char* mine = reinterpret_cast<unsigned char*>(smem4) + (size_t)wid * warp_smem_bytes<S>(c.T);
     float4* tile4 = reinterpret_cast<float4*>(mine);
-    Stage<S>& st = *reinterpret_cast<Stage<S>*>(mine + (size_t)c.T * c.T * sizeof(float2));
-    const TileGeom g = tile_geom(c, k0, tl);
-    float2* P0 = planes + (int64_t)g.kl * c.n * c.n;
-
-    uint32_t nent = 0;
-    for (int q = 0; q < ch.count; ++q) nent += ch.off[q][g.tg + 1] - ch.off[q][g.tg];
-    if (nent > (uint32_t)kHeavyEntries && ch.count == 1) {
-        // many entries: hand the tile to k_grid_chunks as chunks of at most
-        // kHeavyEntries entries, which add into the plane; the tile starts
-        // at zero unless this pass accumulates onto earlier chunks
-        const uint32_t nchunks = (nent + kHeavyEntries - 1) / kHeavyEntries;
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(heavy, nchunks);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base + nchunks <= heavy_cap) {
-            for (uint32_t k = lane; k < nchunks; k += 32) {
-                heavy[1 + 2 * (base + k)] = (uint32_t)tl;
-                heavy[2 + 2 * (base + k)] = k;
-            }
-            if (!accumulate) store_tile<true>(c, g, P0, nullptr, lane);
-            return;
-        }
-        // no room in the chunk list: mark the reserved slots that do exist as
-        // empty, and grid the tile here (correct, slower)
-        for (uint32_t k = base + lane; k < heavy_cap; k += 32) heavy[1 + 2 * k] = 0xffffffffu;
-    }
-    if (nent == 0 && !accumulate) {
-        store_tile<true>(c, g, P0, nullptr, lane);
-        return;
-    }
-    init_tile(c, g, P0, tile4, accumulate != 0, lane);
-    __syncwarp();
+    Stage<S>& st = *reinterpret_cast<Stage<S>*>(mine + (size_t)c.T * pair_pitch(c.T) * sizeof(float4));
     LaneSlots<S> ls;
-    ls.init(lane, c.log2T - 1);
-    for (int q = 0; q < ch.count; ++q)
-        warp_grid_range<S>(c, ch.ent[q], ch.off[q][g.tg], ch.off[q][g.tg + 1], g.u0, g.v0, tile4, st, ls, lane,
-                           shift);
-    __syncwarp();
-    store_tile<false>(c, g, P0, tile4, lane);
+    ls.init(lane, pair_pitch(c.T));
+
+    auto fetch = [&](int64_t t, uint32_t& rb, uint32_t& re) {
+        rb = re = 0;
+        if (t < last && lane < ch.count) {
+            const int64_t tg = (int64_t)k0 * c.ntp + t;
+            rb = __ldg(ch.off[lane] + tg);
+            re = __ldg(ch.off[lane] + tg + 1);
+        }
+    };
+    uint32_t nb, ne;
+    fetch(tl, nb, ne);
+    for (; tl < last; tl += nwt) {
+        const uint32_t cb = nb, ce = ne;
+        fetch(tl + nwt, nb, ne);
+        const TileGeom g = tile_geom(c, k0, tl);
+        float2* P0 = planes + (int64_t)g.kl * c.n * c.n;
+        uint32_t nent = ce - cb;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nent += __shfl_xor_sync(0xffffffffu, nent, o);
+
+        if (nent > (uint32_t)kHeavyEntries && ch.count == 1) {
+            // many entries: hand the tile to k_grid_chunks as chunks of at most
+            // kHeavyEntries entries, which add into the plane; the tile starts
+            // at zero unless this pass accumulates onto earlier chunks
+            const uint32_t nchunks = (nent + kHeavyEntries - 1) / kHeavyEntries;
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(heavy, nchunks);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base + nchunks <= heavy_cap) {
+                for (uint32_t k = lane; k < nchunks; k += 32) {
+                    heavy[1 + 2 * (base + k)] = (uint32_t)tl;
+                    heavy[2 + 2 * (base + k)] = k;
+                }
+                if (!accumulate) store_tile<true>(c, g, P0, nullptr, lane);
+                continue;
+            }
+            // no room in the chunk list: mark the reserved slots that do exist
+            // as empty, and grid the tile here (correct, slower)
+            for (uint32_t k = base + lane; k < heavy_cap; k += 32) heavy[1 + 2 * k] = 0xffffffffu;
+        }
+        if (nent == 0) {
+            if (!accumulate) store_tile<true>(c, g, P0, nullptr, lane);
+            continue;
+        }
+        init_tile(c, g, P0, tile4, accumulate != 0, lane);
+        __syncwarp();
+        for (int q = 0; q < ch.count; ++q) {
+            const uint32_t b = __shfl_sync(0xffffffffu, cb, q), e = __shfl_sync(0xffffffffu, ce, q);
+            if (e > b) warp_grid_range<S>(c, ch.ent[q], b, e, g.u0, g.v0, tile4, st, ls, lane, shift);
+        }
+        __syncwarp();
+        store_tile<false>(c, g, P0, tile4, lane);
+        __syncwarp();  // the next tile's init overwrites the tile copy
+    }
 }
 
 // Chunks of the tiles with many entries: one warp per chunk, private tile in
@@ -365,9 +429,9 @@ __global__ void __launch_bounds__(256) k_grid_chunks(GridCfg c, ChunkList ch, in
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     unsigned char* mine = reinterpret_cast<unsigned char*>(smem4) + (size_t)wid * warp_smem_bytes<S>(c.T);
     float4* tile4 = reinterpret_cast<float4*>(mine);
-    Stage<S>& st = *reinterpret_cast<Stage<S>*>(mine + (size_t)c.T * c.T * sizeof(float2));
+    Stage<S>& st = *reinterpret_cast<Stage<S>*>(mine + (size_t)c.T * pair_pitch(c.T) * sizeof(float4));
     LaneSlots<S> ls;
-    ls.init(lane, c.log2T - 1);
+    ls.init(lane, pair_pitch(c.T));
     const uint32_t count = min(heavy[0], heavy_cap);
     const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
     for (uint32_t it = blockIdx.x * (blockDim.x >> 5) + wid; it < count; it += nwarps) {
@@ -389,7 +453,7 @@ __global__ void __launch_bounds__(256) k_grid_chunks(GridCfg c, ChunkList ch, in
             float4* dst = reinterpret_cast<float4*>(P0 + (int64_t)(g.v0 + w.r0) * c.n + g.u0 + 2 * w.pr);
             const int64_t step = (int64_t)w.dr * (c.n / 2);
             for (int row = w.r0; row < g.wv; row += w.dr, dst += step) {
-                const float4 x = tile4[pair_index(row, w.pr, w.ltp)];
+                const float4 x = tile4[row * w.p2 + w.pr];
                 if (x.x != 0.f || x.y != 0.f || x.z != 0.f || x.w != 0.f) atomicAdd(dst, x);
             }
         }
@@ -406,7 +470,7 @@ cudaError_t allow_smem(K kernel, size_t bytes)
 
 template <int S>
 cudaError_t launch_grid_s(const GridCfg& c, const ChunkList& ch, int k0, int nk, bool shift, bool accumulate,
-                          float2* planes, uint32_t* heavy, cudaStream_t s)
+                          float2* planes, uint32_t* heavy, size_t heavy_words, cudaStream_t s)
 {
     const int64_t ntl = (int64_t)nk * c.ntp;
     if (ntl <= 0) return cudaSuccess;
@@ -414,14 +478,16 @@ cudaError_t launch_grid_s(const GridCfg& c, const ChunkList& ch, int k0, int nk,
     const int wl = light_warps(c.T);
     const int64_t nblocks = (ntl + wl - 1) / wl;
     if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    // heavy: [count, (tile, chunk) pairs]; it has 1 + ntl words
-    const uint32_t cap = (uint32_t)(ntl / 2);
+    // heavy: [count, (tile, chunk) pairs]
+    const size_t pairs = (heavy_words - 1) / 2;
+    const uint32_t cap = (uint32_t)(pairs < 0x7fffffffu ? pairs : 0x7fffffffu);
     cudaError_t e = cudaMemsetAsync(heavy, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     if ((e = allow_smem(k_grid_tiles<S>, tile_bytes * wl)) != cudaSuccess) return e;
     if ((e = allow_smem(k_grid_chunks<S>, tile_bytes * wl)) != cudaSuccess) return e;
-    k_grid_tiles<S><<<(unsigned)nblocks, 32 * wl, tile_bytes * wl, s>>>(c, ch, k0, ntl, shift ? 1 : 0,
-                                                                       accumulate ? 1 : 0, planes, heavy, cap);
+    const unsigned tile_blocks = (unsigned)((nblocks + kTilesPerWarp - 1) / kTilesPerWarp);
+    k_grid_tiles<S><<<tile_blocks, 32 * wl, tile_bytes * wl, s>>>(c, ch, k0, ntl, shift ? 1 : 0, accumulate ? 1 : 0,
+                                                                  planes, heavy, cap);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_chunks<S>, 32 * wl, tile_bytes * wl)) !=
@@ -534,12 +600,23 @@ cudaError_t launch_fit_taps(const GridCfg& c, double kernel_param, float* coef, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_grid(const GridCfg& c, const ChunkList& ch, int k0, int nk, bool shift_sign,
-                        bool accumulate, uint32_t* heavy, float2* planes, cudaStream_t s)
+// Every chunk holds more than kHeavyEntries / 2 entries on average (a heavy
+// tile of n > kHeavyEntries entries makes ceil(n / kHeavyEntries) < 2 n /
+// kHeavyEntries chunks), so a pass over E entries lists fewer than
+// 2 E / kHeavyEntries chunks.
+size_t heavy_words_for(int64_t max_entries)
 {
+    const int64_t chunks = 2 * max_entries / kHeavyEntries + 1;
+    return 1 + 2 * (size_t)(chunks > 0 ? chunks : 1);
+}
+
+cudaError_t launch_grid(const GridCfg& c, const ChunkList& ch, int k0, int nk, bool shift_sign,
+                        bool accumulate, uint32_t* heavy, size_t heavy_words, float2* planes, cudaStream_t s)
+{
+    if (!heavy || heavy_words < 1) return cudaErrorInvalidValue;
     switch (c.S) {
 #define RICK_GRID_CASE(SS) \
-    case SS: return launch_grid_s<SS>(c, ch, k0, nk, shift_sign, accumulate, planes, heavy, s);
+    case SS: return launch_grid_s<SS>(c, ch, k0, nk, shift_sign, accumulate, planes, heavy, heavy_words, s);
         RICK_GRID_CASE(1) RICK_GRID_CASE(2) RICK_GRID_CASE(3) RICK_GRID_CASE(4)
         RICK_GRID_CASE(5) RICK_GRID_CASE(6) RICK_GRID_CASE(7) RICK_GRID_CASE(8)
         RICK_GRID_CASE(9) RICK_GRID_CASE(10) RICK_GRID_CASE(11) RICK_GRID_CASE(12)

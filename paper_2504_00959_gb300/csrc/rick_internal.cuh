@@ -172,8 +172,13 @@ cudaError_t launch_scatter(const GridCfg& c, const float* u, const float* v, con
                            const float* wt, const float2* vis, int64_t m, const uint32_t* density,
                            uint32_t* cursor, float4* entries, Counters* ctr, double* chan_sw, cudaStream_t s);
 // heavy: scratch of 1 + nk * ntp uint32 (count + list of tiles with many entries)
+// heavy: scratch of heavy_words words for the list of chunks of heavily
+// populated tiles (1 + 2 per chunk; a tile that does not fit is gridded by
+// one warp, correct but slower).  heavy_words_for() gives the size that never
+// overflows for a pass over at most max_entries entries.
 cudaError_t launch_grid(const GridCfg& c, const ChunkList& chunks, int k0, int nk, bool shift_sign,
-                        bool accumulate, uint32_t* heavy, float2* planes, cudaStream_t s);
+                        bool accumulate, uint32_t* heavy, size_t heavy_words, float2* planes, cudaStream_t s);
+size_t heavy_words_for(int64_t max_entries);
 cudaError_t launch_taper(const GridCfg& c, double kernel_param, float* taper, cudaStream_t s);
 // Fit the tap polynomials (coef: float[S][kPolyTerms]) and report the largest
 // binary32 evaluation error relative to the kernel's peak in *max_err.
@@ -274,6 +279,8 @@ struct rick_imager {
     uint32_t* b_off;                 // device [ntiles + 1]
     float4* b_ent;                   // device entries
     int64_t b_cap;
+    uint32_t* b_heavy;               // gridder's heavy-chunk list for b_cap entries
+    size_t b_heavy_words;
     cudaGraphExec_t graph;
     const void* graph_key[7];
     int64_t graph_m;

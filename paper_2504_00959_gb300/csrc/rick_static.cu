@@ -180,7 +180,8 @@ extern "C" rick_status rick_grid_planes_static(const rick_params* p, const float
         cl.ent[0] = ent;
         cl.count = 1;
         // the scatter cursors are free again: they hold the gridder's heavy-tile list
-        e = launch_grid(c, cl, 0, c.nw, false, false, cursor, reinterpret_cast<float2*>(planes), stream);
+        e = launch_grid(c, cl, 0, c.nw, false, false, cursor, (size_t)ntiles + 1, reinterpret_cast<float2*>(planes),
+                        stream);
     }
     if (e != cudaSuccess) {
         set_msg(err, err_len, "rick_grid_planes_static launch: %s", cudaGetErrorString(e));

@@ -76,3 +76,36 @@ def test_static_scratch_rejects_sizes_beyond_the_limit(rick):
     status = _call(rick, params, prob, planes, err)
     assert status == 1  # RICK_ERR_ARG
     assert "limit" in err.value.decode()
+
+
+def test_static_scratch_hot_tile_beyond_the_chunk_list(rick):
+    """2e5 measurements inside one cell of a 128^2 x 4-plane grid: the static
+    scratch lists at most (tiles + 1) / 2 chunks, far fewer than that tile's,
+    so the gridder grids it with one warp; it must agree with the allocating
+    path, which splits it into chunks (1e-4 of the largest cell: the hot cell
+    sums 2e5 FP32 terms in another order)."""
+    n = 128
+    prob = synth.disk_problem(n, 4, 20000, synth.KERNEL_KB, 7, 3.0, 50.0, 11)
+    du = 1 / (n * prob["params"]["pixel_rad"])
+    g = torch.Generator().manual_seed(5)
+    hot = 200000
+    prob = dict(params=prob["params"],
+                u=torch.cat([prob["u"], (3.2 + 0.3 * torch.rand(hot, generator=g)) * du]).cuda(),
+                v=torch.cat([prob["v"], (-1.7 + 0.3 * torch.rand(hot, generator=g)) * du]).cuda(),
+                w=torch.cat([prob["w"], torch.full((hot,), 1.0)]).cuda(),
+                wt=torch.ones(20000 + hot, device="cuda"),
+                vis=torch.cat([prob["vis"], torch.complex(torch.randn(hot, generator=g),
+                                                          torch.randn(hot, generator=g))]).cuda())
+    params = dict(prob["params"], flags=synth.FLAG_REAL)
+    im = rick.Imager(params)
+    im.grid(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"])
+    ref = im.grid_planes()
+    torch.cuda.synchronize()
+    im.close()
+    out = torch.full((4, n, n), float("nan"), dtype=torch.complex64, device="cuda")
+    err = ctypes.create_string_buffer(512)
+    assert _call(rick, params, prob, out, err) == 0, err.value.decode()
+    torch.cuda.synchronize()
+    assert torch.isfinite(out).all().item()
+    diff = torch.max(torch.abs(out - ref)).item()
+    assert diff <= 1e-4 * torch.max(torch.abs(ref)).item(), diff

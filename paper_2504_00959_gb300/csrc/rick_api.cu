@@ -481,6 +481,7 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
         if (!(worst <= 2e-6)) return cleanup(RICK_ERR_ARG);  // kernel too sharp for degree-10 taps
         for (int t = 0; t < kMaxSupport; ++t)
             for (int j = 0; j < kPolyTerms; ++j) h->cfg.coef[t][j] = (t < c.S) ? coef[t * kPolyTerms + j] : 0.0f;
+        set_tap_sum(h->cfg);
     }
     cufftHandle plan;
     s = get_plan(h, G, &plan);

@@ -43,6 +43,8 @@ struct GridCfg {
     // is g(t + 1 - S/2 - d), d = frac(p - S/2); as a polynomial in z = 2d - 1:
     // g_t = sum_j coef[t][j] z^j (fitted once per handle, see k_fit_taps)
     float coef[kMaxSupport][kPolyTerms];
+    // sum_t g_t = sum_j sumc[j] z^j: the tap sum of one axis (set_tap_sum)
+    float sumc[kPolyTerms];
 };
 
 // Placement of one measurement: plane, first footprint cell, continuous
@@ -122,20 +124,26 @@ __device__ __forceinline__ void eval_taps(const GridCfg& c, float p, int f, floa
     }
 }
 
-// Sum of the S taps of one axis (same Horner evaluation as eval_taps and the
-// gridder, tap by tap, so normalised taps sum to 1 to binary32 rounding).
+// Sum of the S taps of one axis: one Horner evaluation of the sum of the tap
+// polynomials (normalised taps then sum to 1 to a few binary32 roundings).
 __device__ __forceinline__ float tap_sum(const GridCfg& c, float p, int f)
 {
     const float d = __fsub_rn(__fsub_rn(p, c.half_s), (float)(f - 1));
     const float z = __fmaf_rn(2.0f, d, -1.0f);
-    float s = 0.0f;
-    for (int t = 0; t < c.S; ++t) {
-        float a = c.coef[t][kPolyTerms - 1];
+    float s = c.sumc[kPolyTerms - 1];
 #pragma unroll
-        for (int j = kPolyTerms - 2; j >= 0; --j) a = __fmaf_rn(a, z, c.coef[t][j]);
-        s += a;
-    }
+    for (int j = kPolyTerms - 2; j >= 0; --j) s = __fmaf_rn(s, z, c.sumc[j]);
     return s;
+}
+
+// Coefficients of the tap-sum polynomial from the S tap polynomials (host).
+inline void set_tap_sum(GridCfg& c)
+{
+    for (int j = 0; j < kPolyTerms; ++j) {
+        double s = 0.0;
+        for (int t = 0; t < c.S; ++t) s += (double)c.coef[t][j];
+        c.sumc[j] = (float)s;
+    }
 }
 
 // Whether a measurement with finite placement also has a finite weight and value.

@@ -98,23 +98,46 @@ __global__ void __launch_bounds__(kPrepThreads) k_density(GridCfg c, Inputs in, 
     });
 }
 
+// Tiles touched by the footprint of a placed measurement: t[0] always, t[1]
+// (right neighbour), t[2] (lower), t[3] (lower right) when the footprint
+// straddles; -1 otherwise.
+__device__ __forceinline__ void footprint_tiles(const GridCfg& c, const Place& p, int64_t (&t)[4])
+{
+    const int tu0 = p.fu >> c.log2T, tu1 = (p.fu + c.S - 1) >> c.log2T;
+    const int tv0 = p.fv >> c.log2T, tv1 = (p.fv + c.S - 1) >> c.log2T;
+    const int64_t base = (int64_t)p.k * c.ntp;
+    t[0] = base + tv0 * c.ntu + tu0;
+    t[1] = tu1 != tu0 ? base + tv0 * c.ntu + tu1 : -1;
+    t[2] = tv1 != tv0 ? base + tv1 * c.ntu + tu0 : -1;
+    t[3] = (tu1 != tu0 && tv1 != tv0) ? base + tv1 * c.ntu + tu1 : -1;
+}
+
+// Measurements per thread and loop trip: their loads, and then their atomics,
+// are in flight together.
+constexpr int kVisPerThread = 4;
+
 __global__ void __launch_bounds__(kPrepThreads) k_count(GridCfg c, Inputs in, int64_t m,
                                                         uint32_t* __restrict__ counts)
 {
     for_each_segment(c, m, [&](int chan, int64_t i0, int64_t i1) {
-        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            Place p;
-            float wi;
-            float2 V;
-            if (!load_and_place(c, in, i, chan, p, wi, V)) continue;
-            const int tu0 = p.fu >> c.log2T, tu1 = (p.fu + c.S - 1) >> c.log2T;
-            const int tv0 = p.fv >> c.log2T, tv1 = (p.fv + c.S - 1) >> c.log2T;
-            uint32_t* base = counts + (int64_t)p.k * c.ntp;
-            atomicAdd(base + tv0 * c.ntu + tu0, 1u);
-            if (tu1 != tu0) atomicAdd(base + tv0 * c.ntu + tu1, 1u);
-            if (tv1 != tv0) {
-                atomicAdd(base + tv1 * c.ntu + tu0, 1u);
-                if (tu1 != tu0) atomicAdd(base + tv1 * c.ntu + tu1, 1u);
+        for (int64_t ib = i0 + threadIdx.x; ib < i1; ib += (int64_t)kVisPerThread * blockDim.x) {
+            Place p[kVisPerThread];
+            bool ok[kVisPerThread];
+#pragma unroll
+            for (int q = 0; q < kVisPerThread; ++q) {
+                const int64_t i = ib + (int64_t)q * blockDim.x;
+                float wi;
+                float2 V;
+                ok[q] = i < i1 && load_and_place(c, in, i, chan, p[q], wi, V);
+            }
+#pragma unroll
+            for (int q = 0; q < kVisPerThread; ++q) {
+                if (!ok[q]) continue;
+                int64_t t[4];
+                footprint_tiles(c, p[q], t);
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (t[r] >= 0) atomicAdd(counts + t[r], 1u);
             }
         }
     });
@@ -153,41 +176,52 @@ __global__ void __launch_bounds__(kPrepThreads) k_scatter(GridCfg c, Inputs in, 
     unsigned gridded = 0, dropped = 0, nent = 0;
     for_each_segment(c, m, [&](int chan, int64_t i0, int64_t i1) {
         float sw = 0.0f;
-        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            Place p;
-            float wi;
-            float2 V;
-            if (!load_and_place(c, in, i, chan, p, wi, V)) {
-                ++dropped;
-                continue;
-            }
-            if (c.uniform) {
-                uint32_t cnt = __ldg(density + (int64_t)nearest_cell(c, p.pv) * c.n + nearest_cell(c, p.pu));
-                wi = wi / (float)cnt;
-            }
-            // the gridder reads the visibility already weighted and divided by the
-            // two tap sums (normalised taps), once per measurement here instead of
-            // once per (measurement, tile) entry there
-            const float scale = wi / (tap_sum(c, p.pu, p.fu) * tap_sum(c, p.pv, p.fv));
-            const float4 rec = make_float4(p.pu, p.pv, scale * V.x, scale * V.y);
-            sw += wi;
-            ++gridded;
-            const int tu0 = p.fu >> c.log2T, tu1 = (p.fu + c.S - 1) >> c.log2T;
-            const int tv0 = p.fv >> c.log2T, tv1 = (p.fv + c.S - 1) >> c.log2T;
-            uint32_t* base = cursor + (int64_t)p.k * c.ntp;
-            entries[atomicAdd(base + tv0 * c.ntu + tu0, 1u)] = rec;
-            ++nent;
-            if (tu1 != tu0) {
-                entries[atomicAdd(base + tv0 * c.ntu + tu1, 1u)] = rec;
-                ++nent;
-            }
-            if (tv1 != tv0) {
-                entries[atomicAdd(base + tv1 * c.ntu + tu0, 1u)] = rec;
-                ++nent;
-                if (tu1 != tu0) {
-                    entries[atomicAdd(base + tv1 * c.ntu + tu1, 1u)] = rec;
-                    ++nent;
+        for (int64_t ib = i0 + threadIdx.x; ib < i1; ib += (int64_t)kVisPerThread * blockDim.x) {
+            Place p[kVisPerThread];
+            float wi[kVisPerThread];
+            float2 V[kVisPerThread];
+            bool ok[kVisPerThread];
+#pragma unroll
+            for (int q = 0; q < kVisPerThread; ++q) {
+                const int64_t i = ib + (int64_t)q * blockDim.x;
+                ok[q] = false;
+                if (i < i1) {
+                    ok[q] = load_and_place(c, in, i, chan, p[q], wi[q], V[q]);
+                    if (!ok[q]) ++dropped;
                 }
+            }
+            // the gridder reads the visibility already weighted and divided by
+            // the two tap sums (normalised taps), once per measurement here
+            // instead of once per (measurement, tile) entry there
+            float4 rec[kVisPerThread];
+            uint32_t slot[kVisPerThread][4];
+            int64_t t[kVisPerThread][4];
+#pragma unroll
+            for (int q = 0; q < kVisPerThread; ++q) {
+                if (!ok[q]) continue;
+                if (c.uniform) {
+                    const uint32_t cnt =
+                        __ldg(density + (int64_t)nearest_cell(c, p[q].pv) * c.n + nearest_cell(c, p[q].pu));
+                    wi[q] = wi[q] / (float)cnt;
+                }
+                const float scale = wi[q] / (tap_sum(c, p[q].pu, p[q].fu) * tap_sum(c, p[q].pv, p[q].fv));
+                rec[q] = make_float4(p[q].pu, p[q].pv, scale * V[q].x, scale * V[q].y);
+                sw += wi[q];
+                ++gridded;
+                footprint_tiles(c, p[q], t[q]);
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (t[q][r] >= 0) slot[q][r] = atomicAdd(cursor + t[q][r], 1u);
+            }
+#pragma unroll
+            for (int q = 0; q < kVisPerThread; ++q) {
+                if (!ok[q]) continue;
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (t[q][r] >= 0) {
+                        entries[slot[q][r]] = rec[q];
+                        ++nent;
+                    }
             }
         }
         const float tot = block_sum(sw);

@@ -165,6 +165,7 @@ extern "C" rick_status rick_grid_planes_static(const rick_params* p, const float
         ds.have_coef = true;
     }
     memcpy(c.coef, ds.coef, sizeof(c.coef));
+    set_tap_sum(c);
 
     const float2* vis2 = reinterpret_cast<const float2*>(vis);
     e = cudaMemsetAsync(ctr, 0, sizeof(Counters), stream);

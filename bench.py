@@ -198,11 +198,15 @@ def main():
     ap.add_argument("--nvis", type=int, default=10_000_000)
     ap.add_argument("--nw", type=int, default=32, help="w-planes (profiling cases)")
     ap.add_argument("--tile", type=int, default=0, help="gridder tile side (0 = automatic)")
+    ap.add_argument("--fold", action="store_true",
+                    help="Hermitian fold (real image): measurements with w < 0 mirrored, half the w-planes "
+                         "over [0, max |w|] at the same plane spacing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--workload", choices=["wstack", "channels"], default="wstack",
+    ap.add_argument("--workload", choices=["wstack", "channels", "adjoint"], default="wstack",
                     help="wstack: the 4096^2 / 32-plane / 1e7 image (default); channels: 64 channels "
-                         "batched vs imaged one by one")
+                         "batched vs imaged one by one; adjoint: image + loss gradient through the "
+                         "adjoint degridder on the same workload")
     args = ap.parse_args()
 
     import torch
@@ -215,6 +219,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "channels":
         return run_channels(args, rank, world)
+    if args.workload == "adjoint":
+        return run_adjoint(args, rank, world)
 
     import synth
     import paper_2504_00959_gb300 as rick
@@ -228,6 +234,10 @@ def main():
 
     prob = synth.config2(device=dev, m=args.nvis, nw=args.nw)
     params = dict(prob["params"], flags=synth.FLAG_CORRECT | synth.FLAG_REAL, tile=args.tile)
+    if args.fold:
+        wabs = max(abs(params["w_min"]), abs(params["w_max"]))
+        params = dict(params, nw=max(args.nw // 2, 1), w_min=0.0, w_max=wabs,
+                      flags=params["flags"] | synth.FLAG_FOLD)
     im = rick.Imager(params, device=dev)
     img = torch.empty((params["n"], params["n"]), dtype=torch.float32, device=dev)
     m = prob["u"].numel()
@@ -322,7 +332,9 @@ def main():
         "metric": METRIC, "value": value, "unit": "vis/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": DATA,
-        "config": {"workload": WORKLOAD, "n": n, "nw": nw, "nvis": m, "kernel": "kaiser-bessel", "support": 7,
+        "config": {"workload": WORKLOAD + ("; Hermitian fold: %d w-planes over [0, max |w|]" % nw if args.fold
+                                           else ""),
+                   "n": n, "nw": nw, "nvis": m, "kernel": "kaiser-bessel", "support": 7,
                    "tile": st["tile"], "plane_group": st["plane_group"],
                    "l2": "inputs larger than L2 (4.3 GB of planes written and read every step)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -437,6 +449,87 @@ def run_channels(args, rank, world):
             "loop_ms_per_step": t_loop, "speedup_vs_loop": t_loop / t_batch,
             "max_rel_diff_batch_vs_loop": err, "energy_j_batch": e_batch, "energy_j_loop": e_loop,
             "green_productivity_eq4": gp}))
+
+
+def run_adjoint(args, rank, world):
+    """Differentiable imaging on the 4096^2 / 32-plane / 1e7 workload: one
+    step is the dirty image D(V) and the gradient of L = ||D - t||^2 with
+    respect to V through the hand-written adjoint (torch.autograd.Function
+    whose backward recomputes the w-planes from dL/dD and degrids them).
+    The target t is the image of the same measurements with every
+    visibility scaled by 1 + 0.1 N(0, 1) (a perturbed sky)."""
+    import torch
+
+    import synth
+    import paper_2504_00959_gb300 as rick
+    from paper_2504_00959_gb300 import build as rick_build
+    rick_build.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    prob = synth.config2(device=dev, m=args.nvis, nw=args.nw)
+    params = dict(prob["params"], flags=synth.FLAG_CORRECT | synth.FLAG_REAL, tile=args.tile)
+    im = rick.Imager(params, device=dev)
+    m = prob["u"].numel()
+    n, nw = params["n"], params["nw"]
+    g = torch.Generator(device=dev).manual_seed(synth.BASE_SEED + 5)
+    scale = 1.0 + 0.1 * torch.randn(m, device=dev, generator=g)
+    with torch.no_grad():
+        target = rick.dirty_image(prob["vis"] * scale, prob["u"], prob["v"], prob["w"], prob["wt"], im).clone()
+    vis = prob["vis"].clone().requires_grad_(True)
+
+    def step():
+        vis.grad = None
+        d = rick.dirty_image(vis, prob["u"], prob["v"], prob["w"], prob["wt"], im)
+        loss = ((d - target) ** 2).sum()
+        loss.backward()
+        return loss
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", ""))
+    uuid = uuid if uuid.startswith("GPU-") else ("GPU-" + uuid if uuid else "")
+    nvml = Nvml(uuid) if uuid else None
+    clocks = ClockSampler(uuid if uuid else 0)
+    im.set_timing(True)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    clocks.start()
+    j0 = nvml.energy_mj() if nvml else None
+    s0.record()
+    for _ in range(args.steps):
+        step()
+    s1.record()
+    torch.cuda.synchronize()
+    j1 = nvml.energy_mj() if nvml else None
+    clk = clocks.stop()
+    ms = s0.elapsed_time(s1) / max(args.steps, 1)
+    tm = im.timing()
+    st = im.stats()
+    peak, peak_kind = _peaks()
+    # backward = spread (8 B/cell written) + forward FFT (two passes, read +
+    # write) + gather (planes read once, 16 B of u, v, w, weight + 8 B of
+    # gradient per measurement) + the measurement sort (two passes of 16 B)
+    deg_ms = tm["degrid_ms"] / max(tm["degrid_calls"], 1)
+    deg_bytes = 8.0 * nw * n * n + 32.0 * nw * n * n + 8.0 * nw * n * n + 24.0 * m + 32.0 * m
+    fwd_ms = (tm["prep_ms"] + tm["grid_ms"] + tm["fft_ms"] + tm["stack_ms"]) / max(tm["stack_calls"], 1)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "visibilities/sec, dirty image + loss gradient through the adjoint degridder",
+            "value": m / (ms / 1e3), "unit": "vis/s", "higher_is_better": True, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "dtype": "f32", "data": DATA,
+            "config": {"workload": "differentiable imaging: " + WORKLOAD, "n": n, "nw": nw, "nvis": m,
+                       "tile": st["tile"], "plane_group": st["plane_group"],
+                       "loss": "sum (D - t)^2, t = image of V (1 + 0.1 N(0,1))"},
+            "phases": {"forward_ms": fwd_ms, "backward_degrid_ms": deg_ms,
+                       "backward_algorithmic_gb": deg_bytes / 1e9,
+                       "backward_gbs": deg_bytes / deg_ms / 1e6,
+                       "backward_frac_of_" + peak_kind: deg_bytes / deg_ms / 1e6 / peak},
+            "energy_j_per_solution": (j1 - j0) / 1e3 / max(args.steps, 1) if j0 is not None and j1 is not None
+            else None,
+            "gpu_launches": int(tm["kernel_launches"]), "clocks": clk}))
+    im.close()
 
 
 def run_reference(args, rank, world):

@@ -56,6 +56,11 @@ typedef int32_t rick_status;
 #define RICK_REAL_IMAGE 2u     /* output Re(image) as float[n*n]; else complex float[2*n*n] */
 #define RICK_APPLY_N 4u        /* multiply the image by n = sqrt(1 - l^2 - m^2) (Eq. 1 LHS) */
 #define RICK_UNIFORM_WEIGHT 8u /* weight / (gridded measurements sharing the nearest cell) */
+#define RICK_HERMITIAN_FOLD 32u /* real images only (with RICK_REAL_IMAGE): a measurement with
+                                  w < 0 is imaged as its Hermitian mirror (-u, -v, -w, conj V),
+                                  which leaves Re(image) unchanged, so the w-planes need only
+                                  cover the folded range (w_min, w_max >= 0 typically: half the
+                                  planes for the same plane spacing) */
 
 /* Problem statement of Sec. 2.1: grid size, pixel scale, w-planes, kernel.
  * n: grid side, even, >= 2*support.  nw >= 1.  w_max > w_min when nw > 1.

@@ -9,15 +9,17 @@ arithmetic is in that C file.
 Problem parameters are passed as a mapping with the keys ``n``, ``nw``,
 ``pixel_rad``, ``w_min``, ``w_max``, ``kernel`` (0 Gaussian, 1 Kaiser-Bessel),
 ``support``, ``kernel_param`` (sigma in cells or beta; 0 = default) and
-``flags`` (bit 1 grid correction, 4 multiply by n, 8 uniform weighting).
+``flags`` (bit 1 grid correction, 4 multiply by n, 8 uniform weighting, 32
+Hermitian fold of the measurements with w < 0).
 
 Pins (tests/test_oracle_pins.py): FFT against numpy, I0 against scipy, taper
 against the closed-form Fourier transforms of the truncated Gaussian and of
 the Kaiser-Bessel window, the delta-kernel special case against
 numpy.fft.ifft2, point source / sum / Hermitian / linearity invariants, the
 single-measurement closed form, the direct DFT with the exact w-term within
-the derived w-quantisation + aliasing bound, and the adjoint's dot-product
-identity and dense-matrix check.
+the derived w-quantisation + aliasing bound, the adjoint's dot-product
+identity and dense-matrix check, and the Hermitian fold against the unfolded
+imager on mirrored w-planes.
 """
 import ctypes
 import os
@@ -32,6 +34,7 @@ FLAG_CORRECT = 1
 FLAG_REAL = 2
 FLAG_APPLY_N = 4
 FLAG_UNIFORM = 8
+FLAG_FOLD = 32
 
 _lib = None
 

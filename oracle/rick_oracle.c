@@ -429,6 +429,51 @@ int oracle_taper(int n, int kernel, int support, double kparam, double* taper)
 #define OR_FLAG_CORRECT 1u
 #define OR_FLAG_APPLY_N 4u
 #define OR_FLAG_UNIFORM 8u
+#define OR_FLAG_FOLD 32u
+
+/* Hermitian fold (real images): the visibility of a real sky satisfies
+ * V(-u, -v, -w) = conj V(u, v, w), and a measurement imaged as its mirror
+ * (-u, -v, -w, conj V) adds the complex conjugate of its own image term
+ * (Eq. 1 and Eq. 3 with the mirrored cells: the plane transform of a mirrored,
+ * conjugated grid is the conjugate of the plane image, and the screen
+ * exp(2 pi i (-w)(n-1)) is the conjugate screen), so the real part of the
+ * image is unchanged.  With the flag, every measurement with w < 0 is
+ * replaced by its mirror before anything else; binary32 negation is exact.
+ * The copies are released with or_unfold. */
+typedef struct {
+    float *u, *v, *w, *vis;
+} or_fold_buf;
+
+static void or_fold(unsigned flags, int64_t m, const float** u, const float** v, const float** w,
+                    const float** vis, or_fold_buf* b)
+{
+    b->u = b->v = b->w = b->vis = NULL;
+    if (!(flags & OR_FLAG_FOLD) || m <= 0) return;
+    b->u = (float*)malloc(sizeof(float) * (size_t)m);
+    b->v = (float*)malloc(sizeof(float) * (size_t)m);
+    b->w = (float*)malloc(sizeof(float) * (size_t)m);
+    b->vis = (float*)malloc(sizeof(float) * 2 * (size_t)m);
+    for (int64_t i = 0; i < m; ++i) {
+        const int mirror = (*w)[i] < 0.0f;
+        b->u[i] = mirror ? -(*u)[i] : (*u)[i];
+        b->v[i] = mirror ? -(*v)[i] : (*v)[i];
+        b->w[i] = mirror ? -(*w)[i] : (*w)[i];
+        b->vis[2 * i] = (*vis)[2 * i];
+        b->vis[2 * i + 1] = mirror ? -(*vis)[2 * i + 1] : (*vis)[2 * i + 1];
+    }
+    *u = b->u;
+    *v = b->v;
+    *w = b->w;
+    *vis = b->vis;
+}
+
+static void or_unfold(or_fold_buf* b)
+{
+    free(b->u);
+    free(b->v);
+    free(b->w);
+    free(b->vis);
+}
 
 /* Finalise pixel (x, y) of the stacked sum s: divide by the weight sum, by the
  * taper, multiply by n -- each as the flags ask. */
@@ -456,6 +501,8 @@ int64_t oracle_grid(int n, int nw, double pixel_rad, double w_min, double w_max,
     or_cfg c;
     if (or_make_cfg(&c, n, nw, pixel_rad, w_min, w_max, kernel, support, kparam)) return -1;
     if (k0 < 0 || k1 > nw || k0 > k1) return -1;
+    or_fold_buf fold_buf;
+    or_fold(flags, m, &u, &v, &w, &vis, &fold_buf);
     double* weff = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
     int64_t dropped = or_weights(&c, (flags & OR_FLAG_UNIFORM) != 0, m, u, v, w, wt, vis, weff);
     double sw = 0.0;
@@ -464,6 +511,7 @@ int64_t oracle_grid(int n, int nw, double pixel_rad, double w_min, double w_max,
     or_grid(&c, m, u, v, w, vis, weff, k0, k1, (double complex*)planes_out);
     free(weff);
     if (sum_w_out) *sum_w_out = sw;
+    or_unfold(&fold_buf);
     return dropped;
 }
 
@@ -480,6 +528,8 @@ int64_t oracle_dirty_image(int n, int nw, double pixel_rad, double w_min, double
     or_cfg c;
     if (or_make_cfg(&c, n, nw, pixel_rad, w_min, w_max, kernel, support, kparam)) return -1;
     if (k0 < 0 || k1 > nw || k0 > k1) return -1;
+    or_fold_buf fold_buf;
+    or_fold(flags, m, &u, &v, &w, &vis, &fold_buf);
     const size_t nn = (size_t)n * n;
     double* weff = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
     int64_t dropped = or_weights(&c, (flags & OR_FLAG_UNIFORM) != 0, m, u, v, w, wt, vis, weff);
@@ -514,6 +564,7 @@ int64_t oracle_dirty_image(int n, int nw, double pixel_rad, double w_min, double
     free(acc);
     free(weff);
     if (sum_w_out) *sum_w_out = sw;
+    or_unfold(&fold_buf);
     return dropped;
 }
 
@@ -531,6 +582,8 @@ int64_t oracle_image_at(int n, int nw, double pixel_rad, double w_min, double w_
 {
     or_cfg c;
     if (or_make_cfg(&c, n, nw, pixel_rad, w_min, w_max, kernel, support, kparam)) return -1;
+    or_fold_buf fold_buf;
+    or_fold(flags, m, &u, &v, &w, &vis, &fold_buf);
     double* weff = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
     int64_t dropped = or_weights(&c, (flags & OR_FLAG_UNIFORM) != 0, m, u, v, w, wt, vis, weff);
     double sw = 0.0;
@@ -584,6 +637,7 @@ int64_t oracle_image_at(int n, int nw, double pixel_rad, double w_min, double w_
     free(taper);
     free(weff);
     if (sum_w_out) *sum_w_out = sw;
+    or_unfold(&fold_buf);
     return dropped;
 }
 
@@ -600,6 +654,8 @@ int64_t oracle_dft(int n, int nw, double pixel_rad, double w_min, double w_max,
 {
     or_cfg c;
     if (or_make_cfg(&c, n, nw, pixel_rad, w_min, w_max, kernel, support, kparam)) return -1;
+    or_fold_buf fold_buf;
+    or_fold(flags, m, &u, &v, &w, &vis, &fold_buf);
     double* weff = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
     int64_t dropped = or_weights(&c, (flags & OR_FLAG_UNIFORM) != 0, m, u, v, w, wt, vis, weff);
     double sw = 0.0;
@@ -623,6 +679,7 @@ int64_t oracle_dft(int n, int nw, double pixel_rad, double w_min, double w_max,
         out[q] = d;
     }
     free(weff);
+    or_unfold(&fold_buf);
     return dropped;
 }
 
@@ -640,6 +697,9 @@ int64_t oracle_degrid(int n, int nw, double pixel_rad, double w_min, double w_ma
 {
     or_cfg c;
     if (or_make_cfg(&c, n, nw, pixel_rad, w_min, w_max, kernel, support, kparam)) return -1;
+    const float* w_given = w;  /* signs before the fold: mirrored gradients are conjugated */
+    or_fold_buf fold_buf;
+    or_fold(flags, m, &u, &v, &w, &vis, &fold_buf);
     const size_t nn = (size_t)n * n;
     double* weff = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
     int64_t dropped = or_weights(&c, (flags & OR_FLAG_UNIFORM) != 0, m, u, v, w, wt, vis, weff);
@@ -684,6 +744,10 @@ int64_t oracle_degrid(int n, int nw, double pixel_rad, double w_min, double w_ma
     free(R);
     free(taper);
     free(weff);
+    if (flags & OR_FLAG_FOLD)
+        for (int64_t i = 0; i < m; ++i)
+            if (w_given[i] < 0.0f) g[i] = conj(g[i]);
+    or_unfold(&fold_buf);
     return dropped;
 }
 

@@ -10,7 +10,7 @@ device, raises.
 Parameters are a mapping with keys ``n``, ``nw``, ``pixel_rad``, ``w_min``,
 ``w_max``, ``kernel`` (0 Gaussian, 1 Kaiser-Bessel), ``support``,
 ``kernel_param`` (0 = default sigma S/6 / beta 2.34 S), ``flags``
-(GRID_CORRECT | REAL_IMAGE | APPLY_N | UNIFORM_WEIGHT), and optionally
+(GRID_CORRECT | REAL_IMAGE | APPLY_N | UNIFORM_WEIGHT | HERMITIAN_FOLD), and optionally
 ``plane_group`` and ``tile``.
 """
 import ctypes
@@ -18,12 +18,13 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import (APPLY_N, GRID_CORRECT, KERNEL_GAUSS, KERNEL_KB, REAL_IMAGE, UNIFORM_WEIGHT,  # noqa: F401
+from ._lib import (APPLY_N, GRID_CORRECT, HERMITIAN_FOLD, KERNEL_GAUSS, KERNEL_KB, REAL_IMAGE,  # noqa: F401
+                   UNIFORM_WEIGHT,
                    RickError)
 
 __all__ = ["Imager", "BatchImager", "autotune_batch", "DirtyImage", "dirty_image", "RickError", "load",
            "KERNEL_GAUSS", "KERNEL_KB",
-           "GRID_CORRECT", "REAL_IMAGE", "APPLY_N", "UNIFORM_WEIGHT"]
+           "GRID_CORRECT", "REAL_IMAGE", "APPLY_N", "UNIFORM_WEIGHT", "HERMITIAN_FOLD"]
 
 
 def load():

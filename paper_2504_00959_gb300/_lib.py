@@ -20,6 +20,7 @@ GRID_CORRECT = 1
 REAL_IMAGE = 2
 APPLY_N = 4
 UNIFORM_WEIGHT = 8
+HERMITIAN_FOLD = 32
 
 
 class RickParams(ctypes.Structure):

@@ -98,9 +98,14 @@ rick_status check_params(const rick_params* p, GridCfg* c, double* kparam, char*
         }
         T = 32;
     }
-    const uint32_t known = RICK_GRID_CORRECT | RICK_REAL_IMAGE | RICK_APPLY_N | RICK_UNIFORM_WEIGHT;
+    const uint32_t known = RICK_GRID_CORRECT | RICK_REAL_IMAGE | RICK_APPLY_N | RICK_UNIFORM_WEIGHT |
+                           RICK_HERMITIAN_FOLD;
     if (p->flags & ~known) {
         snprintf(msg, msglen, "unknown flags 0x%x", p->flags & ~known);
+        return RICK_ERR_ARG;
+    }
+    if ((p->flags & RICK_HERMITIAN_FOLD) && !(p->flags & RICK_REAL_IMAGE)) {
+        snprintf(msg, msglen, "RICK_HERMITIAN_FOLD changes the imaginary part: it needs RICK_REAL_IMAGE");
         return RICK_ERR_ARG;
     }
     double kp = p->kernel_param;
@@ -124,6 +129,7 @@ rick_status check_params(const rick_params* p, GridCfg* c, double* kparam, char*
     c->kp = (p->kernel == RICK_KERNEL_GAUSS) ? (float)(1.0 / (2.0 * kp * kp)) : (float)kp;
     c->two_over_s = (float)(2.0 / p->support);
     c->uniform = (p->flags & RICK_UNIFORM_WEIGHT) ? 1 : 0;
+    c->fold = (p->flags & RICK_HERMITIAN_FOLD) ? 1 : 0;
     c->nchan = 1;
     c->nw_chan = p->nw;
     c->chan_w = nullptr;

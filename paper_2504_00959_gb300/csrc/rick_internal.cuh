@@ -33,6 +33,7 @@ struct GridCfg {
     float kp;                        // Gaussian: 1/(2 sigma^2); KB: beta
     float two_over_s;                // 2 / S
     int uniform;                     // uniform weighting on
+    int fold;                        // RICK_HERMITIAN_FOLD: mirror measurements with w < 0
     // batched imaging: nchan channels with nw_chan w-planes each, channel c
     // owning planes c*nw_chan .. (c+1)*nw_chan-1 and measurements
     // chan_off[c] .. chan_off[c+1]-1; chan_w[c] = (w_min, 1/dw) in binary32.
@@ -53,11 +54,19 @@ struct GridCfg {
 struct Place {
     int k, fu, fv;
     float pu, pv;
+    bool conj;  // imaged as the Hermitian mirror: use conj(V)
 };
 
 __device__ __forceinline__ bool place(const GridCfg& c, float u, float v, float w, Place& p, int chan = 0)
 {
     if (!(isfinite(u) && isfinite(v) && isfinite(w))) return false;
+    // binary32 negation is exact: the mirror is placed like any measurement
+    p.conj = c.fold && w < 0.0f;
+    if (p.conj) {
+        u = -u;
+        v = -v;
+        w = -w;
+    }
     float pu = __fmaf_rn(u, c.uvscale, c.half_n);
     float pv = __fmaf_rn(v, c.uvscale, c.half_n);
     float au = floorf(__fsub_rn(pu, c.half_s));

@@ -53,7 +53,9 @@ __device__ __forceinline__ bool load_and_place(const GridCfg& c, const Inputs& i
 {
     wi = in.wt ? __ldg(in.wt + i) : 1.0f;
     V = __ldg(in.vis + i);
-    return place(c, __ldg(in.u + i), __ldg(in.v + i), __ldg(in.w + i), p, chan) && finite_value(wi, V);
+    if (!place(c, __ldg(in.u + i), __ldg(in.v + i), __ldg(in.w + i), p, chan)) return false;
+    if (p.conj) V.y = -V.y;
+    return finite_value(wi, V);
 }
 
 // Each block takes one contiguous range of the m measurements and walks it
@@ -338,7 +340,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_degrid_gather(GridCfg c, const
         }
         float scale = wi / (su * sv);
         if ((p.fu + p.fv) & 1) scale = -scale;
-        grad[i] = make_float2(ar * scale, ai * scale);
+        // a mirrored measurement enters as conj(V): its gradient is conjugated
+        grad[i] = make_float2(ar * scale, p.conj ? -ai * scale : ai * scale);
     }
 }
 

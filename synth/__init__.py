@@ -28,6 +28,7 @@ FLAG_CORRECT = 1
 FLAG_REAL = 2
 FLAG_APPLY_N = 4
 FLAG_UNIFORM = 8
+FLAG_FOLD = 32
 C_LIGHT = 299_792_458.0
 BASE_SEED = 20250401
 

@@ -80,3 +80,10 @@ def test_workspace_size_and_parameter_checks(lib):
     assert lib.rick_workspace_size(ctypes.byref(q), 10, ctypes.byref(size)) == 1
     q.nw = 1
     assert lib.rick_workspace_size(ctypes.byref(q), 10, ctypes.byref(size)) == 0
+    # the Hermitian fold changes the imaginary part: only with real images
+    q = _lib.RickParams()
+    lib.rick_params_default(ctypes.byref(q))
+    q.flags = _lib.HERMITIAN_FOLD | _lib.GRID_CORRECT
+    assert lib.rick_workspace_size(ctypes.byref(q), 10, ctypes.byref(size)) == 1
+    q.flags = _lib.HERMITIAN_FOLD | _lib.REAL_IMAGE
+    assert lib.rick_workspace_size(ctypes.byref(q), 10, ctypes.byref(size)) == 0

@@ -61,6 +61,25 @@ def test_degrid_matches_oracle_adjoint(rick, oracle_mod, flags, extra):
     assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
 
 
+def test_degrid_matches_oracle_with_hermitian_fold(rick, oracle_mod):
+    """The adjoint of the folded imager: mirrored measurements get conjugated
+    gradients (w-planes over [0, 120] for w in [-120, 120])."""
+    prob = synth.disk_problem(96, 4, 20000, KB, 7, 6.0, 120.0, 203, weights="random", fill=0.4)
+    prob["params"] = dict(prob["params"], w_min=0.0)
+    flags = CORRECT | REAL | synth.FLAG_FOLD
+    g = _to(prob)
+    im = rick.Imager(dict(prob["params"], flags=flags))
+    _forward(im, g, g["vis"])
+    n = prob["params"]["n"]
+    r = np.random.default_rng(5).standard_normal((n, n)).astype(np.float32)
+    got = im.degrid(torch.from_numpy(r).cuda(), g["u"], g["v"], g["w"], g["wt"]).cpu().numpy()
+    im.close()
+    p = synth.to_numpy(prob)
+    ref = oracle_mod.degrid(p["params"], p["u"], p["v"], p["w"], p["wt"], p["vis"], r.astype(np.complex128),
+                            flags=flags & ~REAL)
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+
+
 def _dot_test(rick, oracle_mod, prob, flags, seed=7, **extra):
     """<A x, y> against <x, A^H y> for random x (complex) and y (real image).
     With grid correction the operator scales pixel (x, y) by 1/(c(x) c(y)),
@@ -88,7 +107,8 @@ def _dot_test(rick, oracle_mod, prob, flags, seed=7, **extra):
 
 
 @pytest.mark.parametrize("flags,extra", [(CORRECT | REAL, {}), (REAL, {}),
-                                         (CORRECT | REAL | UNIFORM | APPLY_N, {"plane_group": 3})])
+                                         (CORRECT | REAL | UNIFORM | APPLY_N, {"plane_group": 3}),
+                                         (CORRECT | REAL | synth.FLAG_FOLD, {"nw": 4, "w_min": 0.0})])
 def test_dot_product_config1(rick, oracle_mod, flags, extra):
     lhs, rhs = _dot_test(rick, oracle_mod, synth.config1(), flags, **extra)
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs), (lhs, rhs)

@@ -277,6 +277,27 @@ def test_hot_tile_in_chunks(rick, oracle_mod):
     _compare(rick, oracle_mod, dict(params=prob["params"], u=u, v=v, w=w, wt=wt, vis=vis), REAL)
 
 
+def test_hermitian_fold_matches_oracle(rick, oracle_mod):
+    """Config 1 folded onto 4 w-planes over [0, 50] (RICK_HERMITIAN_FOLD)."""
+    prob = synth.config1()
+    prob["params"] = dict(prob["params"], nw=4, w_min=0.0)
+    _compare(rick, oracle_mod, prob, CORRECT | REAL | synth.FLAG_FOLD)
+
+
+def test_hermitian_fold_equals_unfolded_on_mirrored_planes(rick, oracle_mod):
+    """The folded real image on 4 planes over [0, 50] against the unfolded one
+    on 8 planes over [-50, 50] (mirrored plane centres): same sum in another
+    FP32 order."""
+    prob = synth.config1()
+    a, _ = _gpu_image(rick, prob, CORRECT | REAL)
+    folded = dict(prob, params=dict(prob["params"], nw=4, w_min=0.0))
+    b, _ = _gpu_image(rick, folded, CORRECT | REAL | synth.FLAG_FOLD)
+    q = prob["params"]
+    c = oracle_mod.taper(q["n"], q["kernel"], q["support"], q.get("kernel_param", 0.0))
+    cc = np.outer(c, c)
+    assert float(np.max(np.abs(a - b) * cc)) <= 1e-5 * float(np.max(np.abs(a) * cc))
+
+
 def test_repeatable_and_stream_ordered(rick):
     """Two images of the same problem, the second on a side stream, agree to
     FP32 reordering (uncorrected images, so no taper amplification)."""

@@ -244,6 +244,44 @@ def test_hermitian_completion_gives_twice_real_part(oracle_mod):
     assert np.max(np.abs(full - np.real(img))) <= 1e-12 * peak  # 2 Re(img) / 2 (weight sum doubles)
 
 
+def test_hermitian_fold_keeps_the_real_image(oracle_mod):
+    """Folding (w < 0 -> (-u, -v, -w, V*)) onto nw planes over [0, W] gives the
+    real image of the unfolded measurements on 2 nw planes over [-W, W] (their
+    plane centres mirror each other), while the imaginary part changes."""
+    p = _small(n=64, nw=8, m=3000, kernel=KB, support=7, wmax=80.0, seed=33, fov=6.0, fill=0.4)
+    p = _subset(p, _away_from_decisions(p))
+    assert np.any(p["w"] < 0) and np.any(p["w"] > 0)
+    whole, _, _ = oracle_mod.dirty_image(*_args(p), flags=CORRECT)
+    q = dict(p, params=dict(p["params"], nw=4, w_min=0.0, w_max=p["params"]["w_max"]))
+    folded, _, _ = oracle_mod.dirty_image(*_args(q), flags=CORRECT | synth.FLAG_FOLD)
+    peak = np.max(np.abs(whole.real))
+    assert np.max(np.abs(folded.real - whole.real)) <= 1e-12 * peak
+    assert np.max(np.abs(folded.imag - whole.imag)) >= 1e-3 * peak
+
+
+def test_hermitian_fold_adjoint_dot_product(oracle_mod):
+    """With the fold the imager is real-linear (mirrored measurements enter as
+    V*): sum_pix r Re(A x) = Re <A^H r, x> for real r, where the degridder
+    conjugates the gradients of mirrored measurements."""
+    p = _small(n=32, nw=2, m=700, support=7, seed=59, weights="random", fov=8.0, wmax=90.0)
+    q = dict(p["params"], w_min=0.0, w_max=90.0)
+    rng = np.random.default_rng(3)
+    m = p["u"].shape[0]
+    x = (rng.standard_normal(m) + 1j * rng.standard_normal(m)).astype(np.complex64)
+    r = rng.standard_normal((32, 32))
+    flags = CORRECT | synth.FLAG_FOLD
+    Ax, _, _ = oracle_mod.dirty_image(q, p["u"], p["v"], p["w"], p["wt"], x, flags=flags)
+    g = oracle_mod.degrid(q, p["u"], p["v"], p["w"], p["wt"], x, r.astype(np.complex128), flags=flags)
+    lhs = float(np.sum(r * Ax.real))
+    rhs = float(np.real(np.vdot(g, x.astype(np.complex128))))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+    # without the conjugation of mirrored gradients the identity fails
+    g0 = oracle_mod.degrid(q, p["u"], p["v"], p["w"], p["wt"], x, r.astype(np.complex128), flags=flags)
+    neg = p["w"] < 0
+    g0[neg] = np.conj(g0[neg])
+    assert abs(lhs - float(np.real(np.vdot(g0, x.astype(np.complex128))))) >= 1e-6 * abs(lhs)
+
+
 def test_linearity(oracle_mod):
     p = _small(n=32, nw=3, m=800, support=7, seed=37)
     rng = np.random.default_rng(1)

@@ -155,6 +155,19 @@ rick_status rick_grid_planes(rick_handle h, int32_t k0, int32_t nk, float* plane
 rick_status rick_degrid(rick_handle h, const float* image_grad, const float* u, const float* v,
                         const float* w, const float* weights, int64_t nvis, float* vis_grad);
 
+/* Model visibilities from a model image (prediction by degridding; the
+ * paper has no counterpart): vis[i] = the measurement equation (Eq. 2 with
+ * the image in place of I/n) sum_{x,y} model(x,y) exp(-2 pi i (u l + v m +
+ * w (n-1))), evaluated the w-stacking way: model / taper (RICK_GRID_CORRECT)
+ * x n (RICK_APPLY_N), conjugate w-screen per plane, forward FFT, gather with
+ * the gridding taps.  It is the adjoint of the unweighted, unnormalised
+ * imaging map (rick_degrid with unit weights, times the weight sum); weights
+ * and uniform weighting play no part.  model: float[n*n] (RICK_REAL_IMAGE)
+ * or float[2*n*n]; vis: float[2*nvis] (complex), overwritten; measurements
+ * whose footprint leaves the grid get 0.  Needs no forward pass. */
+rick_status rick_predict(rick_handle h, const float* model, const float* u, const float* v,
+                         const float* w, int64_t nvis, float* vis);
+
 /* End to end with HOST buffers: copy the inputs to the device, reset, grid,
  * fft_and_stack, copy the image back to image_host, synchronise.  Host
  * arrays as in rick_grid / rick_fft_and_stack (pinned memory is faster). */

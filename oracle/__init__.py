@@ -75,6 +75,8 @@ def lib():
         L.oracle_dft.argtypes = _CFG + [ctypes.c_uint] + _VIS + [ctypes.c_int, _i32p, _f64p]
         L.oracle_degrid.restype = ctypes.c_int64
         L.oracle_degrid.argtypes = _CFG + [ctypes.c_uint] + _VIS + [_f64p, _f64p]
+        L.oracle_predict.restype = ctypes.c_int64
+        L.oracle_predict.argtypes = _CFG + [ctypes.c_uint, ctypes.c_int64, _f32p, _f32p, _f32p, _f64p, _f64p]
         L.oracle_num_threads.restype = ctypes.c_int
         L.oracle_num_threads.argtypes = []
         _lib = L
@@ -203,6 +205,21 @@ def degrid(p, u, v, w, wt, vis, r, flags=None):
     out = np.zeros(args[0], np.complex128)
     _check(lib().oracle_degrid(*_cfg(p), _flags(p, flags), *args, r.view(np.float64).reshape(-1),
                                out.view(np.float64)), "degrid")
+    return out
+
+
+def predict(p, u, v, w, model, flags=None):
+    """Model visibilities of the complex image model [n, n] at (u, v, w): the
+    w-stacking evaluation of the measurement equation (unit weights, no
+    normalisation)."""
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    m = u.shape[0]
+    model = np.ascontiguousarray(model, dtype=np.complex128)
+    out = np.zeros(m, np.complex128)
+    _check(lib().oracle_predict(*_cfg(p), _flags(p, flags), m, u, v, w, model.view(np.float64).reshape(-1),
+                                out.view(np.float64)), "predict")
     return out
 
 

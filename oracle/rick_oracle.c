@@ -689,11 +689,11 @@ int64_t oracle_dft(int n, int nw, double pixel_rad, double w_min, double w_max,
  * between the same shifts, then each measurement gathers its footprint of
  * F_k with the same normalised taps, times its effective weight.
  * grad_out: complex double [m]. */
-int64_t oracle_degrid(int n, int nw, double pixel_rad, double w_min, double w_max,
-                      int kernel, int support, double kparam, unsigned flags,
-                      int64_t m, const float* u, const float* v, const float* w,
-                      const float* wt, const float* vis, const double* r_in,
-                      double* grad_out)
+static int64_t or_degrid(int n, int nw, double pixel_rad, double w_min, double w_max,
+                         int kernel, int support, double kparam, unsigned flags,
+                         int64_t m, const float* u, const float* v, const float* w,
+                         const float* wt, const float* vis, const double* r_in,
+                         double* grad_out, int predict)
 {
     or_cfg c;
     if (or_make_cfg(&c, n, nw, pixel_rad, w_min, w_max, kernel, support, kparam)) return -1;
@@ -705,6 +705,7 @@ int64_t oracle_degrid(int n, int nw, double pixel_rad, double w_min, double w_ma
     int64_t dropped = or_weights(&c, (flags & OR_FLAG_UNIFORM) != 0, m, u, v, w, wt, vis, weff);
     double sw = 0.0;
     for (int64_t i = 0; i < m; ++i) sw += weff[i];
+    if (predict) sw = 1.0;  /* prediction: no normalisation by the weight sum */
     double* taper = (double*)malloc(sizeof(double) * n);
     or_taper(&c, taper);
     const double complex* r = (const double complex*)r_in;
@@ -749,6 +750,37 @@ int64_t oracle_degrid(int n, int nw, double pixel_rad, double w_min, double w_ma
             if (w_given[i] < 0.0f) g[i] = conj(g[i]);
     or_unfold(&fold_buf);
     return dropped;
+}
+
+int64_t oracle_degrid(int n, int nw, double pixel_rad, double w_min, double w_max,
+                      int kernel, int support, double kparam, unsigned flags,
+                      int64_t m, const float* u, const float* v, const float* w,
+                      const float* wt, const float* vis, const double* r_in,
+                      double* grad_out)
+{
+    return or_degrid(n, nw, pixel_rad, w_min, w_max, kernel, support, kparam, flags, m, u, v, w, wt, vis, r_in,
+                     grad_out, 0);
+}
+
+/* Model visibilities of the image `model` (complex double [n][n]): the same
+ * chain as the adjoint with unit weights and no division by their sum, i.e.
+ * the w-stacking evaluation of the measurement equation (Eq. 2 with the
+ * image in place of I/n): model / taper * n (per flags) * exp(-2 pi i w_k
+ * (n-1)), forward DFT, gather with the normalised taps.  Measurements that
+ * cannot be placed get 0.  vis_out: complex double [m]. */
+int64_t oracle_predict(int n, int nw, double pixel_rad, double w_min, double w_max,
+                       int kernel, int support, double kparam, unsigned flags,
+                       int64_t m, const float* u, const float* v, const float* w,
+                       const double* model, double* vis_out)
+{
+    float* one = (float*)malloc(sizeof(float) * (size_t)(m > 0 ? m : 1));
+    float* zero = (float*)calloc(2 * (size_t)(m > 0 ? m : 1), sizeof(float));
+    for (int64_t i = 0; i < m; ++i) one[i] = 1.0f;
+    const int64_t d = or_degrid(n, nw, pixel_rad, w_min, w_max, kernel, support, kparam, flags & ~OR_FLAG_UNIFORM,
+                                m, u, v, w, one, zero, model, vis_out, 1);
+    free(one);
+    free(zero);
+    return d;
 }
 
 /* Number of OpenMP threads the oracle runs on. */

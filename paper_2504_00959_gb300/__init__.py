@@ -159,6 +159,21 @@ class Imager:
                                        _ptr(out)), self._h)
         return out
 
+    def predict(self, model, u, v, w, out=None):
+        """Model visibilities (complex64 [m]) of the model image at (u, v, w):
+        the measurement equation evaluated by degridding (rick_predict)."""
+        n = self.n
+        m = u.numel()
+        model = self._vec(model.contiguous(), "model", torch.float32 if self.real else torch.complex64, n * n)
+        u, v, w = (self._vec(u, "u", torch.float32, m), self._vec(v, "v", torch.float32, m),
+                   self._vec(w, "w", torch.float32, m))
+        if out is None:
+            out = torch.empty(m, dtype=torch.complex64, device=self.device)
+        self._vec(out, "out", torch.complex64, m)
+        self._sync_stream()
+        _lib.check(self._L.rick_predict(self._h, _ptr(model), _ptr(u), _ptr(v), _ptr(w), m, _ptr(out)), self._h)
+        return out
+
     def image_host(self, vis, u, v, w, wt=None, out=None):
         """End to end with host (CPU) tensors, through rick_image_host."""
         m = u.numel()

@@ -61,6 +61,7 @@ SIGNATURES = {
     "rick_fft_and_stack": (_S, [_H, _P]),
     "rick_grid_planes": (_S, [_H, ctypes.c_int32, ctypes.c_int32, _P]),
     "rick_degrid": (_S, [_H, _P, _P, _P, _P, _P, ctypes.c_int64, _P]),
+    "rick_predict": (_S, [_H, _P, _P, _P, _P, ctypes.c_int64, _P]),
     "rick_image_host": (_S, [_H, _P, _P, _P, _P, _P, ctypes.c_int64, _P]),
     "rick_create_batch": (_S, [ctypes.POINTER(RickParams), ctypes.c_int32, _P, _P,
                                ctypes.POINTER(ctypes.c_void_p)]),

@@ -454,6 +454,12 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
     if (cudaMalloc(&h->block_sums, scan_block_sums_len(ntiles) * sizeof(uint32_t)) != cudaSuccess)
         return cleanup(RICK_ERR_OOM);
     if (cudaMalloc(&h->ctr, sizeof(Counters)) != cudaSuccess) return cleanup(RICK_ERR_OOM);
+    {
+        const double one = 1.0;
+        if (cudaMalloc((void**)&h->one, sizeof(double)) != cudaSuccess) return cleanup(RICK_ERR_OOM);
+        if (cudaMemcpy(h->one, &one, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(RICK_ERR_CUDA);
+    }
     if (p->flags & RICK_UNIFORM_WEIGHT) {
         if (cudaMalloc(&h->density, (size_t)c.n * c.n * sizeof(uint32_t)) != cudaSuccess)
             return cleanup(RICK_ERR_OOM);
@@ -525,6 +531,7 @@ rick_status rick_destroy(rick_handle h)
     cudaFree(h->block_sums);
     cudaFree(h->density);
     cudaFree(h->ctr);
+    cudaFree(h->one);
     cudaFree(h->fft_work);
     cudaFree(h->stage);
     cudaFree(h->img_dev);
@@ -674,19 +681,15 @@ rick_status rick_fft_and_stack(rick_handle h, float* image)
     return RICK_OK;
 }
 
-rick_status rick_degrid(rick_handle h, const float* image_grad, const float* u, const float* v, const float* w,
-                        const float* weights, int64_t nvis, float* vis_grad)
+// The degridding chain shared by rick_degrid and rick_predict: sort the
+// measurements by the tile of their first footprint cell, then per plane
+// group spread the image (adjoint of the finalisation with the weight sum at
+// *sum_w, conjugate w-screen), transform forward and gather each footprint
+// with the gridding taps, times the weight (density: uniform weighting).
+static rick_status degrid_impl(rick_handle h, const GridCfg& c, const double* sum_w, const uint32_t* density,
+                               const float* image_grad, const float* u, const float* v, const float* w,
+                               const float* weights, int64_t nvis, float* vis_grad)
 {
-    if (!h) return RICK_ERR_ARG;
-    if (h->batch) return fail(h, RICK_ERR_STATE, "batched handle: the adjoint is single-channel");
-    if (nvis < 0) return fail(h, RICK_ERR_ARG, "nvis must be >= 0");
-    if (nvis > ((int64_t)1 << 30)) return fail(h, RICK_ERR_ARG, "at most 2^30 measurements per call");
-    if (nvis > 0 && (!u || !v || !w || !vis_grad)) return fail(h, RICK_ERR_ARG, "u, v, w, vis_grad must not be NULL");
-    if (!image_grad) return fail(h, RICK_ERR_ARG, "image_grad is NULL");
-    if (h->chunks.empty())
-        return fail(h, RICK_ERR_STATE, "rick_degrid needs the weight sum of a forward pass: call rick_grid first");
-    if (nvis == 0) return RICK_OK;
-    const GridCfg& c = h->cfg;
     const rick_params& p = h->p;
     const int64_t ntiles = (int64_t)c.nw * c.ntp;
     const size_t off_bytes = (size_t)(ntiles + 1) * sizeof(uint32_t);
@@ -723,7 +726,7 @@ rick_status rick_degrid(rick_handle h, const float* image_grad, const float* u, 
         const int nk = (p.nw - k0 < h->G) ? p.nw - k0 : h->G;
         a.k0 = k0;
         a.nk = nk;
-        e = launch_spread(a, image_grad, h->taper, &h->ctr->sum_w, h->planes, h->stream);
+        e = launch_spread(a, image_grad, h->taper, sum_w, h->planes, h->stream);
         if (e != cudaSuccess) {
             st = fail(h, RICK_ERR_CUDA, "k_spread: %s", cudaGetErrorString(e));
             break;
@@ -737,7 +740,7 @@ rick_status rick_degrid(rick_handle h, const float* image_grad, const float* u, 
             st = fail(h, RICK_ERR_CUFFT, "cufftExecC2C(FORWARD): error %d", (int)r);
             break;
         }
-        e = launch_degrid_gather(c, perm, off, k0, nk, h->planes, u, v, w, weights, h->density, grad, h->stream);
+        e = launch_degrid_gather(c, perm, off, k0, nk, h->planes, u, v, w, weights, density, grad, h->stream);
         if (e != cudaSuccess) {
             st = fail(h, RICK_ERR_CUDA, "k_degrid_gather: %s", cudaGetErrorString(e));
             break;
@@ -748,6 +751,37 @@ rick_status rick_degrid(rick_handle h, const float* image_grad, const float* u, 
     cudaFreeAsync(perm, h->stream);
     return st;
 }
+
+rick_status rick_degrid(rick_handle h, const float* image_grad, const float* u, const float* v, const float* w,
+                        const float* weights, int64_t nvis, float* vis_grad)
+{
+    if (!h) return RICK_ERR_ARG;
+    if (h->batch) return fail(h, RICK_ERR_STATE, "batched handle: the adjoint is single-channel");
+    if (nvis < 0) return fail(h, RICK_ERR_ARG, "nvis must be >= 0");
+    if (nvis > ((int64_t)1 << 30)) return fail(h, RICK_ERR_ARG, "at most 2^30 measurements per call");
+    if (nvis > 0 && (!u || !v || !w || !vis_grad)) return fail(h, RICK_ERR_ARG, "u, v, w, vis_grad must not be NULL");
+    if (!image_grad) return fail(h, RICK_ERR_ARG, "image_grad is NULL");
+    if (h->chunks.empty())
+        return fail(h, RICK_ERR_STATE, "rick_degrid needs the weight sum of a forward pass: call rick_grid first");
+    if (nvis == 0) return RICK_OK;
+    return degrid_impl(h, h->cfg, &h->ctr->sum_w, h->density, image_grad, u, v, w, weights, nvis, vis_grad);
+}
+
+rick_status rick_predict(rick_handle h, const float* model, const float* u, const float* v, const float* w,
+                         int64_t nvis, float* vis)
+{
+    if (!h) return RICK_ERR_ARG;
+    if (h->batch) return fail(h, RICK_ERR_STATE, "batched handle: prediction is single-channel");
+    if (nvis < 0) return fail(h, RICK_ERR_ARG, "nvis must be >= 0");
+    if (nvis > ((int64_t)1 << 30)) return fail(h, RICK_ERR_ARG, "at most 2^30 measurements per call");
+    if (nvis > 0 && (!u || !v || !w || !vis)) return fail(h, RICK_ERR_ARG, "u, v, w, vis must not be NULL");
+    if (!model) return fail(h, RICK_ERR_ARG, "model is NULL");
+    if (nvis == 0) return RICK_OK;
+    GridCfg c = h->cfg;
+    c.uniform = 0;  // unit weights, no density
+    return degrid_impl(h, c, h->one, nullptr, model, u, v, w, nullptr, nvis, vis);
+}
+
 
 rick_status rick_image_host(rick_handle h, const float* vis_host, const float* u_host, const float* v_host,
                             const float* w_host, const float* weights_host, int64_t nvis, float* image_host)

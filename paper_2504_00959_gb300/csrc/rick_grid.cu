@@ -500,35 +500,61 @@ cudaError_t launch_grid_s(const GridCfg& c, const ChunkList& ch, int k0, int nk,
 
 // Taper c(x) = int g(t) cos(2 pi t (x - n/2)/n) dt / int g(t) dt over
 // [-S/2, S/2]: composite Simpson rule with kTaperIntervals intervals, FP64;
-// the kernel samples are computed once per block into shared memory.
+// the weighted kernel samples are computed once (k_taper_samples), then one
+// CTA per pixel sums the rule.
 constexpr int kTaperIntervals = 4096;
 
-__global__ void __launch_bounds__(256) k_taper(GridCfg c, double kparam, float* __restrict__ taper)
+// Simpson-weighted kernel samples w_i g(t_i), t_i = -S/2 + i S / kTaperIntervals.
+__global__ void k_taper_samples(GridCfg c, double kparam, double* __restrict__ g)
 {
-    __shared__ double g[kTaperIntervals + 1];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > kTaperIntervals) return;
     const double a = -0.5 * c.S, h = (double)c.S / kTaperIntervals;
-    for (int i = threadIdx.x; i <= kTaperIntervals; i += blockDim.x) {
-        const double t = a + i * h;
-        double val;
-        if (c.kernel == RICK_KERNEL_GAUSS) {
-            val = exp(-t * t / (2.0 * kparam * kparam));
-        } else {
-            const double z = 2.0 * t / c.S;
-            val = cyl_bessel_i0(kparam * sqrt(fmax(0.0, 1.0 - z * z)));
-        }
-        const double wgt = (i == 0 || i == kTaperIntervals) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
-        g[i] = wgt * val;
+    const double t = a + i * h;
+    double val;
+    if (c.kernel == RICK_KERNEL_GAUSS) {
+        val = exp(-t * t / (2.0 * kparam * kparam));
+    } else {
+        const double z = 2.0 * t / c.S;
+        val = cyl_bessel_i0(kparam * sqrt(fmax(0.0, 1.0 - z * z)));
     }
-    __syncthreads();
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= c.n) return;
+    const double wgt = (i == 0 || i == kTaperIntervals) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+    g[i] = wgt * val;
+}
+
+// One CTA per pixel x: its threads split the quadrature sum, then reduce.
+constexpr int kTaperThreads = 128;
+
+__global__ void __launch_bounds__(kTaperThreads) k_taper(GridCfg c, const double* __restrict__ g,
+                                                         float* __restrict__ taper)
+{
+    const int x = blockIdx.x;
+    const double a = -0.5 * c.S, h = (double)c.S / kTaperIntervals;
     const double xi2 = 2.0 * (double)(x - c.n / 2) / c.n;  // cos(2 pi t xi) = cospi(t * 2 xi)
     double num = 0.0, den = 0.0;
-    for (int i = 0; i <= kTaperIntervals; ++i) {
+    for (int i = threadIdx.x; i <= kTaperIntervals; i += kTaperThreads) {
         num += g[i] * cospi((a + i * h) * xi2);
         den += g[i];
     }
-    taper[x] = (float)(num / den);
+    __shared__ double sn[kTaperThreads / 32], sd[kTaperThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sn[threadIdx.x >> 5] = num;
+        sd[threadIdx.x >> 5] = den;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tn = 0.0, td = 0.0;
+        for (int k = 0; k < kTaperThreads / 32; ++k) {
+            tn += sn[k];
+            td += sd[k];
+        }
+        taper[x] = (float)(tn / td);
+    }
 }
 
 // Kernel value in FP64 (CUDA's exp / cyl_bessel_i0), un-normalised.
@@ -628,8 +654,15 @@ cudaError_t launch_grid(const GridCfg& c, const ChunkList& ch, int k0, int nk, b
 
 cudaError_t launch_taper(const GridCfg& c, double kernel_param, float* taper, cudaStream_t s)
 {
-    k_taper<<<(c.n + 255) / 256, 256, 0, s>>>(c, kernel_param, taper);
-    return cudaGetLastError();
+    double* g = nullptr;
+    cudaError_t e = cudaMalloc((void**)&g, sizeof(double) * (kTaperIntervals + 1));
+    if (e != cudaSuccess) return e;
+    k_taper_samples<<<(kTaperIntervals + 256) / 256, 256, 0, s>>>(c, kernel_param, g);
+    k_taper<<<c.n, kTaperThreads, 0, s>>>(c, g, taper);
+    e = cudaGetLastError();
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaFree(g);
+    return e != cudaSuccess ? e : e2;
 }
 
 }  // namespace rick

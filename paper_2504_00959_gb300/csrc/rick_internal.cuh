@@ -265,6 +265,7 @@ struct rick_imager {
     uint32_t* block_sums;            // scan block totals
     uint32_t* density;               // [n][n] uniform weighting counts
     rick::Counters* ctr;             // device counters
+    double* one;                     // device 1.0: the weight sum of unweighted prediction
     void* fft_work;
     size_t fft_work_bytes;
     std::map<int, cufftHandle> plans;// batch -> plan

@@ -449,6 +449,42 @@ def test_against_direct_dft_with_exact_w_term(oracle_mod):
         assert abs(ws[i] - ref[i]) < 0.02 * fl
 
 
+@pytest.mark.parametrize("fold", [False, True])
+def test_predict_against_measurement_equation(oracle_mod, fold):
+    """Prediction of a model of three point-source pixels against Eq. 2 evaluated
+    directly per measurement, within the bound of the imaging pin: per axis
+    gridding + grid correction (e_a), plus the phase error of snapping w to
+    the plane centre.  With the Hermitian fold (the model is real) on half the
+    planes over [0, W] the same bound holds."""
+    nw = 32
+    p, src = _dft_problem(nw)
+    q = dict(p["params"])
+    if fold:
+        q = dict(q, nw=nw // 2, w_min=0.0)
+    n, S = q["n"], q["support"]
+    dl = q["pixel_rad"]
+    model = np.zeros((n, n), np.complex128)
+    for (ix, iy, fl) in src:
+        model[n // 2 + iy, n // 2 + ix] = fl
+    flags = CORRECT | (synth.FLAG_FOLD if fold else 0)
+    got = oracle_mod.predict(q, p["u"], p["v"], p["w"], model, flags=flags)
+    u, v, w = (p[k].astype(np.float64) for k in ("u", "v", "w"))
+    ref = np.zeros(u.shape[0], np.complex128)
+    bound = np.zeros(u.shape[0])
+    e_a = _alias_bound(KB, S, 2.34 * S, 0.25, lambda nn: kb_taper(nn, S, 2.34 * S))
+    dw = (q["w_max"] - q["w_min"]) / q["nw"]
+    for (ix, iy, fl) in src:
+        l, mm = ix * dl, iy * dl
+        nm1 = -(l * l + mm * mm) / (1 + math.sqrt(1 - l * l - mm * mm))
+        ref += fl * np.exp(-2j * np.pi * (u * l + v * mm + w * nm1))
+        bound += fl * (((1 + e_a) ** 2 - 1) + (1 + e_a) ** 2 * 2 * np.pi * (dw / 2) * abs(nm1))
+    sgn = np.where(p["w"] < 0, -1.0, 1.0).astype(np.float32) if fold else np.ones_like(p["w"])
+    placed = oracle_mod.place(q, sgn * p["u"], sgn * p["v"], sgn * p["w"])[0] >= 0
+    assert np.all(got[~placed] == 0)  # footprints off the grid: no prediction
+    err = np.abs(got - ref)[placed]
+    assert np.all(err <= bound[placed]), (err.max(), bound.min())
+
+
 def test_w_error_shrinks_with_more_planes(oracle_mod):
     """The w-quantisation error at a source falls as planes are added (the
     coherent error scales like dw^2), down to the gridding floor."""

@@ -307,16 +307,29 @@ def main():
         hv = prob["vis"].cpu().pin_memory()
         hu, hvv, hw, hwt = (prob[k].cpu().pin_memory() for k in ("u", "v", "w", "wt"))
         himg = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        himg2 = torch.empty((n, n), dtype=torch.float32).pin_memory()
         im.image_host(hv, hu, hvv, hw, hwt, out=himg)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ksteps = max(min(args.steps, 5), 1)
         for _ in range(ksteps):
             im.image_host(hv, hu, hvv, hw, hwt, out=himg)
+        te_sync = (time.perf_counter() - t0) / ksteps
+        # a stream of images through the pipelined call: upload of image i+1
+        # and download of image i-1 under the imaging of image i
+        for j in range(2):
+            im.image_host_async(hv, hu, hvv, hw, hwt, out=(himg, himg2)[j % 2])
+        im.synchronize()
+        ksteps = max(min(args.steps, 20), 2)
+        t0 = time.perf_counter()
+        for j in range(ksteps):
+            im.image_host_async(hv, hu, hvv, hw, hwt, out=(himg, himg2)[j % 2])
+        im.synchronize()
         te = (time.perf_counter() - t0) / ksteps
         e2e = {"value": m / te, "unit": "vis/s", "ms_per_step": te * 1e3,
                "h2d_bytes_per_step": int(m * (8 + 4 + 4 + 4 + 4)), "d2h_bytes_per_step": int(n * n * 4),
-               "api": "rick_image_host (pinned host buffers)"}
+               "api": "rick_image_host_async over %d images, then rick_synchronize (pinned host buffers)" % ksteps,
+               "unpipelined_ms_per_step": te_sync * 1e3}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -175,6 +175,23 @@ rick_status rick_image_host(rick_handle h, const float* vis_host, const float* u
                             const float* v_host, const float* w_host,
                             const float* weights_host, int64_t nvis, float* image_host);
 
+/* Pipelined form of rick_image_host for a stream of images (the paper's
+ * chunk loop reads the next data while it images, Sec. 2.2): enqueues the
+ * upload of the inputs, the imaging and the download of the image, and
+ * returns without waiting.  Uploads and downloads run on the handle's own
+ * copy streams into two device slots, ordered against the handle's stream
+ * by events, so image i's compute overlaps the upload of image i+1 and the
+ * download of image i-1.  Host arrays must stay valid and unmodified, and
+ * image_host must not be read, until rick_synchronize; they should be
+ * pinned (pageable memory makes the copies synchronous).  Same arguments,
+ * layouts and errors as rick_image_host. */
+rick_status rick_image_host_async(rick_handle h, const float* vis_host, const float* u_host,
+                                  const float* v_host, const float* w_host,
+                                  const float* weights_host, int64_t nvis, float* image_host);
+
+/* Wait for everything enqueued on the handle (its stream and copy streams). */
+rick_status rick_synchronize(rick_handle h);
+
 /* Batched multi-channel imaging (not in the paper; it repeats the chunk loop
  * of Sec. 2.2 over frequency channels in one pass): nchan channels share n,
  * pixel_rad, the kernel and the w-plane count p->nw, each with its own

@@ -192,6 +192,30 @@ class Imager:
         self.generation += 1
         return out
 
+    def image_host_async(self, vis, u, v, w, wt=None, out=None):
+        """Pipelined image_host (rick_image_host_async): enqueues upload,
+        imaging and download and returns at once; the inputs must stay
+        unmodified and `out` (pinned CPU memory) unread until synchronize()."""
+        m = u.numel()
+        for name, t, dt in (("vis", vis, torch.complex64), ("u", u, torch.float32), ("v", v, torch.float32),
+                            ("w", w, torch.float32)):
+            if t.device.type != "cpu" or t.dtype != dt or not t.is_contiguous() or t.numel() != m:
+                raise ValueError(f"{name} must be a contiguous {dt} CPU tensor of {m} elements")
+        if wt is not None and (wt.device.type != "cpu" or wt.dtype != torch.float32 or wt.numel() != m):
+            raise ValueError("wt must be a float32 CPU tensor")
+        n = self.n
+        if out is None:
+            out = torch.empty((n, n), dtype=torch.float32 if self.real else torch.complex64).pin_memory()
+        self._sync_stream()
+        _lib.check(self._L.rick_image_host_async(self._h, _ptr(vis), _ptr(u), _ptr(v), _ptr(w), _ptr(wt), m,
+                                                 _ptr(out)), self._h)
+        self.generation += 1
+        return out
+
+    def synchronize(self):
+        """Wait for everything enqueued on this imager (rick_synchronize)."""
+        _lib.check(self._L.rick_synchronize(self._h), self._h)
+
     def stats(self):
         st = _lib.RickStats()
         _lib.check(self._L.rick_get_stats(self._h, ctypes.byref(st)), self._h)

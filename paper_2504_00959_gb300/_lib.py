@@ -62,6 +62,8 @@ SIGNATURES = {
     "rick_grid_planes": (_S, [_H, ctypes.c_int32, ctypes.c_int32, _P]),
     "rick_degrid": (_S, [_H, _P, _P, _P, _P, _P, ctypes.c_int64, _P]),
     "rick_predict": (_S, [_H, _P, _P, _P, _P, ctypes.c_int64, _P]),
+    "rick_image_host_async": (_S, [_H, _P, _P, _P, _P, _P, ctypes.c_int64, _P]),
+    "rick_synchronize": (_S, [_H]),
     "rick_image_host": (_S, [_H, _P, _P, _P, _P, _P, ctypes.c_int64, _P]),
     "rick_create_batch": (_S, [ctypes.POINTER(RickParams), ctypes.c_int32, _P, _P,
                                ctypes.POINTER(ctypes.c_void_p)]),

@@ -512,10 +512,13 @@ rick_status rick_create(const rick_params* p, rick_handle* out)
     return create_impl(p, 1, nullptr, nullptr, out);
 }
 
+static void async_release(rick_handle h);
+
 rick_status rick_destroy(rick_handle h)
 {
     if (!h) return RICK_OK;
     cudaStreamSynchronize(h->stream);
+    async_release(h);
     free_chunks(h);
     cudaStreamSynchronize(h->stream);
     for (auto& kv : h->plans) cufftDestroy(kv.second);
@@ -833,6 +836,109 @@ rick_status rick_image_host(rick_handle h, const float* vis_host, const float* u
     if (s) return s;
     RICK_CU(h, cudaMemcpyAsync(image_host, h->img_dev, img, cudaMemcpyDeviceToHost, h->stream));
     RICK_CU(h, cudaStreamSynchronize(h->stream));
+    return RICK_OK;
+}
+
+static rick_status async_init(rick_handle h)
+{
+    if (h->async_ready) return RICK_OK;
+    RICK_CU(h, cudaStreamCreateWithFlags(&h->h2d, cudaStreamNonBlocking));
+    RICK_CU(h, cudaStreamCreateWithFlags(&h->d2h, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+        RICK_CU(h, cudaEventCreateWithFlags(&h->ev_staged[b], cudaEventDisableTiming));
+        RICK_CU(h, cudaEventCreateWithFlags(&h->ev_computed[b], cudaEventDisableTiming));
+        RICK_CU(h, cudaEventCreateWithFlags(&h->ev_fetched[b], cudaEventDisableTiming));
+    }
+    h->async_ready = true;
+    return RICK_OK;
+}
+
+static void async_release(rick_handle h)
+{
+    if (!h->async_ready) return;
+    cudaStreamSynchronize(h->h2d);
+    cudaStreamSynchronize(h->d2h);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(h->astage[b]);
+        cudaFree(h->aimg[b]);
+        cudaEventDestroy(h->ev_staged[b]);
+        cudaEventDestroy(h->ev_computed[b]);
+        cudaEventDestroy(h->ev_fetched[b]);
+    }
+    cudaStreamDestroy(h->h2d);
+    cudaStreamDestroy(h->d2h);
+    h->async_ready = false;
+}
+
+rick_status rick_image_host_async(rick_handle h, const float* vis_host, const float* u_host, const float* v_host,
+                                  const float* w_host, const float* weights_host, int64_t nvis, float* image_host)
+{
+    if (!h) return RICK_ERR_ARG;
+    if (h->batch) return fail(h, RICK_ERR_STATE, "batched handle: use rick_image_batch");
+    rick_status s = check_vis_args(h, vis_host, u_host, v_host, w_host, nvis);
+    if (s) return s;
+    if (!image_host) return fail(h, RICK_ERR_ARG, "image_host is NULL");
+    if ((s = async_init(h))) return s;
+    const size_t fb = (size_t)nvis * sizeof(float);
+    const size_t need = (weights_host ? 6 : 5) * fb;
+    const size_t img = (size_t)h->p.n * h->p.n * ((h->p.flags & RICK_REAL_IMAGE) ? 1 : 2) * sizeof(float);
+    if (need > h->astage_bytes || img > h->aimg_bytes) {
+        // grow both slots once nothing is in flight
+        RICK_CU(h, cudaStreamSynchronize(h->h2d));
+        RICK_CU(h, cudaStreamSynchronize(h->stream));
+        RICK_CU(h, cudaStreamSynchronize(h->d2h));
+        const size_t sb = need > h->astage_bytes ? need : h->astage_bytes;
+        const size_t ib = img > h->aimg_bytes ? img : h->aimg_bytes;
+        for (int b = 0; b < 2; ++b) {
+            cudaFree(h->astage[b]);
+            cudaFree(h->aimg[b]);
+            h->astage[b] = nullptr;
+            h->aimg[b] = nullptr;
+        }
+        h->bytes_held -= 2 * (h->astage_bytes + h->aimg_bytes);
+        h->astage_bytes = h->aimg_bytes = 0;
+        for (int b = 0; b < 2; ++b) {
+            RICK_CU(h, cudaMalloc((void**)&h->astage[b], sb));
+            RICK_CU(h, cudaMalloc((void**)&h->aimg[b], ib));
+        }
+        h->astage_bytes = sb;
+        h->aimg_bytes = ib;
+        h->bytes_held += 2 * (sb + ib);
+    }
+    const int b = h->aslot;
+    h->aslot ^= 1;
+    float* d_vis = h->astage[b];
+    float* d_u = d_vis + 2 * nvis;
+    float* d_v = d_u + nvis;
+    float* d_w = d_v + nvis;
+    float* d_wt = weights_host ? d_w + nvis : nullptr;
+    // upload once the compute that last read this slot is done
+    RICK_CU(h, cudaStreamWaitEvent(h->h2d, h->ev_computed[b], 0));
+    RICK_CU(h, cudaMemcpyAsync(d_vis, vis_host, 2 * fb, cudaMemcpyHostToDevice, h->h2d));
+    RICK_CU(h, cudaMemcpyAsync(d_u, u_host, fb, cudaMemcpyHostToDevice, h->h2d));
+    RICK_CU(h, cudaMemcpyAsync(d_v, v_host, fb, cudaMemcpyHostToDevice, h->h2d));
+    RICK_CU(h, cudaMemcpyAsync(d_w, w_host, fb, cudaMemcpyHostToDevice, h->h2d));
+    if (d_wt) RICK_CU(h, cudaMemcpyAsync(d_wt, weights_host, fb, cudaMemcpyHostToDevice, h->h2d));
+    RICK_CU(h, cudaEventRecord(h->ev_staged[b], h->h2d));
+    // image once the inputs have landed and the last download of this slot is done
+    RICK_CU(h, cudaStreamWaitEvent(h->stream, h->ev_staged[b], 0));
+    RICK_CU(h, cudaStreamWaitEvent(h->stream, h->ev_fetched[b], 0));
+    if ((s = rick_reset(h))) return s;
+    if ((s = rick_grid(h, d_vis, d_u, d_v, d_w, d_wt, nvis))) return s;
+    if ((s = rick_fft_and_stack(h, h->aimg[b]))) return s;
+    RICK_CU(h, cudaEventRecord(h->ev_computed[b], h->stream));
+    RICK_CU(h, cudaStreamWaitEvent(h->d2h, h->ev_computed[b], 0));
+    RICK_CU(h, cudaMemcpyAsync(image_host, h->aimg[b], img, cudaMemcpyDeviceToHost, h->d2h));
+    RICK_CU(h, cudaEventRecord(h->ev_fetched[b], h->d2h));
+    return RICK_OK;
+}
+
+rick_status rick_synchronize(rick_handle h)
+{
+    if (!h) return RICK_ERR_ARG;
+    if (h->async_ready) RICK_CU(h, cudaStreamSynchronize(h->h2d));
+    RICK_CU(h, cudaStreamSynchronize(h->stream));
+    if (h->async_ready) RICK_CU(h, cudaStreamSynchronize(h->d2h));
     return RICK_OK;
 }
 

@@ -283,6 +283,16 @@ struct rick_imager {
     size_t stage_bytes;
     float* img_dev;
     size_t img_bytes;
+    // pipelined host path (rick_image_host_async): two slots of device
+    // inputs and images; uploads and downloads on their own streams, ordered
+    // against the compute stream by events
+    bool async_ready;
+    cudaStream_t h2d, d2h;
+    float* astage[2];
+    float* aimg[2];
+    size_t astage_bytes, aimg_bytes;
+    cudaEvent_t ev_staged[2], ev_computed[2], ev_fetched[2];
+    int aslot;
     size_t bytes_held;
     rick::PhaseTimer timer;
     // batched imaging (rick_create_batch): per-channel w-ranges and sums,

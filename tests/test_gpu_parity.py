@@ -326,6 +326,28 @@ def test_image_host_matches_device_path(rick):
     assert torch.max(torch.abs(a - b)).item() <= 1e-6 * torch.max(torch.abs(b)).item()
 
 
+def test_pipelined_host_path_matches_synchronous(rick):
+    """Five images of alternating problems (different data, the second with
+    weights) through rick_image_host_async with two output buffers in
+    flight, against rick_image_host one by one: the slot reuse and the event
+    ordering between the copy streams and the compute stream hold."""
+    probs = [synth.config1(), synth.disk_problem(256, 8, 60000, KB, 7, 2.0, 50.0, 99, weights="random")]
+    probs = [dict(p, **{k: p[k].contiguous() for k in ("vis", "u", "v", "w", "wt")}) for p in probs]
+    pinned = [{k: p[k].pin_memory() for k in ("vis", "u", "v", "w", "wt")} for p in probs]
+    im = rick.Imager(dict(probs[0]["params"], flags=REAL))
+    ref = [im.image_host(p["vis"], p["u"], p["v"], p["w"], p["wt"] if j else None).clone()
+           for j, p in enumerate(pinned)]
+    outs = [torch.empty((256, 256)).pin_memory() for _ in range(5)]
+    for i in range(5):
+        p = pinned[i % 2]
+        im.image_host_async(p["vis"], p["u"], p["v"], p["w"], p["wt"] if i % 2 else None, out=outs[i])
+    im.synchronize()
+    im.close()
+    for i in range(5):
+        r = ref[i % 2]
+        assert torch.max(torch.abs(outs[i] - r)).item() <= 1e-6 * torch.max(torch.abs(r)).item(), i
+
+
 def test_errors_are_returned_not_raised_on_device(rick):
     prob = _to(synth.config1())
     im = rick.Imager(dict(prob["params"]))

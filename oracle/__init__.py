@@ -10,7 +10,8 @@ Problem parameters are passed as a mapping with the keys ``n``, ``nw``,
 ``pixel_rad``, ``w_min``, ``w_max``, ``kernel`` (0 Gaussian, 1 Kaiser-Bessel),
 ``support``, ``kernel_param`` (sigma in cells or beta; 0 = default) and
 ``flags`` (bit 1 grid correction, 4 multiply by n, 8 uniform weighting, 32
-Hermitian fold of the measurements with w < 0).
+Hermitian fold of the measurements with w < 0), and optionally ``w_support``
+(planes per measurement, Eq. 3's kernel in w; 0 or 1 = the nearest plane).
 
 Pins (tests/test_oracle_pins.py): FFT against numpy, I0 against scipy, taper
 against the closed-form Fourier transforms of the truncated Gaussian and of
@@ -90,7 +91,10 @@ def _cfg(p):
 
 
 def _flags(p, flags):
-    return int(p.get("flags", FLAG_CORRECT) if flags is None else flags)
+    """The flags word, with the w-support of p (``w_support``, 0/1 = nearest
+    plane) in bits 8..15."""
+    f = int(p.get("flags", FLAG_CORRECT) if flags is None else flags) & 0xff
+    return f | (int(p.get("w_support", 0) or 0) & 0xff) << 8
 
 
 def _vis_args(u, v, w, wt, vis):

@@ -67,6 +67,13 @@ typedef struct {
     double dw;                              /* plane width in w */
     /* binary32 copies used only for the integer decisions */
     float uvscale_f, half_n_f, half_s_f, wmin_f, invdw_f;
+    /* w-support (Eq. 3's kernel in w): sw planes per measurement with the
+     * kernel family of u and v, support sw, parameter wkparam; 1 = the
+     * nearest plane (Sec. 2.1).  half_sw_f: sw / 2 in binary32. */
+    int sw;
+    double wkparam;
+    float half_sw_f;
+    double wq[4097];  /* Simpson-weighted samples of h over [-sw/2, sw/2] (sw > 1) */
 } or_cfg;
 
 static int or_make_cfg(or_cfg* c, int n, int nw, double pixel_rad, double w_min,
@@ -87,7 +94,39 @@ static int or_make_cfg(or_cfg* c, int n, int nw, double pixel_rad, double w_min,
     c->half_s_f = (float)(0.5 * support);
     c->wmin_f = (float)w_min;
     c->invdw_f = (nw > 1) ? (float)(1.0 / c->dw) : 0.0f;
+    c->sw = 1;
+    c->wkparam = 0.0;
+    c->half_sw_f = 0.5f;
     return 0;
+}
+
+/* The w-support rides in bits 8..15 of the flags (0 or 1: nearest plane). */
+#define OR_WSUPPORT(flags) ((int)(((flags) >> 8) & 0xffu))
+#define OR_MAX_WSUPPORT 16
+
+static int or_set_wsupport(or_cfg* c, unsigned flags)
+{
+    int sw = OR_WSUPPORT(flags);
+    if (sw < 1) sw = 1;
+    if (sw > OR_MAX_WSUPPORT || (sw > 1 && c->nw < sw)) return -1;
+    c->sw = sw;
+    c->wkparam = (c->kernel == OR_GAUSS) ? sw / 6.0 : 2.34 * sw;
+    c->half_sw_f = (float)(0.5 * sw);
+    return 0;
+}
+
+static double or_kernel_w(const or_cfg* c, double x);
+
+/* Samples of the w correction's quadrature (after or_set_wsupport). */
+static void or_prepare_wcorr(or_cfg* c)
+{
+    if (c->sw == 1) return;
+    const int K = 4096;
+    const double a = -0.5 * c->sw, h = (double)c->sw / K;
+    for (int i = 0; i <= K; ++i) {
+        double q = (i == 0 || i == K) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+        c->wq[i] = q * or_kernel_w(c, a + i * h);
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -121,6 +160,19 @@ static double or_kernel(const or_cfg* c, double x)
     return oracle_bessel_i0(c->kparam * sqrt(a));
 }
 
+/* The kernel in w: the same family with support sw, at x plane widths. */
+static double or_kernel_w(const or_cfg* c, double x)
+{
+    if (c->kernel == OR_GAUSS) {
+        double s = c->wkparam;
+        return exp(-x * x / (2.0 * s * s));
+    }
+    double t = 2.0 * x / c->sw;
+    double a = 1.0 - t * t;
+    if (a < 0.0) a = 0.0;
+    return oracle_bessel_i0(c->wkparam * sqrt(a));
+}
+
 double oracle_kernel(int kernel, int support, double kparam, double x)
 {
     or_cfg c;
@@ -133,10 +185,11 @@ double oracle_kernel(int kernel, int support, double kparam, double x)
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-    int k;          /* w-plane */
+    int k;          /* w-plane (sw = 1), first plane of the w-footprint (sw > 1) */
     int fu, fv;     /* first footprint cell */
     int cu, cv;     /* nearest cell (density grid) */
     double pu, pv;  /* continuous cell coordinates, FP64 */
+    double pw;      /* continuous plane coordinate (plane k's centre at k), FP64 */
 } or_place;
 
 /* Returns 1 when the measurement is gridded, 0 when it is dropped (a
@@ -159,13 +212,18 @@ static int oracle_place(const or_cfg* c, float u, float v, float w, or_place* pl
     if (pl->cv > c->n - 1) pl->cv = c->n - 1;
     if (c->nw == 1) {
         pl->k = 0;
-    } else {
+    } else if (c->sw == 1) {
         float t = (w - c->wmin_f) * c->invdw_f;
         float fk = floorf(t);
         if (fk < 0.0f) pl->k = 0;
         else if (fk > (float)(c->nw - 1)) pl->k = c->nw - 1;
         else pl->k = (int)fk;
+    } else {
+        /* planes fk .. fk + sw - 1, fk = floor(pw - sw/2) + 1, like a uv footprint */
+        float pw32 = (w - c->wmin_f) * c->invdw_f - 0.5f;
+        pl->k = (int)floorf(pw32 - c->half_sw_f) + 1;
     }
+    pl->pw = ((double)w - c->w_min) / c->dw - 0.5;
     /* FP64 continuous positions */
     pl->pu = (double)u * c->uvscale + 0.5 * c->n;
     pl->pv = (double)v * c->uvscale + 0.5 * c->n;
@@ -181,6 +239,35 @@ static void or_taps(const or_cfg* c, int f, double p, double* g)
         s += g[t];
     }
     for (int t = 0; t < c->support; ++t) g[t] /= s;
+}
+
+/* Weight of plane k for a placed measurement: 1 for its nearest plane
+ * (sw = 1), else the normalised w-tap h(k - pw) / sum_t h(fk + t - pw) when
+ * k lies in fk .. fk + sw - 1 (planes outside 0 .. nw-1 are dropped with
+ * their taps); 0 otherwise. */
+static double or_plane_weight(const or_cfg* c, const or_place* pl, int k)
+{
+    if (c->sw == 1) return k == pl->k ? 1.0 : 0.0;
+    int t = k - pl->k;
+    if (t < 0 || t >= c->sw) return 0.0;
+    double s = 0.0;
+    for (int q = 0; q < c->sw; ++q) s += or_kernel_w(c, (double)(pl->k + q) - pl->pw);
+    return or_kernel_w(c, (double)k - pl->pw) / s;
+}
+
+/* Grid correction in w (sw > 1): hw(xi) = int h(x) cos(2 pi x xi) dx / int h
+ * over [-sw/2, sw/2] (Simpson, 4096 intervals), the factor the stacked image
+ * is divided by at xi = dw (n - 1). */
+static double or_wcorr(const or_cfg* c, double xi)
+{
+    const int K = 4096;
+    const double a = -0.5 * c->sw, h = (double)c->sw / K;
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i <= K; ++i) {
+        num += c->wq[i] * cos(OR_TWO_PI * (a + i * h) * xi);
+        den += c->wq[i];
+    }
+    return num / den;
 }
 
 static double or_plane_w(const or_cfg* c, int k)
@@ -259,8 +346,8 @@ static int64_t or_weights(const or_cfg* c, int uniform, int64_t m, const float* 
 /* ------------------------------------------------------------------------ */
 
 /* planes: complex double [k1-k0][n][n] (row = v cell, column = u cell),
- * accumulated into (caller zeroes).  Only measurements whose plane lies in
- * [k0, k1) are gridded. */
+ * accumulated into (caller zeroes).  Only planes k0 .. k1-1 are gridded,
+ * each measurement with its weight on that plane (or_plane_weight). */
 static void or_grid(const or_cfg* c, int64_t m, const float* u, const float* v,
                     const float* w, const float* vis, const double* weff, int k0,
                     int k1, double complex* planes)
@@ -271,14 +358,17 @@ static void or_grid(const or_cfg* c, int64_t m, const float* u, const float* v,
         if (weff[i] == 0.0) continue;
         or_place pl;
         if (!oracle_place(c, u[i], v[i], w[i], &pl)) continue;
-        if (pl.k < k0 || pl.k >= k1) continue;
         or_taps(c, pl.fu, pl.pu, gu);
         or_taps(c, pl.fv, pl.pv, gv);
-        double complex a = weff[i] * ((double)vis[2 * i] + I * (double)vis[2 * i + 1]);
-        double complex* P = planes + (size_t)(pl.k - k0) * nn;
-        for (int r = 0; r < c->support; ++r)
-            for (int q = 0; q < c->support; ++q)
-                P[(size_t)(pl.fv + r) * c->n + (pl.fu + q)] += a * gv[r] * gu[q];
+        for (int k = k0; k < k1; ++k) {
+            const double hk = or_plane_weight(c, &pl, k);
+            if (hk == 0.0) continue;
+            double complex a = hk * weff[i] * ((double)vis[2 * i] + I * (double)vis[2 * i + 1]);
+            double complex* P = planes + (size_t)(k - k0) * nn;
+            for (int r = 0; r < c->support; ++r)
+                for (int q = 0; q < c->support; ++q)
+                    P[(size_t)(pl.fv + r) * c->n + (pl.fu + q)] += a * gv[r] * gu[q];
+        }
     }
 }
 
@@ -487,6 +577,7 @@ static double complex or_finalize_pixel(const or_cfg* c, unsigned flags, const d
     double complex d = (sum_w != 0.0) ? s / sum_w : 0.0;
     if (flags & OR_FLAG_CORRECT) d /= taper[x] * taper[y];
     if (flags & OR_FLAG_APPLY_N) d *= 1.0 + nm1;
+    if (c->sw > 1) d /= or_wcorr(c, c->dw * nm1);
     return d;
 }
 
@@ -500,6 +591,8 @@ int64_t oracle_grid(int n, int nw, double pixel_rad, double w_min, double w_max,
 {
     or_cfg c;
     if (or_make_cfg(&c, n, nw, pixel_rad, w_min, w_max, kernel, support, kparam)) return -1;
+    if (or_set_wsupport(&c, flags)) return -1;
+    or_prepare_wcorr(&c);
     if (k0 < 0 || k1 > nw || k0 > k1) return -1;
     or_fold_buf fold_buf;
     or_fold(flags, m, &u, &v, &w, &vis, &fold_buf);
@@ -527,6 +620,8 @@ int64_t oracle_dirty_image(int n, int nw, double pixel_rad, double w_min, double
 {
     or_cfg c;
     if (or_make_cfg(&c, n, nw, pixel_rad, w_min, w_max, kernel, support, kparam)) return -1;
+    if (or_set_wsupport(&c, flags)) return -1;
+    or_prepare_wcorr(&c);
     if (k0 < 0 || k1 > nw || k0 > k1) return -1;
     or_fold_buf fold_buf;
     or_fold(flags, m, &u, &v, &w, &vis, &fold_buf);
@@ -582,6 +677,8 @@ int64_t oracle_image_at(int n, int nw, double pixel_rad, double w_min, double w_
 {
     or_cfg c;
     if (or_make_cfg(&c, n, nw, pixel_rad, w_min, w_max, kernel, support, kparam)) return -1;
+    if (or_set_wsupport(&c, flags)) return -1;
+    or_prepare_wcorr(&c);
     or_fold_buf fold_buf;
     or_fold(flags, m, &u, &v, &w, &vis, &fold_buf);
     double* weff = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
@@ -610,7 +707,6 @@ int64_t oracle_image_at(int n, int nw, double pixel_rad, double w_min, double w_
             or_taps(&c, pl.fu, pl.pu, gu);
             or_taps(&c, pl.fv, pl.pv, gv);
             double complex a = weff[i] * ((double)vis[2 * i] + I * (double)vis[2 * i + 1]);
-            double wk = or_plane_w(&c, pl.k);
             for (int q = 0; q < npix; ++q) {
                 if (!sky[q]) continue;
                 int x = pix[2 * q], y = pix[2 * q + 1];
@@ -621,8 +717,15 @@ int64_t oracle_image_at(int n, int nw, double pixel_rad, double w_min, double w_
                     su += gu[t] * (cos(au) + I * sin(au));
                     sv += gv[t] * (cos(av) + I * sin(av));
                 }
-                double ph = OR_TWO_PI * wk * nm1[q];
-                part[q] += a * su * sv * (cos(ph) + I * sin(ph));
+                /* the screens of the planes the measurement is gridded onto */
+                double complex sw_sum = 0.0;
+                for (int k = 0; k < c.nw; ++k) {
+                    const double hk = or_plane_weight(&c, &pl, k);
+                    if (hk == 0.0) continue;
+                    double ph = OR_TWO_PI * or_plane_w(&c, k) * nm1[q];
+                    sw_sum += hk * (cos(ph) + I * sin(ph));
+                }
+                part[q] += a * su * sv * sw_sum;
             }
         }
 #pragma omp critical
@@ -654,6 +757,8 @@ int64_t oracle_dft(int n, int nw, double pixel_rad, double w_min, double w_max,
 {
     or_cfg c;
     if (or_make_cfg(&c, n, nw, pixel_rad, w_min, w_max, kernel, support, kparam)) return -1;
+    if (or_set_wsupport(&c, flags)) return -1;
+    or_prepare_wcorr(&c);
     or_fold_buf fold_buf;
     or_fold(flags, m, &u, &v, &w, &vis, &fold_buf);
     double* weff = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
@@ -697,6 +802,8 @@ static int64_t or_degrid(int n, int nw, double pixel_rad, double w_min, double w
 {
     or_cfg c;
     if (or_make_cfg(&c, n, nw, pixel_rad, w_min, w_max, kernel, support, kparam)) return -1;
+    if (or_set_wsupport(&c, flags)) return -1;
+    or_prepare_wcorr(&c);
     const float* w_given = w;  /* signs before the fold: mirrored gradients are conjugated */
     or_fold_buf fold_buf;
     or_fold(flags, m, &u, &v, &w, &vis, &fold_buf);
@@ -730,7 +837,9 @@ static int64_t or_degrid(int n, int nw, double pixel_rad, double w_min, double w
         for (int64_t i = 0; i < m; ++i) {
             if (weff[i] == 0.0) continue;
             or_place pl;
-            if (!oracle_place(&c, u[i], v[i], w[i], &pl) || pl.k != k) continue;
+            if (!oracle_place(&c, u[i], v[i], w[i], &pl)) continue;
+            const double hk = or_plane_weight(&c, &pl, k);
+            if (hk == 0.0) continue;
             double gu[OR_MAX_SUPPORT], gv[OR_MAX_SUPPORT];
             or_taps(&c, pl.fu, pl.pu, gu);
             or_taps(&c, pl.fv, pl.pv, gv);
@@ -738,7 +847,7 @@ static int64_t or_degrid(int n, int nw, double pixel_rad, double w_min, double w
             for (int rr = 0; rr < c.support; ++rr)
                 for (int q = 0; q < c.support; ++q)
                     s += gv[rr] * gu[q] * F[(size_t)(pl.fv + rr) * n + (pl.fu + q)];
-            g[i] = weff[i] * s;
+            g[i] += hk * weff[i] * s;
         }
     }
     free(F);

@@ -499,6 +499,103 @@ def test_w_error_shrinks_with_more_planes(oracle_mod):
     assert errs[1] < errs[0] / 2.5 and errs[2] < errs[1] / 2.5, errs
 
 
+def _kb_ft(xi, support, beta):
+    """Closed-form Fourier transform of the Kaiser-Bessel window over
+    [-S/2, S/2] at frequency xi (cycles per unit), normalised to 1 at 0."""
+    a = beta ** 2 - (np.pi * support * np.asarray(xi, dtype=np.float64)) ** 2
+    out = np.ones_like(a)
+    pos, neg = a > 0, a < 0
+    out[pos] = np.sinh(np.sqrt(a[pos])) / np.sqrt(a[pos])
+    out[neg] = np.sin(np.sqrt(-a[neg])) / np.sqrt(-a[neg])
+    out[a == 0] = 1.0
+    return out / (np.sinh(beta) / beta)
+
+
+def _w_alias_bound(sw, xi_max):
+    """max over the measurement's sub-plane offset and |xi| <= xi_max of
+    |sum_t h_t e^{2 pi i x_t xi} / h^(xi) - 1| for the normalised KB w-taps of
+    support sw: the relative error of gridding in w + correction in w."""
+    beta = 2.34 * sw
+    xi = np.linspace(-xi_max, xi_max, 129)
+    worst = 0.0
+    for phi in np.linspace(0, 1, 401, endpoint=False):
+        pw = 50.0 + phi
+        fk = math.floor(pw - sw / 2) + 1
+        x = fk + np.arange(sw) - pw
+        h = sp.i0(beta * np.sqrt(np.maximum(0.0, 1 - (2 * x / sw) ** 2)))
+        h = h / h.sum()
+        hd = (h[None, :] * np.exp(2j * np.pi * np.outer(xi, x))).sum(1)
+        worst = max(worst, np.max(np.abs(hd / _kb_ft(xi, sw, beta) - 1)))
+    return worst * 1.02
+
+
+def _padded_w(q, sw, wmax):
+    """Plane range of nw planes padded by sw/2 planes each side of [-wmax, wmax],
+    so every measurement's w-footprint lies on the planes."""
+    nw = q["nw"]
+    half = wmax / (1.0 - (sw + 1.0) / nw)
+    return dict(q, w_min=-half, w_max=half, w_support=sw)
+
+
+def test_w_gridding_against_direct_dft(oracle_mod):
+    """Eq. 3's kernel in w (w-support 4 on 16 planes): against the direct DFT
+    with the exact w-term over the central half, within the bound of uv
+    gridding + correction (e_a per axis) and w gridding + correction (e_w);
+    nearest-plane w-stacking on the same planes (w snapped by up to dw/2, a
+    phase error of up to pi dw |n-1|) is several times further off."""
+    nw, sw, wmax = 16, 4, 400.0
+    p, src = _dft_problem(nw, seed=47, wmax=wmax)
+    q = _padded_w(p["params"], sw, wmax)
+    n, S = q["n"], q["support"]
+    xs = np.arange(n // 4, 3 * n // 4)
+    pix = np.array([(x, y) for y in xs for x in xs], np.int32)
+    img, sw_sum, _ = oracle_mod.dirty_image(q, p["u"], p["v"], p["w"], p["wt"], p["vis"], flags=CORRECT)
+    ws = img[pix[:, 1], pix[:, 0]]
+    at = oracle_mod.image_at(q, p["u"], p["v"], p["w"], p["wt"], p["vis"], pix, flags=CORRECT)
+    assert np.max(np.abs(at - ws)) < 1e-10 * np.max(np.abs(ws))
+    ref = oracle_mod.dft(q, p["u"], p["v"], p["w"], p["wt"], p["vis"], pix, flags=CORRECT)
+    beta = 2.34 * S
+    e_a = _alias_bound(KB, S, beta, 0.25, lambda nn: kb_taper(nn, S, beta))
+    dl = q["pixel_rad"]
+    r2 = (((pix[:, 0] - n // 2) * dl) ** 2 + ((pix[:, 1] - n // 2) * dl) ** 2)
+    nm1 = r2 / (1 + np.sqrt(1 - r2))
+    dw = (q["w_max"] - q["w_min"]) / nw
+    e_w = _w_alias_bound(sw, dw * nm1.max())
+    amp = np.sum(np.abs(p["vis"].astype(np.complex128)) * p["wt"]) / sw_sum
+    bound = amp * ((1 + e_a) ** 2 * (1 + e_w) - 1)
+    err = np.abs(ws - ref)
+    assert np.all(err <= bound), (err.max(), bound)
+    q1 = dict(q, w_support=1)
+    near, _, _ = oracle_mod.dirty_image(q1, p["u"], p["v"], p["w"], p["wt"], p["vis"], flags=CORRECT)
+    assert np.max(np.abs(near[pix[:, 1], pix[:, 0]] - ref)) > 5 * err.max()
+
+
+def test_w_gridding_keeps_the_gridded_sum(oracle_mod):
+    """Normalised taps in u, v and w: the planes of a w-support-5 grid sum to
+    the weighted visibility sum."""
+    p = _small(n=64, nw=10, m=2000, support=7, seed=53, weights="random")
+    q = _padded_w(p["params"], 5, 50.0)
+    planes, sw, _ = oracle_mod.grid(q, p["u"], p["v"], p["w"], p["wt"], p["vis"])
+    placed = oracle_mod.place(q, p["u"], p["v"], p["w"])[0] >= 0
+    total = np.sum((p["wt"].astype(np.float64) * p["vis"].astype(np.complex128))[placed])
+    assert abs(planes.sum() - total) <= 1e-12 * np.sum(np.abs(p["vis"]) * p["wt"])
+
+
+def test_w_gridding_adjoint_dot_product(oracle_mod):
+    p = _small(n=32, nw=6, m=700, support=7, seed=59, weights="random", fov=8.0, wmax=90.0)
+    q = _padded_w(p["params"], 3, 90.0)
+    rng = np.random.default_rng(6)
+    m = p["u"].shape[0]
+    x = (rng.standard_normal(m) + 1j * rng.standard_normal(m)).astype(np.complex64)
+    y = rng.standard_normal((32, 32)) + 1j * rng.standard_normal((32, 32))
+    for flags in (CORRECT, CORRECT | APPLY_N | UNIFORM):
+        Ax, _, _ = oracle_mod.dirty_image(q, p["u"], p["v"], p["w"], p["wt"], x, flags=flags)
+        AHy = oracle_mod.degrid(q, p["u"], p["v"], p["w"], p["wt"], x, y, flags=flags)
+        lhs = np.vdot(y, Ax)
+        rhs = np.vdot(AHy, x.astype(np.complex128))
+        assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
 def test_phase_screen_sign_matters(oracle_mod):
     """Guards the w-term: with the screen's sign flipped (w -> -w in the data
     while the DFT keeps +w), the source pixel loses most of its flux."""

@@ -66,7 +66,15 @@ typedef int32_t rick_status;
  * n: grid side, even, >= 2*support.  nw >= 1.  w_max > w_min when nw > 1.
  * support: kernel support S in cells, 1..16.  plane_group: w-planes resident
  * in HBM at once (0 = as many as fit).  tile: uv tile side of the gridder,
- * 16, 32 or 64 (0 = automatic); must be >= support. */
+ * 16, 32 or 64 (0 = automatic); must be >= support.  w_support: planes each
+ * measurement is gridded onto, Eq. 3's kernel in w (0 or 1: the nearest
+ * plane, Sec. 2.1; 2..16, at most nw: the sw planes fk .. fk+sw-1 around
+ * its continuous plane coordinate pw = (w - w_min)/dw - 1/2, fk =
+ * floor(pw - sw/2) + 1, with normalised taps of the kernel family of u and v
+ * (support sw, sigma sw/6 or beta 2.34 sw), and the image divided by that
+ * kernel's Fourier transform at dw (n - 1)).  Taps on planes outside
+ * 0 .. nw-1 are dropped, so [w_min, w_max] should extend sw/2 plane widths
+ * beyond the measurements' w.  Not available for batched handles. */
 typedef struct rick_params {
     int32_t n;
     int32_t nw;
@@ -79,7 +87,7 @@ typedef struct rick_params {
     int32_t plane_group;
     int32_t tile;
     uint32_t flags;
-    int32_t reserved;
+    int32_t w_support;
 } rick_params;
 
 typedef struct rick_stats {

@@ -11,7 +11,7 @@ Parameters are a mapping with keys ``n``, ``nw``, ``pixel_rad``, ``w_min``,
 ``w_max``, ``kernel`` (0 Gaussian, 1 Kaiser-Bessel), ``support``,
 ``kernel_param`` (0 = default sigma S/6 / beta 2.34 S), ``flags``
 (GRID_CORRECT | REAL_IMAGE | APPLY_N | UNIFORM_WEIGHT | HERMITIAN_FOLD), and optionally
-``plane_group`` and ``tile``.
+``plane_group``, ``tile`` and ``w_support``.
 """
 import ctypes
 
@@ -45,7 +45,7 @@ def _params_struct(p):
     rp.plane_group = int(p.get("plane_group", 0) or 0)
     rp.tile = int(p.get("tile", 0) or 0)
     rp.flags = int(p.get("flags", GRID_CORRECT | REAL_IMAGE))
-    rp.reserved = 0
+    rp.w_support = int(p.get("w_support", 0) or 0)
     return rp
 
 

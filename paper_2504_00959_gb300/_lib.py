@@ -28,7 +28,7 @@ class RickParams(ctypes.Structure):
                 ("w_min", ctypes.c_double), ("w_max", ctypes.c_double), ("kernel", ctypes.c_int32),
                 ("support", ctypes.c_int32), ("kernel_param", ctypes.c_double),
                 ("plane_group", ctypes.c_int32), ("tile", ctypes.c_int32), ("flags", ctypes.c_uint32),
-                ("reserved", ctypes.c_int32)]
+                ("w_support", ctypes.c_int32)]
 
 
 class RickStats(ctypes.Structure):

@@ -128,6 +128,15 @@ rick_status check_params(const rick_params* p, GridCfg* c, double* kparam, char*
     c->kernel = p->kernel;
     c->kp = (p->kernel == RICK_KERNEL_GAUSS) ? (float)(1.0 / (2.0 * kp * kp)) : (float)kp;
     c->two_over_s = (float)(2.0 / p->support);
+    if (p->w_support < 0 || p->w_support > kMaxWSupport || p->w_support > p->nw) {
+        snprintf(msg, msglen, "w_support must be in [0, min(16, nw)] (got %d)", p->w_support);
+        return RICK_ERR_ARG;
+    }
+    c->Sw = p->w_support > 1 ? p->w_support : 1;
+    c->half_sw = 0.5f * (float)c->Sw;
+    c->two_over_sw = 2.0f / (float)c->Sw;
+    c->wkp = (p->kernel == RICK_KERNEL_GAUSS) ? (float)(1.0 / (2.0 * (c->Sw / 6.0) * (c->Sw / 6.0)))
+                                              : (float)(2.34 * c->Sw);
     c->uniform = (p->flags & RICK_UNIFORM_WEIGHT) ? 1 : 0;
     c->fold = (p->flags & RICK_HERMITIAN_FOLD) ? 1 : 0;
     c->nchan = 1;
@@ -243,7 +252,7 @@ void resolve_timer(rick_handle h, bool accumulate)
     }
 }
 
-int64_t entries_bound(const GridCfg& c, int64_t nvis) { return nvis * (c.S > 1 ? 4 : 1); }
+int64_t entries_bound(const GridCfg& c, int64_t nvis) { return nvis * (c.S > 1 ? 4 : 1) * c.Sw; }
 
 rick_status check_vis_args(rick_handle h, const float* vis, const float* u, const float* v, const float* w,
                            int64_t nvis)
@@ -365,7 +374,7 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
         return RICK_ERR_ARG;
     }
     if (nchan > 1 || w_min) {
-        if (!w_min || !w_max || (p->flags & RICK_UNIFORM_WEIGHT)) {
+        if (!w_min || !w_max || (p->flags & RICK_UNIFORM_WEIGHT) || p->w_support > 1) {
             delete h;
             return RICK_ERR_ARG;
         }
@@ -471,6 +480,15 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
                     ((p->flags & RICK_UNIFORM_WEIGHT) ? (size_t)c.n * c.n * 4 : 0);
     if (cudaMemset(h->ctr, 0, sizeof(Counters)) != cudaSuccess) return cleanup(RICK_ERR_CUDA);
     if (launch_taper(c, h->kernel_param, h->taper, nullptr) != cudaSuccess) return cleanup(RICK_ERR_CUDA);
+    if (c.Sw > 1) {
+        // -(n - 1) over the image reaches its largest value at the corners
+        const double half = 0.5 * p->n * p->pixel_rad, r2 = 2.0 * half * half;
+        const double umax = r2 >= 1.0 ? 1.0 : r2 / (1.0 + std::sqrt(1.0 - r2));
+        const double dw = (p->w_max - p->w_min) / p->nw;
+        if (cudaMalloc((void**)&h->wcorr, sizeof(float) * kWcorrLen) != cudaSuccess) return cleanup(RICK_ERR_OOM);
+        if (launch_wcorr(c, dw * umax, kWcorrLen, h->wcorr, nullptr) != cudaSuccess) return cleanup(RICK_ERR_CUDA);
+        h->wc_scale = (float)((kWcorrLen - 1) / umax);
+    }
     {
         // kernel tap polynomials: fitted on the device, carried in the kernel parameters
         float* d_coef = nullptr;
@@ -535,6 +553,7 @@ rick_status rick_destroy(rick_handle h)
     cudaFree(h->density);
     cudaFree(h->ctr);
     cudaFree(h->one);
+    cudaFree(h->wcorr);
     cudaFree(h->fft_work);
     cudaFree(h->stage);
     cudaFree(h->img_dev);
@@ -661,6 +680,8 @@ rick_status rick_fft_and_stack(rick_handle h, float* image)
     split(p.w_min + 0.5 * dw, &a.wb_hi, &a.wb_lo);
     split(dw, &a.dw_hi, &a.dw_lo);
     a.flags = p.flags;
+    a.wcorr = h->cfg.Sw > 1 ? h->wcorr : nullptr;
+    a.wc_scale = h->wc_scale;
     for (int k0 = 0; k0 < p.nw; k0 += h->G) {
         const int nk = (p.nw - k0 < h->G) ? p.nw - k0 : h->G;
         rick_status s = grid_pass(h, k0, nk, true, h->planes);
@@ -717,6 +738,8 @@ static rick_status degrid_impl(rick_handle h, const GridCfg& c, const double* su
     split(p.w_min + 0.5 * dw, &a.wb_hi, &a.wb_lo);
     split(dw, &a.dw_hi, &a.dw_lo);
     a.flags = p.flags;
+    a.wcorr = h->cfg.Sw > 1 ? h->wcorr : nullptr;
+    a.wc_scale = h->wc_scale;
     rick_status st = RICK_OK;
     e = cudaMemsetAsync(grad, 0, (size_t)nvis * sizeof(float2), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->cursor, 0, (size_t)ntiles * sizeof(uint32_t), h->stream);

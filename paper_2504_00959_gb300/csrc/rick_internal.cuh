@@ -33,6 +33,9 @@ struct GridCfg {
     float kp;                        // Gaussian: 1/(2 sigma^2); KB: beta
     float two_over_s;                // 2 / S
     int uniform;                     // uniform weighting on
+    // w-support (Eq. 3's kernel in w): Sw planes per measurement; 1 = nearest
+    int Sw;
+    float half_sw, wkp, two_over_sw; // Sw/2; Gaussian 1/(2 sigma_w^2) or KB beta_w; 2/Sw
     int fold;                        // RICK_HERMITIAN_FOLD: mirror measurements with w < 0
     // batched imaging: nchan channels with nw_chan w-planes each, channel c
     // owning planes c*nw_chan .. (c+1)*nw_chan-1 and measurements
@@ -52,9 +55,10 @@ struct GridCfg {
 // cell coordinates.  Every float->int decision is binary32 with the
 // operation order written out (explicit _rn intrinsics, no contraction).
 struct Place {
-    int k, fu, fv;
+    int k, fu, fv;  // k: the plane (Sw = 1) or the first plane of the w-footprint (may be off the range)
     float pu, pv;
-    bool conj;  // imaged as the Hermitian mirror: use conj(V)
+    float pw;       // continuous plane coordinate, plane k's centre at k (Sw > 1)
+    bool conj;      // imaged as the Hermitian mirror: use conj(V)
 };
 
 __device__ __forceinline__ bool place(const GridCfg& c, float u, float v, float w, Place& p, int chan = 0)
@@ -83,9 +87,15 @@ __device__ __forceinline__ bool place(const GridCfg& c, float u, float v, float 
             wmin = cw.x;
             invdw = cw.y;
         }
-        float fk = floorf(__fmul_rn(__fsub_rn(w, wmin), invdw));
-        const int k = (fk < 0.0f) ? 0 : ((fk > (float)(c.nw_chan - 1)) ? c.nw_chan - 1 : (int)fk);
-        p.k = chan * c.nw_chan + k;
+        if (c.Sw == 1) {
+            float fk = floorf(__fmul_rn(__fsub_rn(w, wmin), invdw));
+            const int k = (fk < 0.0f) ? 0 : ((fk > (float)(c.nw_chan - 1)) ? c.nw_chan - 1 : (int)fk);
+            p.k = chan * c.nw_chan + k;
+        } else {
+            // planes fk .. fk + Sw - 1, fk = floor(pw - Sw/2) + 1 (one channel)
+            p.pw = __fsub_rn(__fmul_rn(__fsub_rn(w, wmin), invdw), 0.5f);
+            p.k = (int)floorf(__fsub_rn(p.pw, c.half_sw)) + 1;
+        }
     }
     p.pu = pu;
     p.pv = pv;
@@ -145,6 +155,25 @@ __device__ __forceinline__ float tap_sum(const GridCfg& c, float p, int f)
     return s;
 }
 
+constexpr int kMaxWSupport = 16;
+
+// Un-normalised kernel in w at x plane widths from the measurement (Sw > 1).
+__device__ __forceinline__ float w_kernel(const GridCfg& c, float x)
+{
+    if (c.kernel == RICK_KERNEL_GAUSS) return __expf(-x * x * c.wkp);
+    const float z = x * c.two_over_sw;
+    return cyl_bessel_i0f(c.wkp * sqrtf(fmaxf(0.0f, 1.0f - z * z)));
+}
+
+// 1 / (sum of a placed measurement's Sw w-taps); its weight on plane p.k + t
+// is w_kernel(c, (p.k + t) - p.pw) times this.
+__device__ __forceinline__ float w_tap_norm(const GridCfg& c, const Place& p)
+{
+    float s = 0.0f;
+    for (int t = 0; t < c.Sw; ++t) s += w_kernel(c, __fsub_rn((float)(p.k + t), p.pw));
+    return 1.0f / s;
+}
+
 // Coefficients of the tap-sum polynomial from the S tap polynomials (host).
 inline void set_tap_sum(GridCfg& c)
 {
@@ -197,18 +226,36 @@ cudaError_t launch_grid(const GridCfg& c, const ChunkList& chunks, int k0, int n
                         bool accumulate, uint32_t* heavy, size_t heavy_words, float2* planes, cudaStream_t s);
 size_t heavy_words_for(int64_t max_entries);
 cudaError_t launch_taper(const GridCfg& c, double kernel_param, float* taper, cudaStream_t s);
+// The Fourier transform of the w-kernel at xi_j = xi_max j / (len - 1), j < len.
+cudaError_t launch_wcorr(const GridCfg& c, double xi_max, int len, float* out, cudaStream_t s);
 // Fit the tap polynomials (coef: float[S][kPolyTerms]) and report the largest
 // binary32 evaluation error relative to the kernel's peak in *max_err.
 cudaError_t launch_fit_taps(const GridCfg& c, double kernel_param, float* coef, double* max_err, cudaStream_t s);
 
+constexpr int kWcorrLen = 4096;  // samples of the grid correction in w
+
 struct StackArgs {
     int n, k0, nk;
+    const float* wcorr;              // grid correction in w (w-support > 1), else NULL:
+    float wc_scale;                  // table index per unit of -(n - 1)
     float dl2_hi, dl2_lo;            // pixel_rad^2 as a float pair
     float wb_hi, wb_lo;              // w_min + dw/2 as a float pair
     float dw_hi, dw_lo;              // dw as a float pair
     int first, last;                 // first / last plane group
     unsigned flags;
 };
+// The grid correction in w at a pixel with n - 1 = nm1 (linear interpolation
+// of the table; 1 without w-support).
+__device__ __forceinline__ float wcorr_at(const StackArgs& a, float nm1)
+{
+    if (!a.wcorr) return 1.0f;
+    const float x = fminf(-nm1 * a.wc_scale, (float)(kWcorrLen - 1));
+    const int j = min((int)x, kWcorrLen - 2);
+    const float f = x - (float)j;
+    const float c0 = __ldg(a.wcorr + j), c1 = __ldg(a.wcorr + j + 1);
+    return __fmaf_rn(f, c1 - c0, c0);
+}
+
 // sum_w: the weight sum the image is normalised by (device)
 cudaError_t launch_stack(const StackArgs& a, const float2* planes, float2* acc, const float* taper,
                          const double* sum_w, void* image, cudaStream_t s);
@@ -266,6 +313,8 @@ struct rick_imager {
     uint32_t* density;               // [n][n] uniform weighting counts
     rick::Counters* ctr;             // device counters
     double* one;                     // device 1.0: the weight sum of unweighted prediction
+    float* wcorr;                    // [kWcorrLen] grid correction in w (w-support > 1)
+    float wc_scale;
     void* fft_work;
     size_t fft_work_bytes;
     std::map<int, cufftHandle> plans;// batch -> plan

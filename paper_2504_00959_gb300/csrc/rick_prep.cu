@@ -100,14 +100,14 @@ __global__ void __launch_bounds__(kPrepThreads) k_density(GridCfg c, Inputs in, 
     });
 }
 
-// Tiles touched by the footprint of a placed measurement: t[0] always, t[1]
+// Tiles of plane `plane` touched by the uv footprint of a placed measurement: t[0] always, t[1]
 // (right neighbour), t[2] (lower), t[3] (lower right) when the footprint
 // straddles; -1 otherwise.
-__device__ __forceinline__ void footprint_tiles(const GridCfg& c, const Place& p, int64_t (&t)[4])
+__device__ __forceinline__ void footprint_tiles(const GridCfg& c, const Place& p, int plane, int64_t (&t)[4])
 {
     const int tu0 = p.fu >> c.log2T, tu1 = (p.fu + c.S - 1) >> c.log2T;
     const int tv0 = p.fv >> c.log2T, tv1 = (p.fv + c.S - 1) >> c.log2T;
-    const int64_t base = (int64_t)p.k * c.ntp;
+    const int64_t base = (int64_t)plane * c.ntp;
     t[0] = base + tv0 * c.ntu + tu0;
     t[1] = tu1 != tu0 ? base + tv0 * c.ntu + tu1 : -1;
     t[2] = tv1 != tv0 ? base + tv1 * c.ntu + tu0 : -1;
@@ -135,11 +135,16 @@ __global__ void __launch_bounds__(kPrepThreads) k_count(GridCfg c, Inputs in, in
 #pragma unroll
             for (int q = 0; q < kVisPerThread; ++q) {
                 if (!ok[q]) continue;
-                int64_t t[4];
-                footprint_tiles(c, p[q], t);
+                // the measurement's planes: its own (Sw = 1) or its w-footprint
+                for (int tw = 0; tw < c.Sw; ++tw) {
+                    const int plane = p[q].k + tw;
+                    if (plane < 0 || plane >= c.nw) continue;
+                    int64_t t[4];
+                    footprint_tiles(c, p[q], plane, t);
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
-                    if (t[r] >= 0) atomicAdd(counts + t[r], 1u);
+                    for (int r = 0; r < 4; ++r)
+                        if (t[r] >= 0) atomicAdd(counts + t[r], 1u);
+                }
             }
         }
     });
@@ -210,7 +215,27 @@ __global__ void __launch_bounds__(kPrepThreads) k_scatter(GridCfg c, Inputs in, 
                 rec[q] = make_float4(p[q].pu, p[q].pv, scale * V[q].x, scale * V[q].y);
                 sw += wi[q];
                 ++gridded;
-                footprint_tiles(c, p[q], t[q]);
+                if (c.Sw > 1) {
+                    // w-footprint: one set of entries per plane, the w-tap in the scale
+                    const float hn = w_tap_norm(c, p[q]);
+                    for (int tw = 0; tw < c.Sw; ++tw) {
+                        const int plane = p[q].k + tw;
+                        if (plane < 0 || plane >= c.nw) continue;
+                        const float ht = w_kernel(c, __fsub_rn((float)plane, p[q].pw)) * hn;
+                        const float4 rw = make_float4(rec[q].x, rec[q].y, ht * rec[q].z, ht * rec[q].w);
+                        int64_t tt[4];
+                        footprint_tiles(c, p[q], plane, tt);
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+                            if (tt[r] >= 0) {
+                                entries[atomicAdd(cursor + tt[r], 1u)] = rw;
+                                ++nent;
+                            }
+                    }
+                    ok[q] = false;  // written: skip the nearest-plane stores below
+                    continue;
+                }
+                footprint_tiles(c, p[q], p[q].k, t[q]);
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
                     if (t[q][r] >= 0) slot[q][r] = atomicAdd(cursor + t[q][r], 1u);
@@ -263,9 +288,13 @@ __device__ __forceinline__ bool place_coords(const GridCfg& c, const Inputs& in,
     return place(c, __ldg(in.u + i), __ldg(in.v + i), __ldg(in.w + i), p, 0) && isfinite(wi);
 }
 
+// Sort key of the adjoint: the tile of the first footprint cell on the
+// measurement's plane (Sw = 1) or on the first plane of its w-footprint,
+// clamped to the plane range (Sw > 1).
 __device__ __forceinline__ int64_t primary_tile(const GridCfg& c, const Place& p)
 {
-    return (int64_t)p.k * c.ntp + (p.fv >> c.log2T) * c.ntu + (p.fu >> c.log2T);
+    const int k = p.k < 0 ? 0 : (p.k > c.nw - 1 ? c.nw - 1 : p.k);
+    return (int64_t)k * c.ntp + (p.fv >> c.log2T) * c.ntu + (p.fu >> c.log2T);
 }
 
 __global__ void __launch_bounds__(kPrepThreads) k_primary_count(GridCfg c, Inputs in, int64_t m,
@@ -302,7 +331,10 @@ __global__ void __launch_bounds__(kPrepThreads) k_degrid_gather(GridCfg c, const
                                                                 const uint32_t* __restrict__ density,
                                                                 float2* __restrict__ grad)
 {
-    const uint32_t b = off[(int64_t)k0 * c.ntp], e = off[(int64_t)(k0 + nk) * c.ntp];
+    // measurements whose planes reach [k0, k0 + nk): sort key plane in
+    // [k0 - Sw + 1, k0 + nk) (a contiguous run of the sorted list)
+    const int klo = k0 - (c.Sw - 1) > 0 ? k0 - (c.Sw - 1) : 0;
+    const uint32_t b = off[(int64_t)klo * c.ntp], e = off[(int64_t)(k0 + nk) * c.ntp];
     for (int64_t j = b + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < e;
          j += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t i = perm[j];
@@ -324,24 +356,41 @@ __global__ void __launch_bounds__(kPrepThreads) k_degrid_gather(GridCfg c, const
             gu[t] = -gu[t];
             gv[t] = -gv[t];
         }
-        const float2* P = planes + (int64_t)(p.k - k0) * c.n * c.n + (int64_t)p.fv * c.n + p.fu;
+        // its planes in this group: the one plane (Sw = 1), or the w-footprint
+        // with the normalised w-taps (Sw > 1)
+        const float hn = c.Sw > 1 ? w_tap_norm(c, p) : 1.0f;
         float ar = 0.f, ai = 0.f;
+        for (int tw = 0; tw < c.Sw; ++tw) {
+            const int plane = p.k + tw;
+            if (plane < k0 || plane >= k0 + nk) continue;
+            const float ht = c.Sw > 1 ? w_kernel(c, __fsub_rn((float)plane, p.pw)) * hn : 1.0f;
+            const float2* P = planes + (int64_t)(plane - k0) * c.n * c.n + (int64_t)p.fv * c.n + p.fu;
+            float cr = 0.f, ci = 0.f;
 #pragma unroll
-        for (int rr = 0; rr < S; ++rr) {
-            float br = 0.f, bi = 0.f;
+            for (int rr = 0; rr < S; ++rr) {
+                float br = 0.f, bi = 0.f;
 #pragma unroll
-            for (int t = 0; t < S; ++t) {
-                const float2 x = __ldg(P + (int64_t)rr * c.n + t);
-                br = fmaf(gu[t], x.x, br);
-                bi = fmaf(gu[t], x.y, bi);
+                for (int t = 0; t < S; ++t) {
+                    const float2 x = __ldg(P + (int64_t)rr * c.n + t);
+                    br = fmaf(gu[t], x.x, br);
+                    bi = fmaf(gu[t], x.y, bi);
+                }
+                cr = fmaf(gv[rr], br, cr);
+                ci = fmaf(gv[rr], bi, ci);
             }
-            ar = fmaf(gv[rr], br, ar);
-            ai = fmaf(gv[rr], bi, ai);
+            ar = fmaf(ht, cr, ar);
+            ai = fmaf(ht, ci, ai);
         }
         float scale = wi / (su * sv);
         if ((p.fu + p.fv) & 1) scale = -scale;
         // a mirrored measurement enters as conj(V): its gradient is conjugated
-        grad[i] = make_float2(ar * scale, p.conj ? -ai * scale : ai * scale);
+        const float2 gi = make_float2(ar * scale, p.conj ? -ai * scale : ai * scale);
+        if (c.Sw == 1) {
+            grad[i] = gi;
+        } else {  // a w-footprint can span plane groups: add this group's part
+            const float2 prev = grad[i];
+            grad[i] = make_float2(prev.x + gi.x, prev.y + gi.y);
+        }
     }
 }
 

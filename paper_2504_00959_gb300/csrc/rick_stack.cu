@@ -152,6 +152,10 @@ __global__ void __launch_bounds__(kStackThreads) k_stack(StackArgs a, const floa
         f0 *= 1.0f + s0.nm1;
         f1 *= 1.0f + s1.nm1;
     }
+    if (a.wcorr) {  // grid correction in w (w-support > 1)
+        f0 /= wcorr_at(a, s0.nm1);
+        f1 /= wcorr_at(a, s1.nm1);
+    }
     if (a.flags & RICK_REAL_IMAGE) {
         reinterpret_cast<float2*>(image)[pix >> 1] = make_float2(a0.x * f0, a1.x * f1);
     } else {
@@ -197,6 +201,10 @@ __global__ void __launch_bounds__(kStackThreads) k_spread(StackArgs a, const voi
     if (a.flags & RICK_APPLY_N) {
         f0 *= 1.0f + s0.nm1;
         f1 *= 1.0f + s1.nm1;
+    }
+    if (a.wcorr) {  // grid correction in w (w-support > 1)
+        f0 /= wcorr_at(a, s0.nm1);
+        f1 /= wcorr_at(a, s1.nm1);
     }
     // fftshift sign (-1)^(x + y) and the sky mask
     if (y & 1) f0 = -f0; else f1 = -f1;

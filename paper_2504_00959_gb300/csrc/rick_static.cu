@@ -90,7 +90,7 @@ extern "C" rick_status rick_grid_planes_static(const rick_params* p, const float
 
     // scratch layout: counters | coefficients | cursor (+1 word) | offsets | scan sums | density | entries
     const int64_t ntiles = (int64_t)c.nw * c.ntp;
-    const int64_t cap = nvis * (c.S > 1 ? 4 : 1);
+    const int64_t cap = nvis * (c.S > 1 ? 4 : 1) * c.Sw;
     const size_t o_ctr = 0;
     const size_t o_coef = o_ctr + align256(sizeof(Counters));
     const size_t o_err = o_coef + align256(sizeof(float) * kMaxSupport * kPolyTerms);

@@ -128,7 +128,73 @@ __global__ void k_fit_taps(GridCfg c, double kparam, float* __restrict__ coef, d
     max_err[t] = worst;
 }
 
+// Grid correction in w (w-support Sw > 1): hw(xi) = int h(x) cos(2 pi x xi)
+// dx / int h over [-Sw/2, Sw/2], h the kernel family with support Sw, at
+// xi_j = xi_max j / (len - 1); FP64 Simpson rule like the taper.
+__global__ void k_w_samples(GridCfg c, double* __restrict__ g)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > kTaperIntervals) return;
+    const double a = -0.5 * c.Sw, h = (double)c.Sw / kTaperIntervals;
+    const double t = a + i * h;
+    double val;
+    if (c.kernel == RICK_KERNEL_GAUSS) {
+        const double sig = c.Sw / 6.0;
+        val = exp(-t * t / (2.0 * sig * sig));
+    } else {
+        const double z = 2.0 * t / c.Sw;
+        val = cyl_bessel_i0(2.34 * c.Sw * sqrt(fmax(0.0, 1.0 - z * z)));
+    }
+    const double wgt = (i == 0 || i == kTaperIntervals) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+    g[i] = wgt * val;
+}
+
+__global__ void __launch_bounds__(kTaperThreads) k_wcorr(GridCfg c, const double* __restrict__ g, double xi_max,
+                                                         int len, float* __restrict__ out)
+{
+    const int j = blockIdx.x;
+    const double a = -0.5 * c.Sw, h = (double)c.Sw / kTaperIntervals;
+    const double xi2 = 2.0 * xi_max * j / (len - 1);  // cos(2 pi x xi) = cospi(x * 2 xi)
+    double num = 0.0, den = 0.0;
+    for (int i = threadIdx.x; i <= kTaperIntervals; i += kTaperThreads) {
+        num += g[i] * cospi((a + i * h) * xi2);
+        den += g[i];
+    }
+    __shared__ double sn[kTaperThreads / 32], sd[kTaperThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sn[threadIdx.x >> 5] = num;
+        sd[threadIdx.x >> 5] = den;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tn = 0.0, td = 0.0;
+        for (int k = 0; k < kTaperThreads / 32; ++k) {
+            tn += sn[k];
+            td += sd[k];
+        }
+        out[j] = (float)(tn / td);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_wcorr(const GridCfg& c, double xi_max, int len, float* out, cudaStream_t s)
+{
+    double* g = nullptr;
+    cudaError_t e = cudaMalloc((void**)&g, sizeof(double) * (kTaperIntervals + 1));
+    if (e != cudaSuccess) return e;
+    k_w_samples<<<(kTaperIntervals + 256) / 256, 256, 0, s>>>(c, g);
+    k_wcorr<<<len, kTaperThreads, 0, s>>>(c, g, xi_max, len, out);
+    e = cudaGetLastError();
+    const cudaError_t e2 = cudaStreamSynchronize(s);
+    cudaFree(g);
+    return e != cudaSuccess ? e : e2;
+}
 
 cudaError_t launch_fit_taps(const GridCfg& c, double kernel_param, float* coef, double* max_err, cudaStream_t s)
 {

@@ -80,6 +80,14 @@ def test_workspace_size_and_parameter_checks(lib):
     assert lib.rick_workspace_size(ctypes.byref(q), 10, ctypes.byref(size)) == 1
     q.nw = 1
     assert lib.rick_workspace_size(ctypes.byref(q), 10, ctypes.byref(size)) == 0
+    # w-support: at most 16 and at most nw
+    for ws, nw, ok in ((17, 32, False), (9, 8, False), (4, 8, True), (0, 1, True), (-1, 8, False)):
+        q = _lib.RickParams()
+        lib.rick_params_default(ctypes.byref(q))
+        q.nw, q.w_support = nw, ws
+        if nw == 1:
+            q.w_max = q.w_min + 1.0
+        assert (lib.rick_workspace_size(ctypes.byref(q), 10, ctypes.byref(size)) == 0) == ok, (ws, nw)
     # the Hermitian fold changes the imaginary part: only with real images
     q = _lib.RickParams()
     lib.rick_params_default(ctypes.byref(q))

@@ -201,6 +201,9 @@ def main():
     ap.add_argument("--fold", action="store_true",
                     help="Hermitian fold (real image): measurements with w < 0 mirrored, half the w-planes "
                          "over [0, max |w|] at the same plane spacing")
+    ap.add_argument("--w-support", type=int, default=0,
+                    help="planes per measurement (Eq. 3's kernel in w); the plane range is padded by "
+                         "nw / (nw - w_support) so every footprint lies on the planes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--workload", choices=["wstack", "channels", "adjoint"], default="wstack",
@@ -238,6 +241,10 @@ def main():
         wabs = max(abs(params["w_min"]), abs(params["w_max"]))
         params = dict(params, nw=max(args.nw // 2, 1), w_min=0.0, w_max=wabs,
                       flags=params["flags"] | synth.FLAG_FOLD)
+    if args.w_support > 1:
+        lo, hi, nwp = params["w_min"], params["w_max"], params["nw"]
+        mid, half = 0.5 * (lo + hi), 0.5 * (hi - lo) * nwp / (nwp - args.w_support)
+        params = dict(params, w_min=mid - half, w_max=mid + half, w_support=args.w_support)
     im = rick.Imager(params, device=dev)
     img = torch.empty((params["n"], params["n"]), dtype=torch.float32, device=dev)
     m = prob["u"].numel()
@@ -346,7 +353,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": DATA,
         "config": {"workload": WORKLOAD + ("; Hermitian fold: %d w-planes over [0, max |w|]" % nw if args.fold
-                                           else ""),
+                                           else "") +
+                   ("; w-support %d on %d planes" % (args.w_support, nw) if args.w_support > 1 else ""),
                    "n": n, "nw": nw, "nvis": m, "kernel": "kaiser-bessel", "support": 7,
                    "tile": st["tile"], "plane_group": st["plane_group"],
                    "l2": "inputs larger than L2 (4.3 GB of planes written and read every step)",

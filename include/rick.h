@@ -74,7 +74,10 @@ typedef int32_t rick_status;
  * (support sw, sigma sw/6 or beta 2.34 sw), and the image divided by that
  * kernel's Fourier transform at dw (n - 1)).  Taps on planes outside
  * 0 .. nw-1 are dropped, so [w_min, w_max] should extend sw/2 plane widths
- * beyond the measurements' w.  Not available for batched handles. */
+ * beyond the measurements' w.  The planes must sample the w-term: creation
+ * fails (RICK_ERR_ARG) when the correction falls below 1e-2 anywhere in the
+ * image (dw (1 - n) at the corners beyond the w-kernel's passband; add
+ * planes).  Not available for batched handles. */
 typedef struct rick_params {
     int32_t n;
     int32_t nw;

@@ -488,6 +488,13 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
         if (cudaMalloc((void**)&h->wcorr, sizeof(float) * kWcorrLen) != cudaSuccess) return cleanup(RICK_ERR_OOM);
         if (launch_wcorr(c, dw * umax, kWcorrLen, h->wcorr, nullptr) != cudaSuccess) return cleanup(RICK_ERR_CUDA);
         h->wc_scale = (float)((kWcorrLen - 1) / umax);
+        // beyond the w-kernel's passband the correction divides by ~0: refuse
+        std::vector<float> tab(kWcorrLen);
+        if (cudaMemcpy(tab.data(), h->wcorr, sizeof(float) * kWcorrLen, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return cleanup(RICK_ERR_CUDA);
+        float lo = tab[0];
+        for (float x : tab) lo = x < lo ? x : lo;
+        if (!(lo >= kMinWcorr)) return cleanup(RICK_ERR_ARG);
     }
     {
         // kernel tap polynomials: fitted on the device, carried in the kernel parameters

@@ -233,6 +233,7 @@ cudaError_t launch_wcorr(const GridCfg& c, double xi_max, int len, float* out, c
 cudaError_t launch_fit_taps(const GridCfg& c, double kernel_param, float* coef, double* max_err, cudaStream_t s);
 
 constexpr int kWcorrLen = 4096;  // samples of the grid correction in w
+constexpr float kMinWcorr = 1e-2f;  // smallest grid correction in w accepted over the image
 
 struct StackArgs {
     int n, k0, nk;

@@ -288,7 +288,9 @@ rick_status rick_set_timing(rick_handle h, int32_t enable);
 /* Phase times since timing was enabled (synchronises the stream). */
 rick_status rick_get_timing(rick_handle h, rick_timing* out);
 
-/* Message for the last failure on h (static storage of the handle). */
+/* Message for the last failure on h (static storage of the handle); with
+ * h = NULL, the message of the last failed rick_create / rick_create_batch
+ * on the calling thread. */
 const char* rick_last_error(rick_handle h);
 
 /* Name of a status code. */

@@ -109,7 +109,8 @@ class RickError(RuntimeError):
 def check(status, handle=None):
     if status != RICK_OK:
         msg = ""
-        if handle is not None and _lib is not None:
+        if _lib is not None:
+            # handle None: the message of the last failed creation on this thread
             raw = _lib.rick_last_error(handle)
             msg = raw.decode() if raw else ""
         raise RickError(status, msg)

@@ -330,7 +330,15 @@ const char* rick_status_string(rick_status s)
     }
 }
 
-const char* rick_last_error(rick_handle h) { return h ? h->last_error : "null handle"; }
+// The message of the last rick_create / rick_create_batch that failed on
+// this thread (the handle it was building is gone).
+static thread_local char g_create_error[512];
+
+const char* rick_last_error(rick_handle h)
+{
+    if (h) return h->last_error;
+    return g_create_error[0] ? g_create_error : "null handle";
+}
 
 rick_status rick_workspace_size(const rick_params* p, int64_t max_vis, size_t* bytes)
 {
@@ -363,9 +371,11 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
     rick_imager* h = new (std::nothrow) rick_imager();
     if (!h) return RICK_ERR_OOM;
     h->last_error[0] = 0;
+    g_create_error[0] = 0;
     rick_status s = check_params(p, &h->cfg, &h->kernel_param, h->last_error, sizeof(h->last_error));
     if (s) {
-        // keep the message reachable only through the return code: the handle is not returned
+        // the handle is not returned: its message stays reachable through rick_last_error(NULL)
+        snprintf(g_create_error, sizeof(g_create_error), "%s", h->last_error);
         delete h;
         return s;
     }
@@ -438,6 +448,8 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
         return RICK_ERR_OOM;
     }
     auto cleanup = [&](rick_status st) {
+        snprintf(g_create_error, sizeof(g_create_error), "%s",
+                 h->last_error[0] ? h->last_error : rick_status_string(st));
         rick_destroy(h);
         return st;
     };
@@ -494,7 +506,13 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
             return cleanup(RICK_ERR_CUDA);
         float lo = tab[0];
         for (float x : tab) lo = x < lo ? x : lo;
-        if (!(lo >= kMinWcorr)) return cleanup(RICK_ERR_ARG);
+        if (!(lo >= kMinWcorr)) {
+            snprintf(h->last_error, sizeof(h->last_error),
+                     "w_support %d: the grid correction in w falls to %.3g in the image (dw (1 - n) = %.3g "
+                     "plane widths at the corners is beyond the kernel's passband): use more w-planes",
+                     c.Sw, (double)lo, dw * umax);
+            return cleanup(RICK_ERR_ARG);
+        }
     }
     {
         // kernel tap polynomials: fitted on the device, carried in the kernel parameters

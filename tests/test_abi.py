@@ -61,6 +61,19 @@ def test_status_strings_and_null_handles(lib):
     assert lib.rick_workspace_size(None, 0, None) == 1
 
 
+def test_failed_creation_keeps_its_message(lib):
+    """Parameters are checked on the host before any CUDA call: a refused
+    rick_create returns no handle, and rick_last_error(NULL) gives why."""
+    from paper_2504_00959_gb300 import _lib
+    p = _lib.RickParams()
+    lib.rick_params_default(ctypes.byref(p))
+    p.tile = 48
+    h = ctypes.c_void_p(None)
+    assert lib.rick_create(ctypes.byref(p), ctypes.byref(h)) == 1
+    assert not h.value
+    assert b"tile" in lib.rick_last_error(None)
+
+
 def test_workspace_size_and_parameter_checks(lib):
     from paper_2504_00959_gb300 import _lib
     p = _lib.RickParams()

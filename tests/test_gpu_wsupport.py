@@ -134,7 +134,7 @@ def test_refuses_planes_too_coarse_for_the_w_term(rick):
     """A wide field (dw (1 - n) at the corners far beyond the w-kernel's
     passband) would divide the image by ~0: creation fails instead."""
     p = synth.make_params(1024, 8, np.radians(20.0) / 1024, -6000.0, 6000.0, KB, 7)
-    with pytest.raises(rick.RickError):
+    with pytest.raises(rick.RickError, match="passband"):
         rick.Imager(dict(p, w_support=4))
     rick.Imager(dict(p, nw=8, w_support=1)).close()  # nearest-plane stacking has no such division
 

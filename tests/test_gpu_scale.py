@@ -58,3 +58,34 @@ def test_config3_plane_groups_uniform_weighting(rick, oracle_mod):
     del prob
     ref = oracle_mod.image_at(dict(q), p["u"], p["v"], p["w"], p["wt"], p["vis"], pix, flags=UNIFORM)
     assert np.max(np.abs(got - ref.real)) <= 1e-4 * peak, (got, ref.real, peak)
+
+
+def test_maximum_grid_side(rick, oracle_mod):
+    """The largest grid the library accepts, 32768^2 (n^2 > 2^30: the 64-bit
+    index paths of the sort, the gridder's tile stores, cuFFT and the stack),
+    2 w-planes (17 GB of planes), 2e5 measurements with uniform weighting:
+    sampled pixels against the oracle's per-pixel evaluation at 1e-4 of the
+    peak."""
+    n = 32768
+    prob = synth.disk_problem(n, 2, 200000, synth.KERNEL_KB, 7, 4.0, 300.0, 511, fill=0.45)
+    q = dict(prob["params"], flags=REAL | CORRECT | UNIFORM)
+    g = {k: prob[k].cuda() for k in ("vis", "u", "v", "w", "wt")}
+    im = rick.Imager(q)
+    im.grid(g["vis"], g["u"], g["v"], g["w"], g["wt"])
+    img = im.image()
+    torch.cuda.synchronize()
+    st = im.stats()
+    im.close()
+    assert st["n_gridded"] + st["n_dropped"] == 200000
+    rng = np.random.default_rng(29)
+    flat = int(torch.argmax(img.abs()).item())
+    pix = [(flat % n, flat // n), (n // 2, n // 2), (n - 1, n - 1), (0, n // 2 + 3)]
+    pix += [tuple(rng.integers(0, n, 2)) for _ in range(4)]
+    pix = np.array(pix, np.int32)
+    got = img[torch.from_numpy(pix[:, 1]).long().cuda(), torch.from_numpy(pix[:, 0]).long().cuda()].cpu().numpy()
+    del img
+    p = synth.to_numpy(prob)
+    ref = oracle_mod.image_at(q, p["u"], p["v"], p["w"], p["wt"], p["vis"], pix, flags=CORRECT | UNIFORM).real
+    c = oracle_mod.taper(n, synth.KERNEL_KB, 7, 0.0)
+    cc = c[pix[:, 0]] * c[pix[:, 1]]
+    assert np.max(np.abs(got - ref) * cc) <= 1e-4 * np.max(np.abs(ref) * cc), (got, ref)

@@ -222,13 +222,19 @@ rick_status rick_create_batch(const rick_params* p, int32_t nchan, const double*
  * overwritten.  With use_graph != 0 the whole step is captured into a CUDA
  * graph on the first call and replayed by later calls with the same pointers
  * and offsets (needs a non-default stream, rick_set_stream); the entry
- * buffers are persistent and grow outside the capture. */
+ * buffers are persistent and grow outside the capture.  With two or more
+ * plane groups (plane_group smaller than nchan * nw) and room for a second
+ * plane buffer, the groups are pipelined: group g + 1 is gridded on the
+ * handle's stream while group g is transformed and stacked on a second
+ * stream of the handle (event-ordered; joined before the call returns its
+ * work to the handle's stream).  With phase timing on, groups run one by
+ * one. */
 rick_status rick_image_batch(rick_handle h, const float* vis, const float* u, const float* v, const float* w,
                              const float* weights, const int64_t* chan_offsets, float* images, int32_t use_graph);
 
 /* Autotuner for batched imaging: times one rick_image_batch of the given data
  * for every tile side (16, 32, 64, at least the support) and plane group
- * (all channels, half of them) and returns the fastest in *tile_out and
+ * (all channels, half, a quarter of them) and returns the fastest in *tile_out and
  * *plane_group_out (device time in *ms_out, may be NULL).  When the
  * environment variable RICK_AUTOTUNE_CACHE names a file, results are looked
  * up there first and appended after tuning (key: n, nw, nchan, support,

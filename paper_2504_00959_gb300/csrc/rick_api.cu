@@ -466,6 +466,21 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
         if (cudaMalloc(&h->chan_off, sizeof(int64_t) * (nchan + 1)) != cudaSuccess) return cleanup(RICK_ERR_OOM);
         if (cudaMalloc(&h->chan_sw, sizeof(double) * nchan) != cudaSuccess) return cleanup(RICK_ERR_OOM);
         if (cudaMalloc(&h->b_off, sizeof(uint32_t) * (ntiles + 1)) != cudaSuccess) return cleanup(RICK_ERR_OOM);
+        if (G < NW) {
+            // a second plane buffer for pipelined groups, when it fits (else groups run one by one)
+            size_t fr2 = 0, tot2 = 0;
+            if (cudaMemGetInfo(&fr2, &tot2) == cudaSuccess && (size_t)G * pb + 2 * pb + (256u << 20) < fr2 &&
+                cudaMalloc((void**)&h->planes2, (size_t)G * pb) == cudaSuccess) {
+                h->bytes_held += (size_t)G * pb;
+                if (cudaStreamCreateWithFlags(&h->fft_stream, cudaStreamNonBlocking) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+                    return cleanup(RICK_ERR_CUDA);
+                for (int b = 0; b < 2; ++b)
+                    if (cudaEventCreateWithFlags(&h->ev_gridded[b], cudaEventDisableTiming) != cudaSuccess ||
+                        cudaEventCreateWithFlags(&h->ev_free[b], cudaEventDisableTiming) != cudaSuccess)
+                        return cleanup(RICK_ERR_CUDA);
+            }
+        }
         if (cudaMemcpy(h->chan_w, cw.data(), sizeof(float2) * nchan, cudaMemcpyHostToDevice) != cudaSuccess)
             return cleanup(RICK_ERR_CUDA);
         h->cfg.chan_w = h->chan_w;
@@ -589,6 +604,16 @@ rick_status rick_destroy(rick_handle h)
     cudaFree(h->b_off);
     cudaFree(h->b_ent);
     cudaFree(h->b_heavy);
+    if (h->planes2) {
+        if (h->fft_stream) cudaStreamSynchronize(h->fft_stream);
+        cudaFree(h->planes2);
+    }
+    if (h->fft_stream) cudaStreamDestroy(h->fft_stream);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    for (int b = 0; b < 2; ++b) {
+        if (h->ev_gridded[b]) cudaEventDestroy(h->ev_gridded[b]);
+        if (h->ev_free[b]) cudaEventDestroy(h->ev_free[b]);
+    }
     if (h->pool) cudaMemPoolDestroy(h->pool);
     delete h;
     return RICK_OK;
@@ -1053,26 +1078,8 @@ static rick_status batch_body(rick_handle h, const float* vis, const float* u, c
     }
     const size_t img_floats = (size_t)p.n * p.n * ((p.flags & RICK_REAL_IMAGE) ? 1 : 2);
     const size_t nn = (size_t)p.n * p.n;
-    for (int k0 = 0; k0 < c.nw; k0 += h->G) {
-        const int nk = (c.nw - k0 < h->G) ? c.nw - k0 : h->G;
-        {
-            PhaseScope scope(h, kPhaseGrid);
-            ChunkList cl{};
-            cl.off[0] = h->b_off;
-            cl.ent[0] = h->b_ent;
-            cl.count = 1;
-            RICK_CU(h, launch_grid(c, cl, k0, nk, true, false, h->b_heavy, h->b_heavy_words, h->planes, h->stream));
-            count_launches(h, 2);
-        }
-        cufftHandle plan;
-        rick_status s = get_plan(h, nk, &plan);
-        if (s) return s;
-        {
-            PhaseScope fs(h, kPhaseFft);
-            RICK_FFT(h, cufftExecC2C(plan, reinterpret_cast<cufftComplex*>(h->planes),
-                                     reinterpret_cast<cufftComplex*>(h->planes), CUFFT_INVERSE));
-        }
-        PhaseScope ss(h, kPhaseStack);
+    // stack the channels of the group in planes `buf` (first plane k0) on stream st
+    auto stack_group = [&](const float2* buf, int k0, int nk, cudaStream_t st) -> rick_status {
         for (int ch = k0 / c.nw_chan; ch < (k0 + nk) / c.nw_chan; ++ch) {
             const double dw = (p.nw > 1) ? (h->chan_wmax[ch] - h->chan_wmin[ch]) / p.nw
                                          : (h->chan_wmax[ch] - h->chan_wmin[ch]);
@@ -1086,11 +1093,69 @@ static rick_status batch_body(rick_handle h, const float* vis, const float* u, c
             a.nk = c.nw_chan;
             a.first = 1;
             a.last = 1;
-            const float2* pl = h->planes + (size_t)(ch * c.nw_chan - k0) * nn;
-            RICK_CU(h, launch_stack(a, pl, nullptr, h->taper, h->chan_sw + ch, images + (size_t)ch * img_floats,
-                                    h->stream));
+            const float2* pl = buf + (size_t)(ch * c.nw_chan - k0) * nn;
+            RICK_CU(h, launch_stack(a, pl, nullptr, h->taper, h->chan_sw + ch, images + (size_t)ch * img_floats, st));
             count_launches(h, 1);
         }
+        return RICK_OK;
+    };
+    auto grid_group = [&](float2* buf, int k0, int nk) -> rick_status {
+        ChunkList cl{};
+        cl.off[0] = h->b_off;
+        cl.ent[0] = h->b_ent;
+        cl.count = 1;
+        RICK_CU(h, launch_grid(c, cl, k0, nk, true, false, h->b_heavy, h->b_heavy_words, buf, h->stream));
+        count_launches(h, 2);
+        return RICK_OK;
+    };
+    const bool pipelined = h->planes2 && !h->timer.on && h->G < c.nw;
+    if (pipelined) {
+        // group g: gridded on the handle's stream into buffer g % 2 (after the
+        // stacks of group g - 2 released it), then transformed and stacked on
+        // fft_stream, so gridding g + 1 overlaps the FFT and stacks of g
+        RICK_CU(h, cudaEventRecord(h->ev_fork, h->stream));
+        RICK_CU(h, cudaStreamWaitEvent(h->fft_stream, h->ev_fork, 0));
+        int g = 0;
+        for (int k0 = 0; k0 < c.nw; k0 += h->G, ++g) {
+            const int nk = (c.nw - k0 < h->G) ? c.nw - k0 : h->G;
+            const int b = g & 1;
+            float2* buf = b ? h->planes2 : h->planes;
+            if (g >= 2) RICK_CU(h, cudaStreamWaitEvent(h->stream, h->ev_free[b], 0));
+            rick_status s = grid_group(buf, k0, nk);
+            if (s) return s;
+            RICK_CU(h, cudaEventRecord(h->ev_gridded[b], h->stream));
+            RICK_CU(h, cudaStreamWaitEvent(h->fft_stream, h->ev_gridded[b], 0));
+            cufftHandle plan;
+            if ((s = get_plan(h, nk, &plan))) return s;
+            RICK_FFT(h, cufftSetStream(plan, h->fft_stream));
+            RICK_FFT(h, cufftExecC2C(plan, reinterpret_cast<cufftComplex*>(buf), reinterpret_cast<cufftComplex*>(buf),
+                                     CUFFT_INVERSE));
+            if ((s = stack_group(buf, k0, nk, h->fft_stream))) return s;
+            RICK_CU(h, cudaEventRecord(h->ev_free[b], h->fft_stream));
+        }
+        // join: the images are complete on the handle's stream
+        RICK_CU(h, cudaStreamWaitEvent(h->stream, h->ev_free[0], 0));
+        if (g > 1) RICK_CU(h, cudaStreamWaitEvent(h->stream, h->ev_free[1], 0));
+        return RICK_OK;
+    }
+    for (int k0 = 0; k0 < c.nw; k0 += h->G) {
+        const int nk = (c.nw - k0 < h->G) ? c.nw - k0 : h->G;
+        {
+            PhaseScope scope(h, kPhaseGrid);
+            rick_status s = grid_group(h->planes, k0, nk);
+            if (s) return s;
+        }
+        cufftHandle plan;
+        rick_status s = get_plan(h, nk, &plan);
+        if (s) return s;
+        {
+            PhaseScope fs(h, kPhaseFft);
+            RICK_FFT(h, cufftSetStream(plan, h->stream));
+            RICK_FFT(h, cufftExecC2C(plan, reinterpret_cast<cufftComplex*>(h->planes),
+                                     reinterpret_cast<cufftComplex*>(h->planes), CUFFT_INVERSE));
+        }
+        PhaseScope ss(h, kPhaseStack);
+        if ((s = stack_group(h->planes, k0, nk, h->stream))) return s;
     }
     return RICK_OK;
 }
@@ -1231,11 +1296,14 @@ rick_status rick_autotune_batch(const rick_params* p, int32_t nchan, const doubl
     const int tiles[3] = {16, 32, 64};
     for (int ti = 0; ti < 3; ++ti) {
         if (tiles[ti] < p->support) continue;
-        for (int half = 0; half < 2; ++half) {
+        // plane groups of all channels, half and a quarter of them (with two or
+        // more groups the groups are pipelined: gridding overlaps the FFT)
+        for (int part = 0; part < 3; ++part) {
+            const int div = 1 << part;
+            if (part && nchan < div) continue;
             rick_params q = *p;
             q.tile = tiles[ti];
-            q.plane_group = half ? ((nchan / 2 > 0 ? nchan / 2 : 1) * p->nw) : 0;
-            if (half && nchan < 2) continue;
+            q.plane_group = part ? (nchan / div) * p->nw : 0;
             rick_handle h = nullptr;
             if (create_impl(&q, nchan, w_min, w_max, &h) != RICK_OK) continue;
             rick_set_stream(h, st);

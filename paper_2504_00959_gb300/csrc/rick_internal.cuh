@@ -359,6 +359,12 @@ struct rick_imager {
     int64_t b_cap;
     uint32_t* b_heavy;               // gridder's heavy-chunk list for b_cap entries
     size_t b_heavy_words;
+    // pipelined plane groups (batched, two or more groups): a second plane
+    // buffer; group g is gridded on the handle's stream into buffer g % 2 while
+    // group g - 1 is transformed and stacked on fft_stream
+    float2* planes2;
+    cudaStream_t fft_stream;
+    cudaEvent_t ev_fork, ev_gridded[2], ev_free[2];
     cudaGraphExec_t graph;
     const void* graph_key[7];
     int64_t graph_m;

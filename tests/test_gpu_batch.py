@@ -109,6 +109,38 @@ def test_batch_graph_replay_equals_direct(rick, chans):
     assert (out - direct).abs().max().item() <= 1e-6 * direct.abs().max().item()
 
 
+@pytest.mark.parametrize("mode", ["direct", "graph", "timed"])
+def test_pipelined_plane_groups_equal_one_group(rick, chans, mode):
+    """Groups of 2 channels (4 groups: gridding of group g + 1 overlaps the
+    FFT and stacks of group g on the handle's second stream, directly and
+    inside a captured graph; with timing on the groups run one by one)
+    against one group of all channels."""
+    prob = chans
+    args = (prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"], prob["offsets"])
+    one = rick.BatchImager(dict(prob["params"], flags=REAL), prob["ranges"])
+    ref = one.images(*args).clone()
+    one.close()
+    nw = prob["params"]["nw"]
+    pip = rick.BatchImager(dict(prob["params"], flags=REAL, plane_group=2 * nw), prob["ranges"])
+    assert pip.stats()["plane_group"] == 2 * nw
+    out = torch.empty_like(ref)
+    if mode == "graph":
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                pip.images(*args, out=out, use_graph=True)
+    else:
+        if mode == "timed":
+            pip.set_timing(True)
+        pip.images(*args, out=out)
+        if mode == "timed":
+            assert pip.timing()["fft_calls"] == 4
+    torch.cuda.synchronize()
+    pip.close()
+    assert (out - ref).abs().max().item() <= 1e-6 * ref.abs().max().item()
+
+
 def test_autotune_batch_and_cache(rick, chans, tmp_path, monkeypatch):
     prob = chans
     cache = tmp_path / "tune.txt"

@@ -548,7 +548,12 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
         if (e != cudaSuccess) return cleanup(RICK_ERR_CUDA);
         double worst = 0.0;
         for (int t = 0; t < c.S; ++t) worst = err[t] > worst ? err[t] : worst;
-        if (!(worst <= 2e-6)) return cleanup(RICK_ERR_ARG);  // kernel too sharp for degree-10 taps
+        if (!(worst <= 2e-6)) {  // kernel too sharp for degree-10 taps
+            snprintf(h->last_error, sizeof(h->last_error),
+                     "kernel taps: the degree-10 polynomial fit misses the kernel by %.3g (> 2e-6): the kernel is "
+                     "too sharp for support %d (widen kernel_param)", worst, c.S);
+            return cleanup(RICK_ERR_ARG);
+        }
         for (int t = 0; t < kMaxSupport; ++t)
             for (int j = 0; j < kPolyTerms; ++j) h->cfg.coef[t][j] = (t < c.S) ? coef[t * kPolyTerms + j] : 0.0f;
         set_tap_sum(h->cfg);

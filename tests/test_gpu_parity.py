@@ -142,6 +142,26 @@ def test_ragged_and_tiles(rick, oracle_mod, n, tile, kernel, support):
     _compare(rick, oracle_mod, prob, CORRECT | REAL, tile=tile)
 
 
+@pytest.mark.parametrize("n,nw,kernel,support,tile", [(16, 1, KB, 1, 16), (32, 2, KB, 2, 16),
+                                                       (34, 3, KB, 3, 16), (8, 1, GAUSS, 4, 16),
+                                                       (64, 1, KB, 6, 32)])
+def test_degenerate_shapes(rick, oracle_mod, n, nw, kernel, support, tile):
+    """The smallest supports (a one-cell footprint, one and two cell pairs per
+    row), a single w-plane (w ignored), the smallest grid the tile allows and
+    a ragged tile, against the oracle."""
+    prob = synth.disk_problem(n, nw, 3000, kernel, support, 3.0, 60.0, 131 + n + support, weights="random",
+                              fill=0.35)
+    _compare(rick, oracle_mod, prob, CORRECT | REAL, tile=tile)
+    _compare(rick, oracle_mod, prob, APPLY_N, tile=tile)
+
+
+def test_kernel_too_sharp_for_its_taps_is_refused(rick):
+    """The Gaussian's default width for support 2 (sigma = 1/3 cell) is too
+    sharp for degree-10 tap polynomials: creation fails and says why."""
+    with pytest.raises(rick.RickError, match="too sharp"):
+        rick.Imager(synth.make_params(32, 2, 1e-3, -60.0, 60.0, GAUSS, 2))
+
+
 def test_plane_groups_equal_all_planes(rick, oracle_mod):
     prob = synth.disk_problem(128, 8, 30000, KB, 7, 4.0, 80.0, 103)
     a, _, _ = _compare(rick, oracle_mod, prob, CORRECT | REAL, plane_group=3)

@@ -15,7 +15,9 @@
  *   pixel_rad, m = (y - n/2) * pixel_rad; the phase centre is pixel (n/2, n/2).
  * - w-planes: nw uniform bins over [w_min, w_max]; a measurement goes to the
  *   plane floor((w - w_min) / dw) clamped to [0, nw-1] (the closest plane,
- *   Sec. 2.1); plane k has centre w_k = w_min + (k + 1/2) dw.
+ *   Sec. 2.1), or with rick_params.w_support > 1 to the planes of its
+ *   w-footprint (Eq. 3's kernel in w); plane k has centre w_k = w_min +
+ *   (k + 1/2) dw.
  * - Kernel footprint: cells f .. f+S-1 on each axis, f = floor(p - S/2) + 1,
  *   p = u / du + n/2; taps normalised to sum 1 per axis.  A measurement whose
  *   footprint leaves the grid, or with a non-finite coordinate, weight or

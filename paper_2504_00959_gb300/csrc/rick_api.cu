@@ -126,8 +126,6 @@ rick_status check_params(const rick_params* p, GridCfg* c, double* kparam, char*
     c->invdw = (p->nw > 1) ? (float)(1.0 / dw) : 0.0f;
     c->lim = (float)(p->n - p->support - 1);
     c->kernel = p->kernel;
-    c->kp = (p->kernel == RICK_KERNEL_GAUSS) ? (float)(1.0 / (2.0 * kp * kp)) : (float)kp;
-    c->two_over_s = (float)(2.0 / p->support);
     if (p->w_support < 0 || p->w_support > kMaxWSupport || p->w_support > p->nw) {
         snprintf(msg, msglen, "w_support must be in [0, min(16, nw)] (got %d)", p->w_support);
         return RICK_ERR_ARG;

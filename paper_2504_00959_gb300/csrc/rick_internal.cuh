@@ -30,8 +30,6 @@ struct GridCfg {
     float wmin, invdw;               // binary32 plane decision constants
     float lim;                       // n - S - 1: largest first cell - 1
     int kernel;                      // RICK_KERNEL_*
-    float kp;                        // Gaussian: 1/(2 sigma^2); KB: beta
-    float two_over_s;                // 2 / S
     int uniform;                     // uniform weighting on
     // w-support (Eq. 3's kernel in w): Sw planes per measurement; 1 = nearest
     int Sw;
@@ -114,15 +112,6 @@ __device__ __forceinline__ int nearest_cell(const GridCfg& c, float p)
 {
     int j = (int)floorf(__fadd_rn(p, 0.5f));
     return j > c.n - 1 ? c.n - 1 : j;
-}
-
-// Un-normalised kernel value at offset x (cells) from the measurement.
-__device__ __forceinline__ float kernel_value(const GridCfg& c, float x)
-{
-    if (c.kernel == RICK_KERNEL_GAUSS) return __expf(-x * x * c.kp);
-    float t = x * c.two_over_s;
-    float a = fmaxf(0.0f, 1.0f - t * t);
-    return cyl_bessel_i0f(c.kp * sqrtf(a));
 }
 
 // The S (un-normalised) taps of a measurement at continuous coordinate p

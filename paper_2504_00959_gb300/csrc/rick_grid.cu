@@ -31,7 +31,7 @@
 namespace rick {
 namespace {
 
-constexpr int kHeavyEntries = 256;
+constexpr int kHeavyEntries = 768;
 constexpr int kTilesPerWarp = 4;
 
 int sm_count_grid()

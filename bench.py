@@ -206,10 +206,11 @@ def main():
                          "nw / (nw - w_support) so every footprint lies on the planes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--workload", choices=["wstack", "channels", "adjoint"], default="wstack",
+    ap.add_argument("--workload", choices=["wstack", "channels", "adjoint", "large"], default="wstack",
                     help="wstack: the 4096^2 / 32-plane / 1e7 image (default); channels: 64 channels "
                          "batched vs imaged one by one; adjoint: image + loss gradient through the "
-                         "adjoint degridder on the same workload")
+                         "adjoint degridder on the same workload; large: 16384^2 / 128 planes / 2e8 "
+                         "measurements with uniform weighting, in plane groups")
     args = ap.parse_args()
 
     import torch
@@ -224,6 +225,8 @@ def main():
         return run_channels(args, rank, world)
     if args.workload == "adjoint":
         return run_adjoint(args, rank, world)
+    if args.workload == "large":
+        return run_large(args, rank, world)
 
     import synth
     import paper_2504_00959_gb300 as rick
@@ -292,7 +295,10 @@ def main():
     grid_launch_ms = tm["grid_ms"] / max(tm["grid_calls"], 1)
     grid_bytes = 16.0 * st["n_gridded"] + 8.0 * nw * n * n
     achieved = grid_bytes / (grid_launch_ms / 1e3) / 1e9
-    traffic = _traffic("rick_grid.cu", "k_grid@4096x32x1e7")
+    # the committed DRAM counters were taken on the 4096^2 x 32 x 1e7 workload only
+    default_size = (n, nw, m) == (4096, 32, 10_000_000) and params.get("w_support", 1) <= 1 \
+        and not params["flags"] & synth.FLAG_FOLD
+    traffic = _traffic("rick_grid.cu", "k_grid@4096x32x1e7") if default_size else None
     stack_ms = tm["stack_ms"] / max(tm["stack_calls"], 1)
     stack_bytes = 8.0 * nw * n * n + 4.0 * n * n
     fft_ms = tm["fft_ms"] / max(tm["fft_calls"], 1)
@@ -357,7 +363,7 @@ def main():
                    ("; w-support %d on %d planes" % (args.w_support, nw) if args.w_support > 1 else ""),
                    "n": n, "nw": nw, "nvis": m, "kernel": "kaiser-bessel", "support": 7,
                    "tile": st["tile"], "plane_group": st["plane_group"],
-                   "l2": "inputs larger than L2 (4.3 GB of planes written and read every step)",
+                   "l2": "inputs larger than L2 (%.2f GB of planes written and read every step)" % (8.0 * nw * n * n / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"kernel": "k_grid (gridding, Eq. 3)", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
@@ -551,6 +557,93 @@ def run_adjoint(args, rank, world):
             else None,
             "gpu_launches": int(tm["kernel_launches"]), "clocks": clk}))
     im.close()
+
+
+def run_large(args, rank, world):
+    """The 16384^2 / 128-plane / 2e8-measurement image with uniform weighting
+    (5 degree field, Kaiser-Bessel support 8): the planes (275 GB) do not fit
+    at once, so every step grids, transforms and stacks plane group after
+    plane group, re-reading the measurements for each group.  Reported
+    beside the default line, not instead of it."""
+    import torch
+
+    import synth
+    import paper_2504_00959_gb300 as rick
+    from paper_2504_00959_gb300 import build as rick_build
+    rick_build.build()
+    if rank != 0:
+        return
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    prob = synth.config3(device=dev)
+    params = dict(prob["params"], tile=args.tile)
+    im = rick.Imager(params, device=dev)
+    n, nw = params["n"], params["nw"]
+    m = prob["u"].numel()
+    img = torch.empty((n, n), dtype=torch.float32, device=dev)
+
+    def step():
+        im.reset()
+        im.grid(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"])
+        im.image(out=img)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", ""))
+    uuid = uuid if uuid.startswith("GPU-") else ("GPU-" + uuid if uuid else "")
+    nvml = Nvml(uuid) if uuid else None
+    clocks = ClockSampler(uuid if uuid else 0)
+    im.set_timing(True)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    clocks.start()
+    j0 = nvml.energy_mj() if nvml else None
+    s0.record()
+    for _ in range(args.steps):
+        step()
+    s1.record()
+    torch.cuda.synchronize()
+    j1 = nvml.energy_mj() if nvml else None
+    clk = clocks.stop()
+    ms = s0.elapsed_time(s1) / max(args.steps, 1)
+    tm = im.timing()
+    st = im.stats()
+    im.close()
+    peak, peak_kind = _peaks()
+    steps = max(args.steps, 1)
+    groups = -(-nw // max(st["plane_group"], 1))
+    cells = float(nw) * n * n
+    grid_ms = tm["grid_ms"] / steps
+    grid_bytes = 16.0 * st["n_gridded"] + 8.0 * cells
+    phases = {
+        # every plane group sorts all measurements again: two passes of 24 B each
+        "prep": (tm["prep_ms"] / steps, groups * 2 * 24.0 * m + 16.0 * st["n_entries"]),
+        "grid": (grid_ms, grid_bytes),
+        "fft_cufft": (tm["fft_ms"] / steps, 2 * 2 * 8.0 * cells),
+        "stack": (tm["stack_ms"] / steps, 8.0 * cells + 2 * 8.0 * n * n * groups),
+    }
+    ph = {k: {"ms": t, "algorithmic_gb": b / 1e9, "gbs": b / t / 1e6, "frac_of_" + peak_kind: b / t / 1e6 / peak}
+          for k, (t, b) in phases.items() if t > 0}
+    print(json.dumps({
+        "metric": "visibilities/sec end-to-end (grid+FFT+w-stack), 16384^2 x 128 planes, uniform weighting",
+        "value": m / (ms / 1e3), "unit": "vis/s", "higher_is_better": True, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "dtype": "f32",
+        "data": "synthetic: seeded Earth-rotation synthesis (512 antennas, 60 km, 8 h, dec -45, 1.4 GHz), "
+                "N(0,1) visibilities + a unit source at the phase centre",
+        "config": {"workload": "16384x16384 grid, 128 w-planes in groups, 2e8 visibilities, 5 degree field, "
+                               "Kaiser-Bessel support 8, uniform weighting, FP32",
+                   "n": n, "nw": nw, "nvis": m, "support": params["support"], "tile": st["tile"],
+                   "plane_group": st["plane_group"], "plane_groups": groups,
+                   "l2": "inputs larger than L2 (%.0f GB of planes per step)" % (8.0 * cells / 1e9)},
+        "roofline": {"kernel": "k_grid (gridding, Eq. 3)", "bound": "hbm", "achieved": grid_bytes / grid_ms / 1e6,
+                     "peak": peak, "unit": "GB/s", "frac": grid_bytes / grid_ms / 1e6 / peak, "traffic": None,
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_step": grid_bytes, "grid_ms_per_step": grid_ms},
+        "phases": ph,
+        "roofline_frac_end_to_end": sum(b for _, b in phases.values()) / (ms / 1e3) / 1e9 / peak,
+        "energy_j_per_solution": (j1 - j0) / 1e3 / steps if j0 is not None and j1 is not None else None,
+        "gpu_launches": int(tm["kernel_launches"]), "clocks": clk}))
 
 
 def run_reference(args, rank, world):

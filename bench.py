@@ -206,11 +206,12 @@ def main():
                          "nw / (nw - w_support) so every footprint lies on the planes")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--workload", choices=["wstack", "channels", "adjoint", "large"], default="wstack",
+    ap.add_argument("--workload", choices=["wstack", "channels", "adjoint", "large", "small"], default="wstack",
                     help="wstack: the 4096^2 / 32-plane / 1e7 image (default); channels: 64 channels "
                          "batched vs imaged one by one; adjoint: image + loss gradient through the "
                          "adjoint degridder on the same workload; large: 16384^2 / 128 planes / 2e8 "
-                         "measurements with uniform weighting, in plane groups")
+                         "measurements with uniform weighting, in plane groups; small: 256^2 / 8 planes / "
+                         "1e5, microseconds per image")
     args = ap.parse_args()
 
     import torch
@@ -227,6 +228,8 @@ def main():
         return run_adjoint(args, rank, world)
     if args.workload == "large":
         return run_large(args, rank, world)
+    if args.workload == "small":
+        return run_small(args, rank, world)
 
     import synth
     import paper_2504_00959_gb300 as rick
@@ -644,6 +647,66 @@ def run_large(args, rank, world):
         "roofline_frac_end_to_end": sum(b for _, b in phases.values()) / (ms / 1e3) / 1e9 / peak,
         "energy_j_per_solution": (j1 - j0) / 1e3 / steps if j0 is not None and j1 is not None else None,
         "gpu_launches": int(tm["kernel_launches"]), "clocks": clk}))
+
+
+def run_small(args, rank, world):
+    """The 256^2 / 8-plane / 1e5-measurement image (2 degree field, Gaussian
+    support 7): bound by launch latency, so reported in microseconds per
+    image, from CUDA events around the steps and from the host clock."""
+    import torch
+
+    import synth
+    import paper_2504_00959_gb300 as rick
+    from paper_2504_00959_gb300 import build as rick_build
+    rick_build.build()
+    if rank != 0:
+        return
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    prob = synth.config1(device=dev)
+    params = dict(prob["params"], flags=synth.FLAG_CORRECT | synth.FLAG_REAL, tile=args.tile)
+    im = rick.Imager(params, device=dev)
+    n, nw = params["n"], params["nw"]
+    m = prob["u"].numel()
+    img = torch.empty((n, n), dtype=torch.float32, device=dev)
+
+    def step():
+        im.reset()
+        im.grid(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"])
+        im.image(out=img)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    im.set_timing(False)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(args.steps, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s0.record()
+    for _ in range(steps):
+        step()
+    s1.record()
+    torch.cuda.synchronize()
+    host_us = (time.perf_counter() - t0) / steps * 1e6
+    dev_us = s0.elapsed_time(s1) / steps * 1e3
+    im.set_timing(True)
+    step()
+    torch.cuda.synchronize()
+    tm = im.timing()
+    st = im.stats()
+    im.close()
+    print(json.dumps({
+        "metric": "microseconds per image, 256^2 x 8 planes x 1e5 visibilities", "value": dev_us, "unit": "us",
+        "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dev_us / 1e3, "dtype": "f32",
+        "data": "synthetic: uv uniform in a disk of radius 0.45 N du, w uniform in [-50, 50], "
+                "N(0,1) visibilities + a unit source at the phase centre",
+        "config": {"workload": "256x256 grid, 8 w-planes, 1e5 visibilities, 2 degree field, Gaussian support 7, "
+                               "FP32 (launch-latency bound)", "n": n, "nw": nw, "nvis": m, "tile": st["tile"],
+                   "plane_group": st["plane_group"]},
+        "host_us_per_image": host_us, "visibilities_per_s": m / (dev_us / 1e6),
+        "gpu_launches_per_image": int(tm["kernel_launches"])}))
 
 
 def run_reference(args, rank, world):

@@ -20,9 +20,9 @@
 //     groups: the read-modify-write of a footprint is conflict-free;
 //   * a __syncwarp between entries orders one entry's stores before the next
 //     entry's loads.
-// Tiles with more than kHeavyEntries entries (the dense centre of the uv
+// Tiles with more than heavy_threshold() entries (the dense centre of the uv
 // plane) would serialise on one warp: k_grid_tiles writes them as zeros and
-// lists them as chunks of at most kHeavyEntries entries, and k_grid_chunks
+// lists them as chunks of at most that many entries, and k_grid_chunks
 // gives every chunk to a warp, which adds its private tile into the plane
 // with vector atomic adds.  The fftshift checkerboard (-1)^(ju+jv) is folded
 // into the tap signs.
@@ -31,7 +31,14 @@
 namespace rick {
 namespace {
 
-constexpr int kHeavyEntries = 768;
+// Chunking threshold of a pass with E entries: E / kHeavyDiv clamped to
+// [kHeavyMin, kHeavyMax].  A tile of many entries left to k_grid_tiles costs
+// its warp time proportional to the entries, run alone if it comes late in
+// the launch; a large pass hides that tail and gains from fewer chunk
+// flushes, a small one does not.
+constexpr uint32_t kHeavyMin = 256;
+constexpr uint32_t kHeavyMax = 768;
+constexpr uint32_t kHeavyDiv = 16384;
 constexpr int kTilesPerWarp = 4;
 
 int sm_count_grid()
@@ -338,6 +345,18 @@ __device__ __forceinline__ void init_tile(const GridCfg& c, const TileGeom& g, c
     }
 }
 
+// Chunking threshold of the pass [k0, k0 + ntl / ntp) from its entry count
+// (the offsets the gridder reads anyway: tile k0 * ntp + ntl is the end of
+// the last tile's range).  Both gridder kernels derive the same value.  A
+// pass over several entry lists is never chunked.
+__device__ __forceinline__ uint32_t heavy_threshold(const GridCfg& c, const ChunkList& ch, int k0, int64_t ntl)
+{
+    if (ch.count != 1) return 0xffffffffu;
+    const int64_t t0 = (int64_t)k0 * c.ntp;
+    const uint32_t entries = __ldg(ch.off[0] + t0 + ntl) - __ldg(ch.off[0] + t0);
+    return min(max(entries / kHeavyDiv, kHeavyMin), kHeavyMax);
+}
+
 // Each CTA of W warps takes kTilesPerWarp * W consecutive tiles of the pass,
 // warp w the tiles w, w + W, ... of them (neighbours, so similar loads), and
 // loads the next tile's list ranges while it grids the current one; the
@@ -346,7 +365,7 @@ __device__ __forceinline__ void init_tile(const GridCfg& c, const TileGeom& g, c
 template <int S>
 __global__ void __launch_bounds__(256) k_grid_tiles(GridCfg c, ChunkList ch, int k0, int64_t ntl, int shift,
                                                     int accumulate, float2* __restrict__ planes,
-                                                    uint32_t* __restrict__ heavy, uint32_t heavy_cap)
+                                                    uint32_t* __restrict__ heavy_list, uint32_t heavy_cap)
 {
     extern __shared__ float4 smem4[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -355,6 +374,7 @@ __global__ void __launch_bounds__(256) k_grid_tiles(GridCfg c, ChunkList ch, int
     const int64_t last = min(ntl, first + nwt * kTilesPerWarp);
     int64_t tl = first + wid;
     if (tl >= last) return;
+    const uint32_t heavy = heavy_threshold(c, ch, k0, ntl);
     unsigned char* mine = reinterpret_cast<unsigned char*>(smem4) + (size_t)wid * warp_smem_bytes<S>(c.T);
     float4* tile4 = reinterpret_cast<float4*>(mine);
     Stage<S>& st = *reinterpret_cast<Stage<S>*>(mine + (size_t)c.T * pair_pitch(c.T) * sizeof(float4));
@@ -380,25 +400,25 @@ __global__ void __launch_bounds__(256) k_grid_tiles(GridCfg c, ChunkList ch, int
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) nent += __shfl_xor_sync(0xffffffffu, nent, o);
 
-        if (nent > (uint32_t)kHeavyEntries && ch.count == 1) {
+        if (nent > heavy && ch.count == 1) {
             // many entries: hand the tile to k_grid_chunks as chunks of at most
-            // kHeavyEntries entries, which add into the plane; the tile starts
-            // at zero unless this pass accumulates onto earlier chunks
-            const uint32_t nchunks = (nent + kHeavyEntries - 1) / kHeavyEntries;
+            // `heavy` entries, which add into the plane; the tile starts at
+            // zero unless this pass accumulates onto earlier chunks
+            const uint32_t nchunks = (nent + heavy - 1) / heavy;
             uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(heavy, nchunks);
+            if (lane == 0) base = atomicAdd(heavy_list, nchunks);
             base = __shfl_sync(0xffffffffu, base, 0);
             if (base + nchunks <= heavy_cap) {
                 for (uint32_t k = lane; k < nchunks; k += 32) {
-                    heavy[1 + 2 * (base + k)] = (uint32_t)tl;
-                    heavy[2 + 2 * (base + k)] = k;
+                    heavy_list[1 + 2 * (base + k)] = (uint32_t)tl;
+                    heavy_list[2 + 2 * (base + k)] = k;
                 }
                 if (!accumulate) store_tile<true>(c, g, P0, nullptr, lane);
                 continue;
             }
             // no room in the chunk list: mark the reserved slots that do exist
             // as empty, and grid the tile here (correct, slower)
-            for (uint32_t k = base + lane; k < heavy_cap; k += 32) heavy[1 + 2 * k] = 0xffffffffu;
+            for (uint32_t k = base + lane; k < heavy_cap; k += 32) heavy_list[1 + 2 * k] = 0xffffffffu;
         }
         if (nent == 0) {
             if (!accumulate) store_tile<true>(c, g, P0, nullptr, lane);
@@ -421,9 +441,9 @@ __global__ void __launch_bounds__(256) k_grid_tiles(GridCfg c, ChunkList ch, int
 // the non-zero cell pairs (the tile's cells were zeroed by k_grid_tiles,
 // which ran before on the same stream).
 template <int S>
-__global__ void __launch_bounds__(256) k_grid_chunks(GridCfg c, ChunkList ch, int k0, int shift,
-                                                     float2* __restrict__ planes, const uint32_t* __restrict__ heavy,
-                                                     uint32_t heavy_cap)
+__global__ void __launch_bounds__(256) k_grid_chunks(GridCfg c, ChunkList ch, int k0, int64_t ntl, int shift,
+                                                     float2* __restrict__ planes,
+                                                     const uint32_t* __restrict__ heavy_list, uint32_t heavy_cap)
 {
     extern __shared__ float4 smem4[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -432,18 +452,19 @@ __global__ void __launch_bounds__(256) k_grid_chunks(GridCfg c, ChunkList ch, in
     Stage<S>& st = *reinterpret_cast<Stage<S>*>(mine + (size_t)c.T * pair_pitch(c.T) * sizeof(float4));
     LaneSlots<S> ls;
     ls.init(lane, pair_pitch(c.T));
-    const uint32_t count = min(heavy[0], heavy_cap);
+    const uint32_t heavy = heavy_threshold(c, ch, k0, ntl);
+    const uint32_t count = min(heavy_list[0], heavy_cap);
     const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
     for (uint32_t it = blockIdx.x * (blockDim.x >> 5) + wid; it < count; it += nwarps) {
-        const uint32_t tl32 = heavy[1 + 2 * it];
+        const uint32_t tl32 = heavy_list[1 + 2 * it];
         if (tl32 == 0xffffffffu) continue;  // slot of a tile gridded by k_grid_tiles itself
         const int64_t tl = tl32;
-        const uint32_t k = heavy[2 + 2 * it];
+        const uint32_t k = heavy_list[2 + 2 * it];
         const TileGeom g = tile_geom(c, k0, tl);
         float2* P0 = planes + (int64_t)g.kl * c.n * c.n;
         const uint32_t b0 = ch.off[0][g.tg], e0 = ch.off[0][g.tg + 1];
-        const uint32_t b = b0 + k * kHeavyEntries;
-        const uint32_t e = min(e0, b + kHeavyEntries);
+        const uint32_t b = b0 + k * heavy;
+        const uint32_t e = min(e0, b + heavy);
         init_tile(c, g, P0, tile4, false, lane);
         __syncwarp();
         warp_grid_range<S>(c, ch.ent[0], b, e, g.u0, g.v0, tile4, st, ls, lane, shift);
@@ -494,19 +515,19 @@ cudaError_t launch_grid_s(const GridCfg& c, const ChunkList& ch, int k0, int nk,
         cudaSuccess)
         return e;
     const unsigned nchunk_blocks = (unsigned)(max(per_sm, 1) * sm_count_grid());
-    k_grid_chunks<S><<<nchunk_blocks, 32 * wl, tile_bytes * wl, s>>>(c, ch, k0, shift ? 1 : 0, planes, heavy, cap);
+    k_grid_chunks<S><<<nchunk_blocks, 32 * wl, tile_bytes * wl, s>>>(c, ch, k0, ntl, shift ? 1 : 0, planes, heavy,
+                                                                    cap);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-// Every chunk holds more than kHeavyEntries / 2 entries on average (a heavy
-// tile of n > kHeavyEntries entries makes ceil(n / kHeavyEntries) < 2 n /
-// kHeavyEntries chunks), so a pass over E entries lists fewer than
-// 2 E / kHeavyEntries chunks.
+// Every chunk holds more than h / 2 entries on average for a threshold h
+// (a heavy tile of n > h entries makes ceil(n / h) < 2 n / h chunks), so a
+// pass over E entries lists fewer than 2 E / h <= 2 E / kHeavyMin chunks.
 size_t heavy_words_for(int64_t max_entries)
 {
-    const int64_t chunks = 2 * max_entries / kHeavyEntries + 1;
+    const int64_t chunks = 2 * max_entries / kHeavyMin + 1;
     return 1 + 2 * (size_t)(chunks > 0 ? chunks : 1);
 }
 

@@ -118,6 +118,7 @@ rick_status check_params(const rick_params* p, GridCfg* c, double* kparam, char*
     c->log2T = ilog2(T);
     c->ntu = (p->n + T - 1) / T;
     c->ntp = (int64_t)c->ntu * c->ntu;
+    c->cstride = counter_stride((int64_t)c->nw * c->ntp);
     c->uvscale = (float)((double)p->n * p->pixel_rad);
     c->half_n = (float)(p->n / 2);
     c->half_s = (float)(0.5 * p->support);
@@ -351,7 +352,8 @@ rick_status rick_workspace_size(const rick_params* p, int64_t max_vis, size_t* b
     size_t b = (size_t)G * plane_bytes(p);                           // planes
     if (G < p->nw) b += plane_bytes(p);                              // image accumulator
     b += (size_t)c.n * sizeof(float);                                // taper
-    b += (size_t)ntiles * sizeof(uint32_t) * 2 + sizeof(uint32_t);   // cursor + offsets
+    b += (size_t)ntiles * c.cstride * sizeof(uint32_t) + sizeof(uint32_t);  // padded counters / cursor
+    b += (size_t)(ntiles + 1) * sizeof(uint32_t);                          // offsets
     b += scan_block_sums_len(ntiles) * sizeof(uint32_t);
     b += (size_t)entries_bound(c, max_vis) * sizeof(float4);         // entries
     b += heavy_words_for(entries_bound(c, max_vis)) * sizeof(uint32_t);  // gridder's heavy-chunk list
@@ -396,6 +398,7 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
         h->cfg.nchan = nchan;
         h->cfg.nw_chan = p->nw;
         h->cfg.nw = nchan * p->nw;
+        h->cfg.cstride = counter_stride((int64_t)h->cfg.nw * h->cfg.ntp);
         h->nchan = nchan;
         h->chan_wmin.assign(w_min, w_min + nchan);
         h->chan_wmax.assign(w_max, w_max + nchan);
@@ -484,7 +487,8 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
         h->cfg.chan_w = h->chan_w;
         h->cfg.chan_off = h->chan_off;
     }
-    if (cudaMalloc(&h->cursor, (size_t)(ntiles + 1) * sizeof(uint32_t)) != cudaSuccess) return cleanup(RICK_ERR_OOM);
+    if (cudaMalloc(&h->cursor, (size_t)(ntiles * c.cstride + 1) * sizeof(uint32_t)) != cudaSuccess)
+        return cleanup(RICK_ERR_OOM);
     if (cudaMalloc(&h->block_sums, scan_block_sums_len(ntiles) * sizeof(uint32_t)) != cudaSuccess)
         return cleanup(RICK_ERR_OOM);
     if (cudaMalloc(&h->ctr, sizeof(Counters)) != cudaSuccess) return cleanup(RICK_ERR_OOM);
@@ -693,9 +697,10 @@ rick_status rick_grid(rick_handle h, const float* vis, const float* u, const flo
     }
     // the chunk is registered only once every kernel that fills it is enqueued,
     // so a failed call never leaves unfilled offsets for the gridder to read
-    e = cudaMemsetAsync(h->cursor, 0, (size_t)ntiles * sizeof(uint32_t), h->stream);
+    e = cudaMemsetAsync(h->cursor, 0, (size_t)ntiles * c.cstride * sizeof(uint32_t), h->stream);
     if (e == cudaSuccess) e = launch_count(c, u, v, w, weights, vis2, nvis, h->cursor, h->stream);
-    if (e == cudaSuccess) e = launch_scan(h->cursor, ntiles, ch.off, h->cursor, h->block_sums, h->stream);
+    if (e == cudaSuccess)
+        e = launch_scan(h->cursor, ntiles, c.cstride, ch.off, h->cursor, h->block_sums, h->stream);
     if (e == cudaSuccess)
         e = launch_scatter(c, u, v, w, weights, vis2, nvis, h->density, h->cursor, ch.ent, h->ctr, nullptr,
                            h->stream);
@@ -795,9 +800,10 @@ static rick_status degrid_impl(rick_handle h, const GridCfg& c, const double* su
     a.wc_scale = h->wc_scale;
     rick_status st = RICK_OK;
     e = cudaMemsetAsync(grad, 0, (size_t)nvis * sizeof(float2), h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->cursor, 0, (size_t)ntiles * sizeof(uint32_t), h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(h->cursor, 0, (size_t)ntiles * c.cstride * sizeof(uint32_t), h->stream);
     if (e == cudaSuccess) e = launch_primary_count(c, u, v, w, weights, nvis, h->cursor, h->stream);
-    if (e == cudaSuccess) e = launch_scan(h->cursor, ntiles, off, h->cursor, h->block_sums, h->stream);
+    if (e == cudaSuccess) e = launch_scan(h->cursor, ntiles, c.cstride, off, h->cursor, h->block_sums, h->stream);
     if (e == cudaSuccess) e = launch_primary_scatter(c, u, v, w, weights, nvis, h->cursor, perm, h->stream);
     if (e != cudaSuccess) st = fail(h, RICK_ERR_CUDA, "rick_degrid sort: %s", cudaGetErrorString(e));
     if (!st) count_launches(h, 5);
@@ -1072,9 +1078,9 @@ static rick_status batch_body(rick_handle h, const float* vis, const float* u, c
         PhaseScope scope(h, kPhasePrep);
         RICK_CU(h, cudaMemsetAsync(h->ctr, 0, sizeof(Counters), h->stream));
         RICK_CU(h, cudaMemsetAsync(h->chan_sw, 0, sizeof(double) * h->nchan, h->stream));
-        RICK_CU(h, cudaMemsetAsync(h->cursor, 0, (size_t)ntiles * sizeof(uint32_t), h->stream));
+        RICK_CU(h, cudaMemsetAsync(h->cursor, 0, (size_t)ntiles * c.cstride * sizeof(uint32_t), h->stream));
         RICK_CU(h, launch_count(c, u, v, w, weights, vis2, m, h->cursor, h->stream));
-        RICK_CU(h, launch_scan(h->cursor, ntiles, h->b_off, h->cursor, h->block_sums, h->stream));
+        RICK_CU(h, launch_scan(h->cursor, ntiles, c.cstride, h->b_off, h->cursor, h->block_sums, h->stream));
         RICK_CU(h, launch_scatter(c, u, v, w, weights, vis2, m, nullptr, h->cursor, h->b_ent, h->ctr, h->chan_sw,
                                   h->stream));
         count_launches(h, 5);

@@ -36,7 +36,7 @@ namespace {
 // its warp time proportional to the entries, run alone if it comes late in
 // the launch; a large pass hides that tail and gains from fewer chunk
 // flushes, a small one does not.
-constexpr uint32_t kHeavyMin = 256;
+constexpr uint32_t kHeavyMin = 64;
 constexpr uint32_t kHeavyMax = 768;
 constexpr uint32_t kHeavyDiv = 16384;
 constexpr int kTilesPerWarp = 4;

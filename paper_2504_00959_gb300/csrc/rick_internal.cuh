@@ -20,11 +20,24 @@ constexpr int kScanBlock = 1024;          // threads of the scan kernels
 constexpr int kScanItems = 4;             // items per scan thread
 constexpr int kScanTile = kScanBlock * kScanItems;
 
+// Words between consecutive per-tile counters of the counting sort.  With
+// few tiles (a small grid) the counters would share a handful of L2 lines,
+// and every measurement's atomic add would queue at the same few L2 slices;
+// spreading them up to one 128-byte line each (at most 2^16 words in all)
+// lets every slice take a share.  Large grids keep them packed.
+__host__ __device__ inline int counter_stride(int64_t ntiles)
+{
+    int s = 1;
+    while (s < 32 && ntiles * s * 2 <= 65536) s *= 2;
+    return s;
+}
+
 // Everything a kernel needs to place a measurement, by value.
 struct GridCfg {
     int n, nw, S, T, log2T, ntu;     // nw: planes in total (channels x planes per channel)
                                      // ntu: tiles per side = ceil(n / T)
     int64_t ntp;                     // tiles per plane = ntu * ntu
+    int cstride;                     // words between the per-tile counters (counter_stride)
     float uvscale;                   // cells per wavelength, binary32
     float half_n, half_s;            // n/2, S/2
     float wmin, invdw;               // binary32 plane decision constants
@@ -200,7 +213,9 @@ cudaError_t launch_density(const GridCfg& c, const float* u, const float* v, con
 cudaError_t launch_count(const GridCfg& c, const float* u, const float* v, const float* w,
                          const float* wt, const float2* vis, int64_t m, uint32_t* counts,
                          cudaStream_t s);
-cudaError_t launch_scan(const uint32_t* counts, int64_t len, uint32_t* offsets, uint32_t* cursor,
+// counts[i * stride] for i < len -> offsets[0..len] (packed, exclusive, total
+// last) and cursor[i * stride] = offsets[i]; counts may alias cursor
+cudaError_t launch_scan(const uint32_t* counts, int64_t len, int stride, uint32_t* offsets, uint32_t* cursor,
                         uint32_t* block_sums, cudaStream_t s);
 // chan_sw: per-channel weight sums (NULL: ctr->sum_w, single channel)
 cudaError_t launch_scatter(const GridCfg& c, const float* u, const float* v, const float* w,

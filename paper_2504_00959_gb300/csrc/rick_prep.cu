@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_count(GridCfg c, Inputs in, in
                     footprint_tiles(c, p[q], plane, t);
 #pragma unroll
                     for (int r = 0; r < 4; ++r)
-                        if (t[r] >= 0) atomicAdd(counts + t[r], 1u);
+                        if (t[r] >= 0) atomicAdd(counts + t[r] * c.cstride, 1u);
                 }
             }
         }
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_scatter(GridCfg c, Inputs in, 
 #pragma unroll
                         for (int r = 0; r < 4; ++r)
                             if (tt[r] >= 0) {
-                                entries[atomicAdd(cursor + tt[r], 1u)] = rw;
+                                entries[atomicAdd(cursor + tt[r] * c.cstride, 1u)] = rw;
                                 ++nent;
                             }
                     }
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_scatter(GridCfg c, Inputs in, 
                 footprint_tiles(c, p[q], p[q].k, t[q]);
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
-                    if (t[q][r] >= 0) slot[q][r] = atomicAdd(cursor + t[q][r], 1u);
+                    if (t[q][r] >= 0) slot[q][r] = atomicAdd(cursor + t[q][r] * c.cstride, 1u);
             }
 #pragma unroll
             for (int q = 0; q < kVisPerThread; ++q) {
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_primary_count(GridCfg c, Input
          i += (int64_t)gridDim.x * blockDim.x) {
         Place p;
         float wi;
-        if (place_coords(c, in, i, p, wi)) atomicAdd(counts + primary_tile(c, p), 1u);
+        if (place_coords(c, in, i, p, wi)) atomicAdd(counts + primary_tile(c, p) * c.cstride, 1u);
     }
 }
 
@@ -316,7 +316,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_primary_scatter(GridCfg c, Inp
          i += (int64_t)gridDim.x * blockDim.x) {
         Place p;
         float wi;
-        if (place_coords(c, in, i, p, wi)) perm[atomicAdd(cursor + primary_tile(c, p), 1u)] = (uint32_t)i;
+        if (place_coords(c, in, i, p, wi))
+            perm[atomicAdd(cursor + primary_tile(c, p) * c.cstride, 1u)] = (uint32_t)i;
     }
 }
 
@@ -424,7 +425,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* t
 }
 
 __global__ void __launch_bounds__(kScanBlock) k_scan_local(const uint32_t* __restrict__ in, int64_t len,
-                                                           uint32_t* __restrict__ out,
+                                                           int stride, uint32_t* __restrict__ out,
                                                            uint32_t* __restrict__ block_sums)
 {
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
@@ -432,7 +433,7 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_local(const uint32_t* __res
     uint32_t s = 0;
 #pragma unroll
     for (int j = 0; j < kScanItems; ++j) {
-        x[j] = (base + j < len) ? in[base + j] : 0u;
+        x[j] = (base + j < len) ? in[(base + j) * stride] : 0u;
         s += x[j];
     }
     uint32_t total;
@@ -463,7 +464,7 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_sums(uint32_t* __restrict__
 }
 
 __global__ void __launch_bounds__(kScanBlock) k_scan_add(const uint32_t* __restrict__ sums, int64_t len,
-                                                         uint32_t* __restrict__ out,
+                                                         int stride, uint32_t* __restrict__ out,
                                                          uint32_t* __restrict__ cursor)
 {
     const uint32_t add = sums[blockIdx.x];
@@ -473,7 +474,7 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_add(const uint32_t* __restr
         if (base + j < len) {
             const uint32_t o = out[base + j] + add;
             out[base + j] = o;
-            cursor[base + j] = o;
+            cursor[(base + j) * stride] = o;
         }
     }
 }
@@ -548,15 +549,15 @@ cudaError_t launch_count(const GridCfg& c, const float* u, const float* v, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan(const uint32_t* counts, int64_t len, uint32_t* offsets, uint32_t* cursor,
+cudaError_t launch_scan(const uint32_t* counts, int64_t len, int stride, uint32_t* offsets, uint32_t* cursor,
                         uint32_t* block_sums, cudaStream_t s)
 {
     const int64_t nb = (len + kScanTile - 1) / kScanTile;
     if (nb > 0x7fffffff) return cudaErrorInvalidValue;
     if (nb == 0) return cudaMemsetAsync(offsets, 0, sizeof(uint32_t), s);
-    k_scan_local<<<(unsigned)nb, kScanBlock, 0, s>>>(counts, len, offsets, block_sums);
+    k_scan_local<<<(unsigned)nb, kScanBlock, 0, s>>>(counts, len, stride, offsets, block_sums);
     k_scan_sums<<<1, kScanBlock, 0, s>>>(block_sums, nb, offsets, len);
-    k_scan_add<<<(unsigned)nb, kScanBlock, 0, s>>>(block_sums, len, offsets, cursor);
+    k_scan_add<<<(unsigned)nb, kScanBlock, 0, s>>>(block_sums, len, stride, offsets, cursor);
     return cudaGetLastError();
 }
 

@@ -95,7 +95,8 @@ extern "C" rick_status rick_grid_planes_static(const rick_params* p, const float
     const size_t o_coef = o_ctr + align256(sizeof(Counters));
     const size_t o_err = o_coef + align256(sizeof(float) * kMaxSupport * kPolyTerms);
     const size_t o_cursor = o_err + align256(sizeof(double) * kMaxSupport);
-    const size_t o_off = o_cursor + align256((size_t)(ntiles + 1) * sizeof(uint32_t));
+    const size_t cursor_words = (size_t)ntiles * c.cstride + 1;
+    const size_t o_off = o_cursor + align256(cursor_words * sizeof(uint32_t));
     const size_t o_sums = o_off + align256((size_t)(ntiles + 1) * sizeof(uint32_t));
     const size_t o_dens = o_sums + align256(scan_block_sums_len(ntiles) * sizeof(uint32_t));
     const size_t dens_bytes = c.uniform ? (size_t)c.n * c.n * sizeof(uint32_t) : 0;
@@ -169,11 +170,11 @@ extern "C" rick_status rick_grid_planes_static(const rick_params* p, const float
 
     const float2* vis2 = reinterpret_cast<const float2*>(vis);
     e = cudaMemsetAsync(ctr, 0, sizeof(Counters), stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, (size_t)ntiles * sizeof(uint32_t), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, (size_t)ntiles * c.cstride * sizeof(uint32_t), stream);
     if (e == cudaSuccess && density) e = cudaMemsetAsync(density, 0, dens_bytes, stream);
     if (e == cudaSuccess && density) e = launch_density(c, u, v, w, weights, vis2, nvis, density, stream);
     if (e == cudaSuccess) e = launch_count(c, u, v, w, weights, vis2, nvis, cursor, stream);
-    if (e == cudaSuccess) e = launch_scan(cursor, ntiles, off, cursor, sums, stream);
+    if (e == cudaSuccess) e = launch_scan(cursor, ntiles, c.cstride, off, cursor, sums, stream);
     if (e == cudaSuccess) e = launch_scatter(c, u, v, w, weights, vis2, nvis, density, cursor, ent, ctr, nullptr, stream);
     if (e == cudaSuccess) {
         ChunkList cl{};
@@ -181,7 +182,7 @@ extern "C" rick_status rick_grid_planes_static(const rick_params* p, const float
         cl.ent[0] = ent;
         cl.count = 1;
         // the scatter cursors are free again: they hold the gridder's heavy-tile list
-        e = launch_grid(c, cl, 0, c.nw, false, false, cursor, (size_t)ntiles + 1, reinterpret_cast<float2*>(planes),
+        e = launch_grid(c, cl, 0, c.nw, false, false, cursor, cursor_words, reinterpret_cast<float2*>(planes),
                         stream);
     }
     if (e != cudaSuccess) {

@@ -118,6 +118,7 @@ rick_status check_params(const rick_params* p, GridCfg* c, double* kparam, char*
     c->log2T = ilog2(T);
     c->ntu = (p->n + T - 1) / T;
     c->ntp = (int64_t)c->ntu * c->ntu;
+    c->ntu_log2 = (c->ntu & (c->ntu - 1)) == 0 ? ilog2(c->ntu) : -1;
     c->cstride = counter_stride((int64_t)c->nw * c->ntp);
     c->uvscale = (float)((double)p->n * p->pixel_rad);
     c->half_n = (float)(p->n / 2);
@@ -154,9 +155,18 @@ void split(double x, float* hi, float* lo)
 
 size_t plane_bytes(const rick_params* p) { return (size_t)p->n * p->n * sizeof(float2); }
 
-rick_status get_plan(rick_handle h, int batch, cufftHandle* out)
+// Plans of a handle, one per (kind, batch):
+//   kPlan2D    2D n x n transforms of `batch` planes
+//   kPlanRows  1D n-point transforms of the rows of `batch` planes
+//   kPlanColA  the first column factor of one plane for k_colstack: n1-point
+//              transforms along the column at a stride of n2 rows, for each
+//              of the n2 * n (row in block, column) pairs (batch unused)
+enum { kPlan2D = 0, kPlanRows = 1, kPlanColA = 2 };
+
+rick_status get_plan(rick_handle h, int batch, cufftHandle* out, int kind = kPlan2D)
 {
-    auto it = h->plans.find(batch);
+    const int key = (kind << 24) | batch;
+    auto it = h->plans.find(key);
     if (it != h->plans.end()) {
         *out = it->second;
         return RICK_OK;
@@ -164,14 +174,29 @@ rick_status get_plan(rick_handle h, int batch, cufftHandle* out)
     cufftHandle plan;
     RICK_FFT(h, cufftCreate(&plan));
     RICK_FFT(h, cufftSetAutoAllocation(plan, 0));
-    int dims[2] = {h->p.n, h->p.n};
+    const int n = h->p.n;
     size_t work = 0;
-    const long long dist = (long long)h->p.n * h->p.n;
-    cufftResult r = cufftMakePlanMany(plan, 2, dims, nullptr, 1, (int)dist, nullptr, 1, (int)dist, CUFFT_C2C,
-                                      batch, &work);
+    const long long dist = (long long)n * n;
+    cufftResult r;
+    if (kind == kPlan2D) {
+        int dims[2] = {n, n};
+        r = cufftMakePlanMany(plan, 2, dims, nullptr, 1, (int)dist, nullptr, 1, (int)dist, CUFFT_C2C, batch, &work);
+    } else if (kind == kPlanRows) {
+        int dims[1] = {n};
+        r = cufftMakePlanMany(plan, 1, dims, nullptr, 1, n, nullptr, 1, n, CUFFT_C2C, batch * n, &work);
+    } else {
+        int n1 = 0, n2 = 0;
+        if (!colstack_shape(n, &n1, &n2)) {
+            cufftDestroy(plan);
+            return fail(h, RICK_ERR_ARG, "no column split for n=%d", n);
+        }
+        int dims[1] = {n1}, emb[1] = {n1};
+        r = cufftMakePlanMany(plan, 1, dims, emb, n2 * n, 1, emb, n2 * n, 1, CUFFT_C2C, n2 * n, &work);
+    }
     if (r != CUFFT_SUCCESS) {
         cufftDestroy(plan);
-        return fail(h, RICK_ERR_CUFFT, "cufftMakePlanMany(n=%d, batch=%d): error %d", h->p.n, batch, (int)r);
+        return fail(h, RICK_ERR_CUFFT, "cufftMakePlanMany(kind=%d, n=%d, batch=%d): error %d", kind, n, batch,
+                    (int)r);
     }
     if (work > h->fft_work_bytes) {
         size_t fr = 0, tot = 0;
@@ -194,7 +219,7 @@ rick_status get_plan(rick_handle h, int batch, cufftHandle* out)
     }
     RICK_FFT(h, cufftSetWorkArea(plan, h->fft_work));
     RICK_FFT(h, cufftSetStream(plan, h->stream));
-    h->plans[batch] = plan;
+    h->plans[key] = plan;
     *out = plan;
     return RICK_OK;
 }
@@ -740,24 +765,49 @@ rick_status rick_fft_and_stack(rick_handle h, float* image)
     a.flags = p.flags;
     a.wcorr = h->cfg.Sw > 1 ? h->wcorr : nullptr;
     a.wc_scale = h->wc_scale;
+    // power-of-two n up to 4096: cuFFT transforms the rows and the first
+    // factor of the columns, k_colstack the last factor with the screen and
+    // the stack (the planes are read once after two cuFFT passes); otherwise
+    // cuFFT's 2D plan and k_stack
+    int n1 = 0, n2 = 0;
+    const bool split = colstack_shape(p.n, &n1, &n2);
+    const int64_t nn = (int64_t)p.n * p.n;
     for (int k0 = 0; k0 < p.nw; k0 += h->G) {
         const int nk = (p.nw - k0 < h->G) ? p.nw - k0 : h->G;
         rick_status s = grid_pass(h, k0, nk, true, h->planes);
         if (s) return s;
-        cufftHandle plan;
-        s = get_plan(h, nk, &plan);
-        if (s) return s;
-        {
-            PhaseScope fs(h, kPhaseFft);
-            RICK_FFT(h, cufftExecC2C(plan, reinterpret_cast<cufftComplex*>(h->planes),
-                                     reinterpret_cast<cufftComplex*>(h->planes), CUFFT_INVERSE));
-        }
+        cufftComplex* planes = reinterpret_cast<cufftComplex*>(h->planes);
         a.k0 = k0;
         a.nk = nk;
         a.first = (k0 == 0);
         a.last = (k0 + nk >= p.nw);
-        PhaseScope ss(h, kPhaseStack);
-        RICK_CU(h, launch_stack(a, h->planes, h->acc, h->taper, &h->ctr->sum_w, image, h->stream));
+        if (split) {
+            cufftHandle rows, cola;
+            if ((s = get_plan(h, nk, &rows, kPlanRows))) return s;
+            if ((s = get_plan(h, 1, &cola, kPlanColA))) return s;
+            {
+                PhaseScope fs(h, kPhaseFft);
+                RICK_FFT(h, cufftExecC2C(rows, planes, planes, CUFFT_INVERSE));
+                for (int kl = 0; kl < nk; ++kl)
+                    RICK_FFT(h, cufftExecC2C(cola, planes + kl * nn, planes + kl * nn, CUFFT_INVERSE));
+            }
+            if (!h->colmap_ready) {
+                RICK_CU(h, encode_colstack_map(h->colmap, h->planes, p.n, h->G));
+                h->colmap_ready = true;
+            }
+            PhaseScope ss(h, kPhaseStack);
+            RICK_CU(h, launch_colstack(h->colmap, a, n1, n2, h->acc, h->taper, &h->ctr->sum_w, image, &h->ctr->err,
+                                       h->stream));
+        } else {
+            cufftHandle plan;
+            if ((s = get_plan(h, nk, &plan))) return s;
+            {
+                PhaseScope fs(h, kPhaseFft);
+                RICK_FFT(h, cufftExecC2C(plan, planes, planes, CUFFT_INVERSE));
+            }
+            PhaseScope ss(h, kPhaseStack);
+            RICK_CU(h, launch_stack(a, h->planes, h->acc, h->taper, &h->ctr->sum_w, image, h->stream));
+        }
         count_launches(h, 1);
     }
     return RICK_OK;
@@ -1355,6 +1405,7 @@ rick_status rick_get_stats(rick_handle h, rick_stats* out)
     Counters c;
     RICK_CU(h, cudaStreamSynchronize(h->stream));
     RICK_CU(h, cudaMemcpy(&c, h->ctr, sizeof(c), cudaMemcpyDeviceToHost));
+    if (c.err) return fail(h, RICK_ERR_TIMEOUT, "a bounded wait of the column-stack kernel ran out (image invalid)");
     out->n_gridded = (int64_t)c.gridded;
     out->n_dropped = (int64_t)c.dropped;
     out->n_entries = (int64_t)c.entries;

@@ -285,9 +285,19 @@ struct TileGeom {
 __device__ __forceinline__ TileGeom tile_geom(const GridCfg& c, int k0, int64_t tl)
 {
     TileGeom g;
-    g.kl = (int)(tl / c.ntp);
-    const int rem = (int)(tl - (int64_t)g.kl * c.ntp);
-    const int tv = rem / c.ntu, tu = rem - tv * c.ntu;
+    int rem, tv, tu;
+    if (c.ntu_log2 >= 0) {
+        // power-of-two tiles per side: shifts instead of 64-bit division
+        g.kl = (int)(tl >> (2 * c.ntu_log2));
+        rem = (int)(tl & (c.ntp - 1));
+        tv = rem >> c.ntu_log2;
+        tu = rem & (c.ntu - 1);
+    } else {
+        g.kl = (int)(tl / c.ntp);
+        rem = (int)(tl - (int64_t)g.kl * c.ntp);
+        tv = rem / c.ntu;
+        tu = rem - tv * c.ntu;
+    }
     g.tg = (int64_t)(k0 + g.kl) * c.ntp + rem;
     g.u0 = tu * c.T;
     g.v0 = tv * c.T;

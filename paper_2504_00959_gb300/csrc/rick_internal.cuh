@@ -37,6 +37,7 @@ struct GridCfg {
     int n, nw, S, T, log2T, ntu;     // nw: planes in total (channels x planes per channel)
                                      // ntu: tiles per side = ceil(n / T)
     int64_t ntp;                     // tiles per plane = ntu * ntu
+    int ntu_log2;                    // log2(ntu) when ntu is a power of two, else -1
     int cstride;                     // words between the per-tile counters (counter_stride)
     float uvscale;                   // cells per wavelength, binary32
     float half_n, half_s;            // n/2, S/2
@@ -202,7 +203,8 @@ struct ChunkList {
 
 // Device-resident counters of a handle.
 struct Counters {
-    unsigned long long gridded, dropped, entries, pad;
+    unsigned long long gridded, dropped, entries;
+    unsigned long long err;          // bit 0: a bounded wait of k_colstack ran out
     double sum_w;
 };
 
@@ -262,6 +264,16 @@ __device__ __forceinline__ float wcorr_at(const StackArgs& a, float nm1)
 }
 
 // sum_w: the weight sum the image is normalised by (device)
+// n = n1 * n2 split of the column transform for k_colstack (power-of-two n in
+// [64, 4096]: n2 = 64 from n = 512 on, else 16); false: use cuFFT 2D + k_stack
+bool colstack_shape(int n, int* n1, int* n2);
+// screen + stack of a group whose rows and first column factor are transformed
+// (cuFFT), the last column factor done here; err: Counters::err
+// map: a CUtensorMap (128 bytes, 64-byte aligned) from encode_colstack_map
+// for the plane buffer the group is in
+cudaError_t encode_colstack_map(void* map, const float2* planes, int n, int planes_in_buffer);
+cudaError_t launch_colstack(const void* map, const StackArgs& a, int n1, int n2, float2* acc, const float* taper,
+                            const double* sum_w, void* image, unsigned long long* err, cudaStream_t s);
 cudaError_t launch_stack(const StackArgs& a, const float2* planes, float2* acc, const float* taper,
                          const double* sum_w, void* image, cudaStream_t s);
 
@@ -322,7 +334,9 @@ struct rick_imager {
     float wc_scale;
     void* fft_work;
     size_t fft_work_bytes;
-    std::map<int, cufftHandle> plans;// batch -> plan
+    std::map<int, cufftHandle> plans;// (kind, batch) -> plan
+    alignas(64) unsigned char colmap[128];  // tensor map of `planes` for k_colstack
+    bool colmap_ready;
     struct Chunk {
         uint32_t* off;
         float4* ent;

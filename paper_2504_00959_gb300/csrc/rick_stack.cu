@@ -12,6 +12,9 @@
 // complex rotation per plane and re-evaluated directly every kResync planes.
 #include "rick_internal.cuh"
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 namespace rick {
 namespace {
 
@@ -91,8 +94,10 @@ __global__ void __launch_bounds__(kStackThreads) k_stack(StackArgs a, const floa
     const int halfn = a.n >> 1;
     const int64_t idx = blockIdx.x * (int64_t)kStackThreads + threadIdx.x;
     if (idx >= (int64_t)a.n * halfn) return;
-    const int y = (int)(idx / halfn);
-    const int x0 = (int)(idx - (int64_t)y * halfn) * 2;
+    // n <= 32768: idx < n * n / 2 <= 2^29, so 32-bit division is exact
+    const uint32_t ui = (uint32_t)idx;
+    const int y = (int)(ui / (uint32_t)halfn);
+    const int x0 = (int)(ui - (uint32_t)y * (uint32_t)halfn) * 2;
     const int64_t pix = (int64_t)y * a.n + x0;
     const int64_t nn = (int64_t)a.n * a.n;
 
@@ -174,8 +179,10 @@ __global__ void __launch_bounds__(kStackThreads) k_spread(StackArgs a, const voi
     const int halfn = a.n >> 1;
     const int64_t idx = blockIdx.x * (int64_t)kStackThreads + threadIdx.x;
     if (idx >= (int64_t)a.n * halfn) return;
-    const int y = (int)(idx / halfn);
-    const int x0 = (int)(idx - (int64_t)y * halfn) * 2;
+    // n <= 32768: idx < n * n / 2 <= 2^29, so 32-bit division is exact
+    const uint32_t ui = (uint32_t)idx;
+    const int y = (int)(ui / (uint32_t)halfn);
+    const int x0 = (int)(ui - (uint32_t)y * (uint32_t)halfn) * 2;
     const int64_t pix = (int64_t)y * a.n + x0;
     const int64_t nn = (int64_t)a.n * a.n;
 
@@ -233,6 +240,302 @@ __global__ void __launch_bounds__(kStackThreads) k_spread(StackArgs a, const voi
     }
 }
 
+// ---------------------------------------------------------------------------
+// Column transform + w-screen + plane stack in one pass (the single-image path
+// for power-of-two n in [64, 4096]).  cuFFT has already transformed the rows
+// and the first factor of the column dimension: with n = N1 * N2 (N2 = 16),
+// row v = N2 a + b and output row y = f1 + N1 f2 (w_M = exp(2 pi i / M), the
+// inverse sign),
+//     Y[N2 f1 + b] = sum_a x[N2 a + b] w_N1^(a f1)
+// is in the plane, and the remaining factor
+//     X[f1 + N1 f2] = sum_b w_N2^(b f2) (w_n^(b f1) Y[N2 f1 + b])
+// is a 16-point transform of one contiguous block of 16 rows per f1.  A CTA
+// owns one f1 and 32 columns.  It streams that block of every plane of the
+// group through a ring of shared-memory stages, one 2D TMA box per plane
+// completing on the stage's mbarrier, does the 16 = 4 x 4 transform in two
+// register passes with an exchange inside each warp (b = 4 b1 + b0,
+// f2 = g0 + 4 g1: w_16^(b f2) = w_4^(b1 g0) w_16^(b0 g0) w_4^(b0 g1)), and sums
+// the planes with their w-screen per pixel.  The planes are read once and
+// never written back.
+
+constexpr int kColQ = 4;                     // N2 = kColQ^2 = 16-point column factor
+constexpr int kColN2 = kColQ * kColQ;
+constexpr int kColW = 32;                    // columns per CTA: one 256-byte row segment
+constexpr int kColWarps = kColW / 8;         // a warp owns 8 columns x kColQ values of j
+constexpr int kColThreads = 32 * kColWarps;
+constexpr int kColStages = 4;
+constexpr int kColPitch = kColW;             // complex values per staged row (the TMA box, dense)
+constexpr int kColExPitch = 36;              // complex values per g of a warp's exchange (2-way reads)
+constexpr size_t kColStageBytes = (size_t)kColN2 * kColPitch * sizeof(float2);
+constexpr size_t kColExBytes = (size_t)kColWarps * kColQ * kColExPitch * sizeof(float2);
+// stages (TMA destinations, at the 128-byte aligned start) | full and empty
+// mbarriers | the warps' exchange buffers | abort flag and issue count
+constexpr size_t kColSmem =
+    kColStages * kColStageBytes + 2 * kColStages * sizeof(unsigned long long) + kColExBytes + 2 * sizeof(int);
+constexpr unsigned long long kColWaitNs = 1000000000ull;  // bound of one wait: 1 s
+// planes summed by Horner's rule between direct evaluations of the screen
+// (the rotation per plane is applied in binary32, relative error ~1e-7 each)
+constexpr int kColResync = 32;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// one 2D tensor copy (TMA) of the box at (x, y) into shared memory,
+// completing its bytes on the mbarrier
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int xc, int yc, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(xc), "r"(yc), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait for the phase of the given parity to complete; false once kColWaitNs
+// have passed without it or another warp has given up (*abort set)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort)
+{
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (*abort || global_ns() - t0 > kColWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// In-place 4-point DFT with the + sign, natural order in and out.
+__device__ __forceinline__ void dft4(float2 (&v)[4])
+{
+    const float2 a0 = cadd(v[0], v[2]), a2 = csub(v[0], v[2]);
+    const float2 a1 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+    const float2 a3 = make_float2(-d.y, d.x);  // times +i
+    v[0] = cadd(a0, a1);
+    v[2] = csub(a0, a1);
+    v[1] = cadd(a2, a3);
+    v[3] = csub(a2, a3);
+}
+
+// planes: the group's nk planes, rows and the first column factor already
+// transformed; grid (n / kColW, N1).  Warp w owns columns x0 + 8 w + cl
+// (cl < 8) and lane j + 4 cl: b0 = j in the first pass, g0 = j in the second,
+// so the exchange between the passes stays inside the warp.  Stage s has a
+// "full" mbarrier (the bulk copies) and an "empty" one (one arrival per warp
+// once it has read the stage); warp 0 refills a stage when it is empty.
+// Planes are taken from the last to the first and summed per pixel by
+// Horner's rule, h <- h rho + v, times the screen of the block's first plane.
+// err: set to 1 when a bounded wait ran out.
+__global__ void __launch_bounds__(kColThreads, 4) k_colstack(const __grid_constant__ CUtensorMap map, StackArgs a,
+                                                             int n1,
+                                                             float2* __restrict__ acc, const float* __restrict__ taper,
+                                                             const double* __restrict__ sum_w, void* image,
+                                                             unsigned long long* err)
+{
+    extern __shared__ __align__(128) unsigned char col_smem[];
+    float2* stage = reinterpret_cast<float2*>(col_smem);  // [stages][N2][kColPitch]
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(col_smem + kColStages * kColStageBytes);
+    unsigned long long* empty = full + kColStages;
+    float2* exw = reinterpret_cast<float2*>(col_smem + kColStages * kColStageBytes +
+                                            2 * kColStages * sizeof(unsigned long long));
+    int& s_abort = *reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(exw) + kColExBytes);
+    int& s_issued = (&s_abort)[1];
+
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int j = lane & (kColQ - 1), cl = lane >> 2;
+    const int cw = 8 * w + cl;  // column in the CTA's strip
+    const int n = a.n, nk = a.nk;
+    const int x0 = blockIdx.x * kColW, x = x0 + cw;
+    const int f1 = blockIdx.y;
+    float2* ex = exw + (size_t)w * kColQ * kColExPitch;
+
+    if (t == 0) {
+        s_abort = 0;
+        for (int st = 0; st < kColStages; ++st) {
+            mbar_init(smem_u32(full + st), 1);
+            mbar_init(smem_u32(empty + st), kColWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    // slot i of the pipeline carries plane nk - 1 - i into stage i % stages:
+    // one TMA box of kColW columns x N2 rows, at row (plane n + N2 f1) of the
+    // map's [planes x n] x n view of the plane buffer
+    auto issue = [&](int i) {  // called by all of warp 0
+        if (lane == 0) {
+            const int st = i % kColStages;
+            const uint32_t bar = smem_u32(full + st);
+            mbar_expect(bar, (uint32_t)kColStageBytes);
+            tma_load_2d(smem_u32(stage + (size_t)st * kColN2 * kColPitch), &map, x0, (nk - 1 - i) * n + kColN2 * f1,
+                        bar);
+        }
+        __syncwarp();
+    };
+    int issued = nk < kColStages ? nk : kColStages;
+    if (w == 0)
+        for (int i = 0; i < issued; ++i) issue(i);
+
+    // twiddles: w_n^(b f1) for the thread's rows b = 4 b1 + j, and w_16^(j g0),
+    // each a power series of one exactly evaluated step (integer phases mod n)
+    float2 tw[kColQ], tin[kColQ];
+    {
+        float sn, cs;
+        sincospif(2.0f * (float)((int)(((int64_t)j * f1) % n)) / (float)n, &sn, &cs);
+        tw[0] = make_float2(cs, sn);
+        sincospif(2.0f * (float)((int)(((int64_t)kColQ * f1) % n)) / (float)n, &sn, &cs);
+        const float2 step = make_float2(cs, sn);
+        sincospif(2.0f * (float)j / (float)kColN2, &sn, &cs);
+        const float2 istep = make_float2(cs, sn);
+        tin[0] = make_float2(1.f, 0.f);
+#pragma unroll
+        for (int q = 1; q < kColQ; ++q) {
+            tw[q] = cmul(tw[q - 1], step);
+            tin[q] = cmul(tin[q - 1], istep);
+        }
+    }
+
+    // the thread's output pixels (x, y_g), y_g = f1 + N1 (j + 4 g): the screen's
+    // rotation per plane, the Horner sum of the current block and the total
+    float2 rho[kColQ], h[kColQ], sum[kColQ];
+#pragma unroll
+    for (int g = 0; g < kColQ; ++g) {
+        const PixelScreen ps = pixel_screen(a, x, f1 + n1 * (j + kColQ * g));
+        rho[g] = turns_to_phasor(ps.B.hi, ps.B.lo);
+        h[g] = make_float2(0.f, 0.f);
+        sum[g] = make_float2(0.f, 0.f);
+    }
+
+    bool ok = true;
+    for (int i = 0; i < nk && ok; ++i) {
+        const int st = i % kColStages;
+        const uint32_t ph = (uint32_t)((i / kColStages) & 1);
+        ok = mbar_wait(smem_u32(full + st), ph, &s_abort);
+        // first pass: 4-point transforms over b1 of w_n^(b f1) Y[b], times w_16^(b0 g0)
+        float2 v[kColQ];
+        const float2* blk = stage + (size_t)st * kColN2 * kColPitch;
+#pragma unroll
+        for (int q = 0; q < kColQ; ++q) v[q] = cmul(blk[(kColQ * q + j) * kColPitch + cw], tw[q]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(empty + st));  // this warp is done with the stage
+        dft4(v);
+#pragma unroll
+        for (int g = 0; g < kColQ; ++g) ex[g * kColExPitch + 8 * j + cl] = cmul(v[g], tin[g]);
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < kColQ; ++q) v[q] = ex[j * kColExPitch + 8 * q + cl];
+        __syncwarp();
+        // second pass: 4-point transforms over b0 for g0 = j
+        dft4(v);
+        // Horner step of plane p; at a block start, times the screen of plane p
+        const int p = nk - 1 - i;
+#pragma unroll
+        for (int g = 0; g < kColQ; ++g) h[g] = cadd(cmul(h[g], rho[g]), v[g]);
+        if (p % kColResync == 0) {
+#pragma unroll
+            for (int g = 0; g < kColQ; ++g) {
+                const PixelScreen ps = pixel_screen(a, x, f1 + n1 * (j + kColQ * g));
+                const float2 r = cmul(h[g], screen(ps.A, ps.B, a.k0 + p));
+                sum[g] = cadd(sum[g], r);
+                h[g] = make_float2(0.f, 0.f);
+            }
+        }
+        // warp 0 refills the stage once every warp has read it
+        if (w == 0 && ok && i + kColStages < nk) {
+            ok = mbar_wait(smem_u32(empty + st), ph, &s_abort);
+            if (ok) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(i + kColStages);
+                ++issued;
+            }
+        }
+        if (!ok) s_abort = 1;
+    }
+    if (w == 0 && lane == 0) s_issued = issued;
+    __syncthreads();
+    if (s_abort) {
+        // leave no bulk copy in flight into this CTA's shared memory: wait
+        // (bounded) for the last slot issued into every stage, in slot order
+        if (t == 0) {
+            atomicOr(err, 1ull);
+            const int last = s_issued;
+            for (int i = last > kColStages ? last - kColStages : 0; i < last; ++i) {
+                const unsigned long long t0 = global_ns();
+                for (;;) {
+                    uint32_t done;
+                    asm volatile(
+                        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                        " selp.u32 %0, 1, 0, p;\n}"
+                        : "=r"(done)
+                        : "r"(smem_u32(full + i % kColStages)), "r"((uint32_t)((i / kColStages) & 1))
+                        : "memory");
+                    if (done || global_ns() - t0 > kColWaitNs) break;
+                }
+            }
+        }
+        __syncthreads();
+        return;
+    }
+
+    const double sw = *sum_w;
+    const float inv_sw = (sw != 0.0) ? (float)(1.0 / sw) : 0.0f;
+#pragma unroll
+    for (int g = 0; g < kColQ; ++g) {
+        const int y = f1 + n1 * (j + kColQ * g);
+        const int64_t pix = (int64_t)y * n + x;
+        float2 r = sum[g];
+        if ((x + y) & 1) r = make_float2(-r.x, -r.y);  // fftshift sign (-1)^(x + y)
+        const PixelScreen ps = pixel_screen(a, x, y);
+        if (!ps.sky) r = make_float2(0.f, 0.f);
+        if (!a.first) {
+            const float2 prev = acc[pix];
+            r.x += prev.x;
+            r.y += prev.y;
+        }
+        if (!a.last) {
+            acc[pix] = r;
+            continue;
+        }
+        float f = inv_sw;
+        if (a.flags & RICK_GRID_CORRECT) f = f / (__ldg(taper + x) * __ldg(taper + y));
+        if (a.flags & RICK_APPLY_N) f *= 1.0f + ps.nm1;
+        if (a.wcorr) f /= wcorr_at(a, ps.nm1);
+        if (a.flags & RICK_REAL_IMAGE)
+            reinterpret_cast<float*>(image)[pix] = r.x * f;
+        else
+            reinterpret_cast<float2*>(image)[pix] = make_float2(r.x * f, r.y * f);
+    }
+}
 }  // namespace
 
 cudaError_t launch_spread(const StackArgs& a, const void* rimg, const float* taper, const double* sum_w,
@@ -252,6 +555,58 @@ cudaError_t launch_stack(const StackArgs& a, const float2* planes, float2* acc, 
     const int64_t blocks = (threads + kStackThreads - 1) / kStackThreads;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     k_stack<<<(unsigned)blocks, kStackThreads, 0, s>>>(a, planes, acc, taper, sum_w, image);
+    return cudaGetLastError();
+}
+
+
+bool colstack_shape(int n, int* n1, int* n2)
+{
+    if (n < 64 || n > 4096 || (n & (n - 1))) return false;
+    *n2 = kColN2;
+    *n1 = n / kColN2;
+    return true;
+}
+
+cudaError_t encode_colstack_map(void* map, const float2* planes, int n, int planes_in_buffer)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        const cudaError_t e =
+            cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    // the plane buffer as a [planes_in_buffer * n] x n matrix of 8-byte complex values
+    const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)planes_in_buffer * (cuuint64_t)n};
+    const cuuint64_t strides[1] = {(cuuint64_t)n * sizeof(float2)};
+    const cuuint32_t box[2] = {(cuuint32_t)kColW, (cuuint32_t)kColN2};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_UINT64, 2,
+                              const_cast<float2*>(planes), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_colstack(const void* map, const StackArgs& a, int n1, int n2, float2* acc, const float* taper,
+                            const double* sum_w, void* image, unsigned long long* err, cudaStream_t s)
+{
+    if (a.nk <= 0) return cudaSuccess;
+    if (n2 != kColN2 || (int64_t)n1 * n2 != a.n || a.n % kColW != 0) return cudaErrorInvalidValue;
+    static bool attr_done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_colstack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColSmem);
+        if (e != cudaSuccess) return e;
+        attr_done[dev] = true;
+    }
+    const dim3 grid((unsigned)(a.n / kColW), (unsigned)n1);
+    k_colstack<<<grid, kColThreads, kColSmem, s>>>(*reinterpret_cast<const CUtensorMap*>(map), a, n1, acc, taper,
+                                                   sum_w, image, err);
     return cudaGetLastError();
 }
 

@@ -63,6 +63,14 @@ typedef int32_t rick_status;
                                   which leaves Re(image) unchanged, so the w-planes need only
                                   cover the folded range (w_min, w_max >= 0 typically: half the
                                   planes for the same plane spacing) */
+#define RICK_FFT_2D 64u         /* transform the planes with cuFFT's 2D plan and stack them in a
+                                  separate pass, also where the library would otherwise split
+                                  the column transform and fuse its last factor with the
+                                  w-screen and the stack (single images with n = 4096) */
+#define RICK_FFT_SPLIT 128u     /* the split transform for any power-of-two n in [64, 4096]
+                                  (single images; slower than the 2D plan below 4096, for tests
+                                  and measurement).  Not with RICK_FFT_2D.  Either way the
+                                  result is the same up to rounding */
 
 /* Problem statement of Sec. 2.1: grid size, pixel scale, w-planes, kernel.
  * n: grid side, even, >= 2*support.  nw >= 1.  w_max > w_min when nw > 1.

@@ -21,6 +21,8 @@ REAL_IMAGE = 2
 APPLY_N = 4
 UNIFORM_WEIGHT = 8
 HERMITIAN_FOLD = 32
+FFT_2D = 64
+FFT_SPLIT = 128
 
 
 class RickParams(ctypes.Structure):

@@ -317,17 +317,22 @@ __device__ __forceinline__ unsigned long long global_ns()
 
 // wait for the phase of the given parity to complete; false once kColWaitNs
 // have passed without it or another warp has given up (*abort set)
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done)
+                 : "r"(bar), "r"(parity)
+                 : "memory");
+    return done != 0;
+}
+
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort)
 {
+    if (mbar_try(bar, parity)) return true;  // the common case: no clock reads
     const unsigned long long t0 = global_ns();
     for (;;) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
+        if (mbar_try(bar, parity)) return true;
         if (*abort || global_ns() - t0 > kColWaitNs) return false;
     }
 }
@@ -449,8 +454,9 @@ __global__ void __launch_bounds__(kColThreads, 4) k_colstack(const __grid_consta
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(empty + st));  // this warp is done with the stage
         dft4(v);
+        ex[8 * j + cl] = v[0];  // w_16^0 = 1
 #pragma unroll
-        for (int g = 0; g < kColQ; ++g) ex[g * kColExPitch + 8 * j + cl] = cmul(v[g], tin[g]);
+        for (int g = 1; g < kColQ; ++g) ex[g * kColExPitch + 8 * j + cl] = cmul(v[g], tin[g]);
         __syncwarp();
 #pragma unroll
         for (int q = 0; q < kColQ; ++q) v[q] = ex[j * kColExPitch + 8 * q + cl];
@@ -491,15 +497,8 @@ __global__ void __launch_bounds__(kColThreads, 4) k_colstack(const __grid_consta
             const int last = s_issued;
             for (int i = last > kColStages ? last - kColStages : 0; i < last; ++i) {
                 const unsigned long long t0 = global_ns();
-                for (;;) {
-                    uint32_t done;
-                    asm volatile(
-                        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                        " selp.u32 %0, 1, 0, p;\n}"
-                        : "=r"(done)
-                        : "r"(smem_u32(full + i % kColStages)), "r"((uint32_t)((i / kColStages) & 1))
-                        : "memory");
-                    if (done || global_ns() - t0 > kColWaitNs) break;
+                while (!mbar_try(smem_u32(full + i % kColStages), (uint32_t)((i / kColStages) & 1)) &&
+                       global_ns() - t0 <= kColWaitNs) {
                 }
             }
         }

@@ -1,0 +1,133 @@
+"""The split plane transform of single images (the default at n = 4096,
+RICK_FFT_SPLIT for any power-of-two n in [64, 4096]): cuFFT on the rows and
+on the first column factor, then k_colstack for the last 16-point factor
+together with the w-screen and the plane sum.  Checked against the FP64
+oracle (1e-4 of the image peak after weighting by the taper, as every image
+comparison) and against cuFFT's 2D plan with the separate stack
+(RICK_FFT_2D) on the same inputs (1e-5 of the peak), across plane groups
+(the accumulator between groups), the Hermitian fold, w-support > 1 (the w
+grid correction), the factor n and complex images."""
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+KB = synth.KERNEL_KB
+CORRECT, REAL, APPLY_N, FOLD = synth.FLAG_CORRECT, synth.FLAG_REAL, synth.FLAG_APPLY_N, synth.FLAG_FOLD
+
+
+@pytest.fixture(scope="module")
+def rick():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_00959_gb300 import build
+    build.build()
+    import paper_2504_00959_gb300 as r
+    r.load()
+    return r
+
+
+def _image(rick, prob, flags, **extra):
+    g = {k: prob[k].cuda() for k in ("vis", "u", "v", "w", "wt")}
+    im = rick.Imager(dict(prob["params"], flags=flags, **extra))
+    im.grid(g["vis"], g["u"], g["v"], g["w"], g["wt"])
+    out = im.image()
+    torch.cuda.synchronize()
+    st = im.stats()  # raises RickError if a bounded wait of the kernel ran out
+    im.close()
+    return out.cpu().numpy(), st
+
+
+@pytest.mark.parametrize("flags,extra", [
+    (CORRECT | REAL, {}),
+    (CORRECT | REAL, {"plane_group": 3}),
+    (CORRECT, {}),
+    (REAL | APPLY_N, {"plane_group": 5}),
+])
+def test_matches_oracle(rick, oracle_mod, flags, extra):
+    prob = synth.disk_problem(1024, 8, 30000, KB, 7, 4.0, 150.0, 611, fill=0.42, weights="random")
+    got, _ = _image(rick, prob, flags | rick.FFT_SPLIT, **extra)
+    p = synth.to_numpy(prob)
+    q = p["params"]
+    ref, _, _ = oracle_mod.dirty_image(q, p["u"], p["v"], p["w"], p["wt"], p["vis"], flags=flags & ~REAL)
+    if flags & REAL:
+        ref = ref.real
+    cc = np.ones((q["n"], q["n"]))
+    if flags & CORRECT:
+        c = oracle_mod.taper(q["n"], KB, 7, 0.0)
+        cc = np.outer(c, c)
+    err = np.max(np.abs(got - ref) * cc) / np.max(np.abs(ref) * cc)
+    assert err <= 1e-4, err
+
+
+@pytest.mark.parametrize("n,nw,m,flags,extra", [
+    (4096, 32, 400000, CORRECT | REAL, {}),
+    (4096, 12, 300000, CORRECT | REAL, {"plane_group": 5}),
+    (2048, 16, 300000, CORRECT, {"plane_group": 7}),
+    (2048, 8, 200000, CORRECT | REAL | APPLY_N, {}),
+])
+def test_split_equals_2d_plan(rick, n, nw, m, flags, extra):
+    prob = synth.config2(m=m, n=n, nw=nw)
+    a, st = _image(rick, prob, flags | rick.FFT_SPLIT, **extra)
+    b, _ = _image(rick, prob, flags | rick.FFT_2D, **extra)
+    assert st["n_gridded"] > 0.9 * m
+    assert np.max(np.abs(a - b)) <= 1e-5 * np.max(np.abs(b))
+
+
+def test_fold_and_w_support_through_the_split(rick):
+    """Hermitian fold (half the planes) and w-support 4 (the w grid
+    correction in the finalisation) through both transform paths."""
+    prob = synth.config2(m=300000, n=2048, nw=16)
+    q = prob["params"]
+    wabs = max(abs(q["w_min"]), abs(q["w_max"]))
+    fold = dict(nw=8, w_min=0.0, w_max=wabs)
+    a, _ = _image(rick, prob, CORRECT | REAL | FOLD | rick.FFT_SPLIT, **fold)
+    b, _ = _image(rick, prob, CORRECT | REAL | FOLD | rick.FFT_2D, **fold)
+    assert np.max(np.abs(a - b)) <= 1e-5 * np.max(np.abs(b))
+    half = wabs / (1.0 - 5.0 / 16)
+    ws = dict(w_min=-half, w_max=half, w_support=4)
+    a, _ = _image(rick, prob, CORRECT | REAL | rick.FFT_SPLIT, **ws)
+    b, _ = _image(rick, prob, CORRECT | REAL | rick.FFT_2D, **ws)
+    assert np.max(np.abs(a - b)) <= 1e-5 * np.max(np.abs(b))
+
+
+def test_repeated_images_reuse_the_tensor_map(rick):
+    """The TMA tensor map is encoded once per handle: later images and plane
+    groups on the same handle give the same result."""
+    prob = synth.config2(m=200000, n=1024, nw=9)
+    g = {k: prob[k].cuda() for k in ("vis", "u", "v", "w", "wt")}
+    im = rick.Imager(dict(prob["params"], flags=CORRECT | REAL | rick.FFT_SPLIT, plane_group=4))
+    outs = []
+    for _ in range(3):
+        im.reset()
+        im.grid(g["vis"], g["u"], g["v"], g["w"], g["wt"])
+        outs.append(im.image().clone())
+    torch.cuda.synchronize()
+    im.close()
+    # the same up to the rounding order of the gridder's atomic chunk flushes,
+    # which the taper division amplifies towards the edges (measured ~1e-6 of
+    # the peak); a stale tensor map would give errors of the order of the peak
+    peak = outs[0].abs().max().item()
+    for o in outs[1:]:
+        assert (o - outs[0]).abs().max().item() <= 1e-5 * peak
+
+
+def test_default_at_4096_is_the_split(rick):
+    """Without either flag, n = 4096 takes the split transform: the image
+    equals the one RICK_FFT_SPLIT gives, up to the gridder's atomic rounding."""
+    prob = synth.config2(m=300000, n=4096, nw=8)
+    a, _ = _image(rick, prob, CORRECT | REAL)
+    b, _ = _image(rick, prob, CORRECT | REAL | rick.FFT_SPLIT)
+    assert np.max(np.abs(a - b)) <= 1e-5 * np.max(np.abs(b))
+
+
+def test_flag_checks(rick):
+    prob = synth.config2(m=1000, n=1024, nw=4)
+    with pytest.raises(rick.RickError, match="exclude"):
+        rick.Imager(dict(prob["params"], flags=REAL | rick.FFT_2D | rick.FFT_SPLIT))
+    p = synth.disk_problem(34, 2, 100, KB, 7, 4.0, 10.0, 1)["params"]
+    with pytest.raises(rick.RickError, match="power-of-two"):
+        rick.Imager(dict(p, flags=REAL | rick.FFT_SPLIT))

@@ -361,7 +361,7 @@ __device__ __forceinline__ void dft4(float2 (&v)[4])
 // Planes are taken from the last to the first and summed per pixel by
 // Horner's rule, h <- h rho + v, times the screen of the block's first plane.
 // err: set to 1 when a bounded wait ran out.
-__global__ void __launch_bounds__(kColThreads, 4) k_colstack(const __grid_constant__ CUtensorMap map, StackArgs a,
+__global__ void __launch_bounds__(kColThreads, 6) k_colstack(const __grid_constant__ CUtensorMap map, StackArgs a,
                                                              int n1,
                                                              float2* __restrict__ acc, const float* __restrict__ taper,
                                                              const double* __restrict__ sum_w, void* image,

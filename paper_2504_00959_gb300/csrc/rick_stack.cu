@@ -442,6 +442,8 @@ __global__ void __launch_bounds__(kColThreads, 6) k_colstack(const __grid_consta
     }
 
     bool ok = true;
+    // two planes per trip (measured: 1.115 -> 1.082 ms at 4096^2 x 32; four: 1.158)
+#pragma unroll 2
     for (int i = 0; i < nk && ok; ++i) {
         const int st = i % kColStages;
         const uint32_t ph = (uint32_t)((i / kColStages) & 1);

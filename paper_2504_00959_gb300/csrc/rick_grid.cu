@@ -39,7 +39,7 @@ namespace {
 constexpr uint32_t kHeavyMin = 64;
 constexpr uint32_t kHeavyMax = 768;
 constexpr uint32_t kHeavyDiv = 16384;
-constexpr int kTilesPerWarp = 4;
+constexpr int kTilesPerWarp = 8;
 
 int sm_count_grid()
 {

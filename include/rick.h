@@ -158,7 +158,11 @@ rick_status rick_add_density(rick_handle h, const float* vis, const float* u, co
  * (cuFFT, unnormalised, exponent +), multiply by the phase screen
  * exp(+2 pi i w_k (n-1)) and sum over planes (Eq. 1); then divide by the
  * weight sum and, per flags, by the taper and times n.  image: float[n*n]
- * (RICK_REAL_IMAGE) or float[2*n*n] complex, fully overwritten. */
+ * (RICK_REAL_IMAGE) or float[2*n*n] complex, fully overwritten.  At n = 4096
+ * (or with RICK_FFT_SPLIT) cuFFT transforms the rows and the first factor of
+ * the columns and one kernel does the last 16-point column factor together
+ * with the screen and the sum, reading each plane once more; otherwise
+ * cuFFT's 2D plan and a separate screen-and-sum pass (RICK_FFT_2D). */
 rick_status rick_fft_and_stack(rick_handle h, float* image);
 
 /* Eq. 3 alone: the gridded planes k0 .. k0+nk-1 as complex float
@@ -281,7 +285,9 @@ rick_status rick_grid_planes_static(const rick_params* p, const float* vis, cons
                                     int64_t nvis, float* planes, void* cuda_stream, char* err,
                                     size_t err_len);
 
-/* Counters since the last reset (synchronises the stream). */
+/* Counters since the last reset (synchronises the stream).  RICK_ERR_TIMEOUT
+ * when a bounded wait inside the fused column-transform kernel ran out since
+ * the last reset (the image of that call is invalid; the context stays usable). */
 rick_status rick_get_stats(rick_handle h, rick_stats* out);
 
 /* Per-phase device time of the library's own work, from CUDA events recorded

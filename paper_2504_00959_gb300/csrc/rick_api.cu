@@ -179,6 +179,16 @@ enum { kPlan2D = 0, kPlanRows = 1, kPlanColA = 2 };
 // costs one cuFFT call per plane), at 4096^2 x 32 planes 8 % faster
 constexpr int kSplitMinN = 4096;
 
+// The split transform (cuFFT on the rows and the first column factor, the
+// last factor fused with the screen) for single images: n = 4096 by default,
+// any eligible n with RICK_FFT_SPLIT, never with RICK_FFT_2D.
+bool use_split(const rick_params& p, int* n1, int* n2)
+{
+    if (!colstack_shape(p.n, n1, n2)) return false;
+    if (p.flags & RICK_FFT_SPLIT) return true;
+    return !(p.flags & RICK_FFT_2D) && p.n >= kSplitMinN;
+}
+
 rick_status get_plan(rick_handle h, int batch, cufftHandle* out, int kind = kPlan2D)
 {
     const int key = (kind << 24) | batch;
@@ -786,8 +796,7 @@ rick_status rick_fft_and_stack(rick_handle h, float* image)
     // the stack (the planes are read once after two cuFFT passes); otherwise
     // cuFFT's 2D plan and k_stack
     int n1 = 0, n2 = 0;
-    const bool eligible = colstack_shape(p.n, &n1, &n2);
-    const bool split = eligible && ((p.flags & RICK_FFT_SPLIT) || (!(p.flags & RICK_FFT_2D) && p.n >= kSplitMinN));
+    const bool split = use_split(p, &n1, &n2);
     const int64_t nn = (int64_t)p.n * p.n;
     for (int k0 = 0; k0 < p.nw; k0 += h->G) {
         const int nk = (p.nw - k0 < h->G) ? p.nw - k0 : h->G;
@@ -874,20 +883,37 @@ static rick_status degrid_impl(rick_handle h, const GridCfg& c, const double* su
     if (e == cudaSuccess) e = launch_primary_scatter(c, u, v, w, weights, nvis, h->cursor, perm, h->stream);
     if (e != cudaSuccess) st = fail(h, RICK_ERR_CUDA, "rick_degrid sort: %s", cudaGetErrorString(e));
     if (!st) count_launches(h, 5);
+    // the adjoint of rick_fft_and_stack's transform path: with the split,
+    // k_spreadcol writes the planes after the adjoint of the last column
+    // factor, then cuFFT's forward first column factor and rows; otherwise
+    // k_spread and cuFFT's forward 2D plan
+    int n1 = 0, n2 = 0;
+    const bool split = use_split(p, &n1, &n2);
+    const int64_t nn = (int64_t)p.n * p.n;
+    cufftComplex* planes = reinterpret_cast<cufftComplex*>(h->planes);
     for (int k0 = 0; !st && k0 < p.nw; k0 += h->G) {
         const int nk = (p.nw - k0 < h->G) ? p.nw - k0 : h->G;
         a.k0 = k0;
         a.nk = nk;
-        e = launch_spread(a, image_grad, h->taper, sum_w, h->planes, h->stream);
+        e = split ? launch_spreadcol(a, n1, n2, image_grad, h->taper, sum_w, h->planes, h->stream)
+                  : launch_spread(a, image_grad, h->taper, sum_w, h->planes, h->stream);
         if (e != cudaSuccess) {
-            st = fail(h, RICK_ERR_CUDA, "k_spread: %s", cudaGetErrorString(e));
+            st = fail(h, RICK_ERR_CUDA, "%s: %s", split ? "k_spreadcol" : "k_spread", cudaGetErrorString(e));
             break;
         }
-        cufftHandle plan;
-        st = get_plan(h, nk, &plan);
-        if (st) break;
-        cufftResult r = cufftExecC2C(plan, reinterpret_cast<cufftComplex*>(h->planes),
-                                     reinterpret_cast<cufftComplex*>(h->planes), CUFFT_FORWARD);
+        cufftResult r = CUFFT_SUCCESS;
+        if (split) {
+            cufftHandle cola, rows;
+            if ((st = get_plan(h, 1, &cola, kPlanColA))) break;
+            if ((st = get_plan(h, nk, &rows, kPlanRows))) break;
+            for (int kl = 0; kl < nk && r == CUFFT_SUCCESS; ++kl)
+                r = cufftExecC2C(cola, planes + kl * nn, planes + kl * nn, CUFFT_FORWARD);
+            if (r == CUFFT_SUCCESS) r = cufftExecC2C(rows, planes, planes, CUFFT_FORWARD);
+        } else {
+            cufftHandle plan;
+            if ((st = get_plan(h, nk, &plan))) break;
+            r = cufftExecC2C(plan, planes, planes, CUFFT_FORWARD);
+        }
         if (r != CUFFT_SUCCESS) {
             st = fail(h, RICK_ERR_CUFFT, "cufftExecC2C(FORWARD): error %d", (int)r);
             break;

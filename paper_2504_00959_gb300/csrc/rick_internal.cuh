@@ -274,6 +274,11 @@ bool colstack_shape(int n, int* n1, int* n2);
 cudaError_t encode_colstack_map(void* map, const float2* planes, int n, int planes_in_buffer);
 cudaError_t launch_colstack(const void* map, const StackArgs& a, int n1, int n2, float2* acc, const float* taper,
                             const double* sum_w, void* image, unsigned long long* err, cudaStream_t s);
+// adjoint of launch_colstack: planes of the group from the image gradient
+// (rows 16 f1 + b after the last column factor's adjoint); cuFFT's forward
+// first column factor and rows complete the forward 2D transform
+cudaError_t launch_spreadcol(const StackArgs& a, int n1, int n2, const void* rimg, const float* taper,
+                             const double* sum_w, float2* planes, cudaStream_t s);
 cudaError_t launch_stack(const StackArgs& a, const float2* planes, float2* acc, const float* taper,
                          const double* sum_w, void* image, cudaStream_t s);
 

@@ -537,6 +537,122 @@ __global__ void __launch_bounds__(kColThreads, 6) k_colstack(const __grid_consta
             reinterpret_cast<float2*>(image)[pix] = make_float2(r.x * f, r.y * f);
     }
 }
+// In-place 4-point DFT with the - sign (the adjoint of dft4 up to order).
+__device__ __forceinline__ void dft4m(float2 (&v)[4])
+{
+    const float2 a0 = cadd(v[0], v[2]), a2 = csub(v[0], v[2]);
+    const float2 a1 = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+    const float2 a3 = make_float2(d.y, -d.x);  // times -i
+    v[0] = cadd(a0, a1);
+    v[2] = csub(a0, a1);
+    v[1] = cadd(a2, a3);
+    v[3] = csub(a2, a3);
+}
+
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b)  // a * conj(b)
+{
+    return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+
+// Adjoint of k_colstack (the backward pass of imaging and prediction, n with
+// the split transform): for one f1 and 32 columns, every plane k of the group
+// gets the rows 16 f1 + b
+//     Y'[16 f1 + b] = conj(w_n^(b f1)) sum_f2 w_16^(-b f2) Z_k[f1 + N1 f2],
+//     Z_k(x, y) = R(x, y) conj(screen_k(x, y)),
+// R the adjoint of the finalisation applied to the image gradient (sign,
+// sky mask, 1 / weight sum, taper, n and w correction per flags, as
+// k_spread).  cuFFT then applies the forward N1-point column factor and the
+// forward row transform: together the 2D forward transform of the screened
+// planes.  The thread's pixels, twiddles and the warp-local exchange are
+// those of k_colstack, the two 4-point passes taken in reverse order with
+// the conjugate sign; nothing waits on memory but the stores.
+__global__ void __launch_bounds__(kColThreads, 5) k_spreadcol(StackArgs a, int n1, const void* __restrict__ rimg,
+                                                              const float* __restrict__ taper,
+                                                              const double* __restrict__ sum_w,
+                                                              float2* __restrict__ planes)
+{
+    __shared__ float2 exw[kColWarps * kColQ * kColExPitch];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int j = lane & (kColQ - 1), cl = lane >> 2;
+    const int n = a.n;
+    const int x = blockIdx.x * kColW + 8 * w + cl;
+    const int f1 = blockIdx.y;
+    const int64_t nn = (int64_t)n * n;
+    float2* ex = exw + (size_t)w * kColQ * kColExPitch;
+
+    float2 tw[kColQ], tin[kColQ];
+    {
+        float sn, cs;
+        sincospif(2.0f * (float)((int)(((int64_t)j * f1) % n)) / (float)n, &sn, &cs);
+        tw[0] = make_float2(cs, sn);
+        sincospif(2.0f * (float)((int)(((int64_t)kColQ * f1) % n)) / (float)n, &sn, &cs);
+        const float2 step = make_float2(cs, sn);
+        sincospif(2.0f * (float)j / (float)kColN2, &sn, &cs);
+        const float2 istep = make_float2(cs, sn);
+        tin[0] = make_float2(1.f, 0.f);
+#pragma unroll
+        for (int q = 1; q < kColQ; ++q) {
+            tw[q] = cmul(tw[q - 1], step);
+            tin[q] = cmul(tin[q - 1], istep);
+        }
+    }
+
+    // the thread's pixels (x, y_g), y_g = f1 + N1 (j + 4 g): R, the screen's
+    // rotation per plane and the screen of the current plane
+    const double sw = *sum_w;
+    const float inv_sw = (sw != 0.0) ? (float)(1.0 / sw) : 0.0f;
+    float2 r[kColQ], rho[kColQ], z[kColQ];
+#pragma unroll
+    for (int g = 0; g < kColQ; ++g) {
+        const int y = f1 + n1 * (j + kColQ * g);
+        const int64_t pix = (int64_t)y * n + x;
+        const PixelScreen ps = pixel_screen(a, x, y);
+        float2 rv = (a.flags & RICK_REAL_IMAGE) ? make_float2(reinterpret_cast<const float*>(rimg)[pix], 0.f)
+                                                : reinterpret_cast<const float2*>(rimg)[pix];
+        float f = inv_sw;
+        if (a.flags & RICK_GRID_CORRECT) f = f / (__ldg(taper + x) * __ldg(taper + y));
+        if (a.flags & RICK_APPLY_N) f *= 1.0f + ps.nm1;
+        if (a.wcorr) f /= wcorr_at(a, ps.nm1);
+        if ((x + y) & 1) f = -f;  // fftshift sign (-1)^(x + y)
+        if (!ps.sky) f = 0.f;
+        r[g] = make_float2(rv.x * f, rv.y * f);
+        rho[g] = turns_to_phasor(ps.B.hi, ps.B.lo);
+        z[g] = screen(ps.A, ps.B, a.k0);
+    }
+
+    const int64_t row0 = (int64_t)kColN2 * f1;
+#pragma unroll 2
+    for (int p = 0; p < a.nk; ++p) {
+        float2 v[kColQ];
+#pragma unroll
+        for (int g = 0; g < kColQ; ++g) {
+            if (p > 0) {
+                if (p % kColResync == 0) {
+                    const PixelScreen ps = pixel_screen(a, x, f1 + n1 * (j + kColQ * g));
+                    z[g] = screen(ps.A, ps.B, a.k0 + p);
+                } else {
+                    z[g] = cmul(z[g], rho[g]);
+                }
+            }
+            v[g] = cmulc(r[g], z[g]);
+        }
+        // over g1 -> b0 (this thread is g0 = j), times conj(w_16^(b0 g0))
+        dft4m(v);
+        ex[8 * j + cl] = v[0];
+#pragma unroll
+        for (int q = 1; q < kColQ; ++q) ex[q * kColExPitch + 8 * j + cl] = cmulc(v[q], tin[q]);
+        __syncwarp();
+        // over g0 -> b1 (this thread is b0 = j), times conj(w_n^(b f1))
+#pragma unroll
+        for (int q = 0; q < kColQ; ++q) v[q] = ex[j * kColExPitch + 8 * q + cl];
+        __syncwarp();
+        dft4m(v);
+        float2* dst = planes + (int64_t)p * nn + (row0 + j) * n + x;
+#pragma unroll
+        for (int q = 0; q < kColQ; ++q) __stcs(dst + (int64_t)kColQ * q * n, cmulc(v[q], tw[q]));
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_spread(const StackArgs& a, const void* rimg, const float* taper, const double* sum_w,
@@ -559,6 +675,16 @@ cudaError_t launch_stack(const StackArgs& a, const float2* planes, float2* acc, 
     return cudaGetLastError();
 }
 
+
+cudaError_t launch_spreadcol(const StackArgs& a, int n1, int n2, const void* rimg, const float* taper,
+                             const double* sum_w, float2* planes, cudaStream_t s)
+{
+    if (a.nk <= 0) return cudaSuccess;
+    if (n2 != kColN2 || (int64_t)n1 * n2 != a.n || a.n % kColW != 0) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)(a.n / kColW), (unsigned)n1);
+    k_spreadcol<<<grid, kColThreads, 0, s>>>(a, n1, rimg, taper, sum_w, planes);
+    return cudaGetLastError();
+}
 
 bool colstack_shape(int n, int* n1, int* n2)
 {

@@ -261,13 +261,15 @@ rick_status rick_autotune_batch(const rick_params* p, int32_t nchan, const doubl
 /* Eq. 3 alone for one set of measurements, into caller-provided planes,
  * WITHOUT allocating any device memory.  The paper has no counterpart.  It is
  * for callers that cannot call cudaMalloc: code inside a framework that owns
- * the whole device heap, contexts where allocating is not allowed (stream
- * callbacks), real-time loops that forbid allocation after start-up.  No
- * handle is needed.  planes: complex float [nw][n][n] (no fftshift sign),
+ * the whole device heap through its own allocator, real-time loops that
+ * forbid allocation after start-up.  No handle is needed.  planes: complex float [nw][n][n] (no fftshift sign),
  * fully overwritten -- the same result as rick_create + rick_grid +
  * rick_grid_planes(0, nw).  The working memory is one fixed 64 MiB array in
- * the library's static device data, held by every GPU that loads the library
- * until the process exits.  What a call needs -- counters, kernel-tap
+ * the library's static device data.  Under CUDA's default lazy module
+ * loading that array is committed on a device at this function's first call
+ * there (the first cudaGetSymbolAddress loads its module), not when the
+ * library is loaded, and stays until the process exits; so make the first
+ * call before a framework claims the rest of the device heap.  What a call needs -- counters, kernel-tap
  * polynomials, two uint32 arrays of nw * ceil(n/tile)^2 (+1) tile counts and
  * offsets, the scan totals, n*n uint32 of density with RICK_UNIFORM_WEIGHT,
  * and 64 bytes per measurement (16 when support is 1), each piece 256-byte
@@ -284,6 +286,19 @@ rick_status rick_grid_planes_static(const rick_params* p, const float* vis, cons
                                     const float* v, const float* w, const float* weights,
                                     int64_t nvis, float* planes, void* cuda_stream, char* err,
                                     size_t err_len);
+
+/* Test hook of the error path of the fused column-transform kernel (the
+ * split transform of rick_fft_and_stack; the paper has no counterpart).
+ * Every wait of that kernel on its shared-memory pipeline is bounded; with
+ * skip_slot >= 0 the kernel's producer leaves out the copy of that pipeline
+ * slot (plane nk - 1 - skip_slot of a group of nk), so every thread block's
+ * wait on it runs out after wait_ns nanoseconds (<= 0: the default 1 s), the
+ * block waits for its other copies, leaves, and the failure is recorded:
+ * the next rick_get_stats returns RICK_ERR_TIMEOUT until rick_reset.  The
+ * image of such a call is invalid; the CUDA context stays usable.
+ * skip_slot = -1 restores normal operation (wait_ns still sets the bound).
+ * For tests of the timeout handling only; RICK_ERR_ARG for skip_slot < -1. */
+rick_status rick_debug_colstack(rick_handle h, int32_t skip_slot, int64_t wait_ns);
 
 /* Counters since the last reset (synchronises the stream).  RICK_ERR_TIMEOUT
  * when a bounded wait inside the fused column-transform kernel ran out since

@@ -216,6 +216,12 @@ class Imager:
         """Wait for everything enqueued on this imager (rick_synchronize)."""
         _lib.check(self._L.rick_synchronize(self._h), self._h)
 
+    def debug_colstack(self, skip_slot=-1, wait_ns=0):
+        """Test hook of the fused column kernel's bounded waits
+        (rick_debug_colstack): skip_slot >= 0 leaves that pipeline slot's copy
+        out so every wait on it runs out after wait_ns; -1 restores."""
+        _lib.check(self._L.rick_debug_colstack(self._h, int(skip_slot), int(wait_ns)), self._h)
+
     def stats(self):
         st = _lib.RickStats()
         _lib.check(self._L.rick_get_stats(self._h, ctypes.byref(st)), self._h)

@@ -791,6 +791,8 @@ rick_status rick_fft_and_stack(rick_handle h, float* image)
     a.flags = p.flags;
     a.wcorr = h->cfg.Sw > 1 ? h->wcorr : nullptr;
     a.wc_scale = h->wc_scale;
+    a.wait_ns = h->dbg_wait_ns;
+    a.skip_slot1 = h->dbg_skip_slot1;
     // power-of-two n up to 4096: cuFFT transforms the rows and the first
     // factor of the columns, k_colstack the last factor with the screen and
     // the stack (the planes are read once after two cuFFT passes); otherwise
@@ -1439,6 +1441,15 @@ rick_status rick_autotune_batch(const rick_params* p, int32_t nchan, const doubl
             fclose(f);
         }
     }
+    return RICK_OK;
+}
+
+rick_status rick_debug_colstack(rick_handle h, int32_t skip_slot, int64_t wait_ns)
+{
+    if (!h) return RICK_ERR_ARG;
+    if (skip_slot < -1) return fail(h, RICK_ERR_ARG, "skip_slot must be >= -1 (got %d)", (int)skip_slot);
+    h->dbg_skip_slot1 = skip_slot + 1;
+    h->dbg_wait_ns = wait_ns > 0 ? (unsigned long long)wait_ns : 0ull;
     return RICK_OK;
 }
 

@@ -250,6 +250,11 @@ struct StackArgs {
     float dw_hi, dw_lo;              // dw as a float pair
     int first, last;                 // first / last plane group
     unsigned flags;
+    // k_colstack's bounded waits: the limit of one wait in ns (0: 1 s), and
+    // a test hook: 1 + the pipeline slot whose copy the producer leaves out
+    // (0: none), so that every wait on it runs out and the error path runs
+    unsigned long long wait_ns;
+    int skip_slot1;
 };
 // The grid correction in w at a pixel with n - 1 = nm1 (linear interpolation
 // of the table; 1 without w-support).
@@ -391,5 +396,8 @@ struct rick_imager {
     cudaGraphExec_t graph;
     const void* graph_key[7];
     int64_t graph_m;
+    // test hook of k_colstack's bounded waits (rick_debug_colstack)
+    int dbg_skip_slot1;
+    unsigned long long dbg_wait_ns;
     char last_error[512];
 };

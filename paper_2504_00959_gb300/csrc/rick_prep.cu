@@ -1,6 +1,6 @@
-// rick_prep.cu -- sub-step 1 of gridding (Sec. 2.1: "an array is created for
-// each sector, concatenating the data with u-v coordinates inside the
-// corresponding sector"), done as a device counting sort by (w-plane, uv tile):
+// rick_prep.cu -- sub-step 1 of gridding (Sec. 2.1: the measurements are
+// gathered into one array per sector of the uv plane), done as a device
+// counting sort by (w-plane, uv tile):
 //   k_density  nearest-cell counts for uniform weighting
 //   k_count    entries per tile (a footprint straddling tiles is listed in
 //              every tile it touches)

@@ -272,7 +272,7 @@ constexpr size_t kColExBytes = (size_t)kColWarps * kColQ * kColExPitch * sizeof(
 // mbarriers | the warps' exchange buffers | abort flag and issue count
 constexpr size_t kColSmem =
     kColStages * kColStageBytes + 2 * kColStages * sizeof(unsigned long long) + kColExBytes + 2 * sizeof(int);
-constexpr unsigned long long kColWaitNs = 1000000000ull;  // bound of one wait: 1 s
+constexpr unsigned long long kColWaitNs = 1000000000ull;  // default bound of one wait: 1 s
 // planes summed by Horner's rule between direct evaluations of the screen
 // (the rotation per plane is applied in binary32, relative error ~1e-7 each)
 constexpr int kColResync = 32;
@@ -315,8 +315,10 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// wait for the phase of the given parity to complete; false once kColWaitNs
-// have passed without it or another warp has given up (*abort set)
+// wait for the phase of the given parity to complete; false once limit_ns
+// have passed without it or another warp has given up (*abort set).  The
+// result is per lane: callers make it warp-uniform (__all_sync) before
+// acting on it.
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
 {
     uint32_t done;
@@ -327,13 +329,14 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
     return done != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort,
+                                          unsigned long long limit_ns)
 {
     if (mbar_try(bar, parity)) return true;  // the common case: no clock reads
     const unsigned long long t0 = global_ns();
     for (;;) {
         if (mbar_try(bar, parity)) return true;
-        if (*abort || global_ns() - t0 > kColWaitNs) return false;
+        if (*abort || global_ns() - t0 > limit_ns) return false;
     }
 }
 
@@ -383,6 +386,7 @@ __global__ void __launch_bounds__(kColThreads, 6) k_colstack(const __grid_consta
     const int x0 = blockIdx.x * kColW, x = x0 + cw;
     const int f1 = blockIdx.y;
     float2* ex = exw + (size_t)w * kColQ * kColExPitch;
+    const unsigned long long limit = a.wait_ns ? a.wait_ns : kColWaitNs;
 
     if (t == 0) {
         s_abort = 0;
@@ -398,7 +402,7 @@ __global__ void __launch_bounds__(kColThreads, 6) k_colstack(const __grid_consta
     // one TMA box of kColW columns x N2 rows, at row (plane n + N2 f1) of the
     // map's [planes x n] x n view of the plane buffer
     auto issue = [&](int i) {  // called by all of warp 0
-        if (lane == 0) {
+        if (lane == 0 && i + 1 != a.skip_slot1) {
             const int st = i % kColStages;
             const uint32_t bar = smem_u32(full + st);
             mbar_expect(bar, (uint32_t)kColStageBytes);
@@ -447,7 +451,8 @@ __global__ void __launch_bounds__(kColThreads, 6) k_colstack(const __grid_consta
     for (int i = 0; i < nk && ok; ++i) {
         const int st = i % kColStages;
         const uint32_t ph = (uint32_t)((i / kColStages) & 1);
-        ok = mbar_wait(smem_u32(full + st), ph, &s_abort);
+        // one decision per warp: a lane whose wait ran out takes its warp out
+        ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(full + st), ph, &s_abort, limit));
         // first pass: 4-point transforms over b1 of w_n^(b f1) Y[b], times w_16^(b0 g0)
         float2 v[kColQ];
         const float2* blk = stage + (size_t)st * kColN2 * kColPitch;
@@ -480,7 +485,7 @@ __global__ void __launch_bounds__(kColThreads, 6) k_colstack(const __grid_consta
         }
         // warp 0 refills the stage once every warp has read it
         if (w == 0 && ok && i + kColStages < nk) {
-            ok = mbar_wait(smem_u32(empty + st), ph, &s_abort);
+            ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(empty + st), ph, &s_abort, limit));
             if (ok) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 issue(i + kColStages);
@@ -500,7 +505,7 @@ __global__ void __launch_bounds__(kColThreads, 6) k_colstack(const __grid_consta
             for (int i = last > kColStages ? last - kColStages : 0; i < last; ++i) {
                 const unsigned long long t0 = global_ns();
                 while (!mbar_try(smem_u32(full + i % kColStages), (uint32_t)((i / kColStages) & 1)) &&
-                       global_ns() - t0 <= kColWaitNs) {
+                       global_ns() - t0 <= limit) {
                 }
             }
         }

@@ -2,16 +2,19 @@
 //
 // Some callers cannot allocate device memory at all: code running inside a
 // host framework that owns the whole device heap (a fixed arena handed out by
-// the application), code called from a CUDA stream callback or another
-// context where cudaMalloc / cudaMallocAsync is not permitted, or real-time
-// pipelines that forbid allocation after start-up because it may block or
-// fragment.  rick_grid_planes_static serves them: it grids measurements into
-// planes the caller provides, and every byte of working memory it needs comes
-// from one fixed array in the library's static device data.
+// the application), or real-time pipelines that forbid allocation after
+// start-up because it may block or fragment.  rick_grid_planes_static serves
+// them: it grids measurements into planes the caller provides, and every
+// byte of working memory it needs comes from one fixed array in the
+// library's static device data.
 //
-// The array is kStaticScratchBytes (64 MiB).  Every GPU on which this library
-// is loaded holds it until the process exits, whether or not the function is
-// called.  All calls on a device share the same array and it keeps the last
+// The array is kStaticScratchBytes (64 MiB).  The library is built without
+// relocatable device code, so this file is a module of its own; under CUDA's
+// default lazy module loading the module, and with it the array, is loaded
+// on a device at the first cudaGetSymbolAddress there -- the function's
+// first call on that device -- and stays until the process exits.  That
+// first call must therefore come before a framework claims the rest of the
+// heap, and before any stream capture.  All calls on a device share the same array and it keeps the last
 // call's contents, so calls whose GPU work overlaps (on different streams or
 // from different host threads) race; the caller must order them.  Anything
 // that must start at zero is cleared at the start of each call.

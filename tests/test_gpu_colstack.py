@@ -220,3 +220,35 @@ def test_predict_split_equals_2d_plan(rick, oracle_mod):
                               prob["w"].cuda()).cpu().numpy())
         im.close()
     assert np.max(np.abs(out[0] - out[1])) <= 1e-5 * np.max(np.abs(out[1]))
+
+
+def test_bounded_wait_times_out_and_handle_recovers(rick):
+    """The error path of k_colstack's bounded waits: the test hook leaves the
+    copy of pipeline slot 0 out, so every thread block's wait on it runs out
+    after 2 ms; the call must be reported as RICK_ERR_TIMEOUT by the next
+    stats query (not hang), and after a reset the same handle must image
+    correctly again (the context stays usable)."""
+    prob = synth.disk_problem(256, 8, 20000, KB, 7, 3.0, 80.0, 907)
+    g = {k: prob[k].cuda() for k in ("vis", "u", "v", "w", "wt")}
+    flags = CORRECT | REAL
+    im = rick.Imager(dict(prob["params"], flags=flags | rick.FFT_SPLIT))
+    ref = rick.Imager(dict(prob["params"], flags=flags | rick.FFT_2D))
+    ref.grid(g["vis"], g["u"], g["v"], g["w"], g["wt"])
+    want = ref.image().cpu().numpy()
+    ref.close()
+    im.debug_colstack(0, 2_000_000)
+    im.grid(g["vis"], g["u"], g["v"], g["w"], g["wt"])
+    im.image()
+    torch.cuda.synchronize()
+    with pytest.raises(rick.RickError) as exc:
+        im.stats()
+    assert exc.value.status == 5  # RICK_ERR_TIMEOUT
+    # the hook off: the same handle images correctly after a reset
+    im.debug_colstack(-1, 0)
+    for _ in range(2):
+        im.reset()
+        im.grid(g["vis"], g["u"], g["v"], g["w"], g["wt"])
+        got = im.image().cpu().numpy()
+        im.stats()
+        assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want))
+    im.close()

@@ -358,6 +358,10 @@ static void or_grid(const or_cfg* c, int64_t m, const float* u, const float* v,
         if (weff[i] == 0.0) continue;
         or_place pl;
         if (!oracle_place(c, u[i], v[i], w[i], &pl)) continue;
+        /* taps only for a measurement with a plane in [k0, k1) */
+        int on_range = 0;
+        for (int k = k0; k < k1 && !on_range; ++k) on_range = or_plane_weight(c, &pl, k) != 0.0;
+        if (!on_range) continue;
         or_taps(c, pl.fu, pl.pu, gu);
         or_taps(c, pl.fv, pl.pv, gv);
         for (int k = k0; k < k1; ++k) {
@@ -668,7 +672,13 @@ int64_t oracle_dirty_image(int n, int nw, double pixel_rad, double w_min, double
  * pixel (x, y) of its plane image is
  *   a_m * [sum_t gu_t e^{2 pi i (fu+t-n/2)(x-n/2)/n}] [sum_t gv_t e^{2 pi i (fv+t-n/2)(y-n/2)/n}],
  * multiplied by the plane's phase screen.  Used for sampled checks at sizes
- * where the full FFT oracle is too slow.  pix: int32 pairs (x, y). */
+ * where the full FFT oracle is too slow.  pix: int32 pairs (x, y).
+ *
+ * The u-axis sum depends on the pixel's x only and the v-axis sum on its y
+ * only, so each is formed once per distinct column x and row y among the
+ * pixels; the phase factors e^{2 pi i ((j-n/2)(x-n/2) mod n)/n} of every cell
+ * j and the screens e^{2 pi i w_k (n-1)} of every plane are tabulated once
+ * (the same expressions evaluated once instead of per measurement). */
 int64_t oracle_image_at(int n, int nw, double pixel_rad, double w_min, double w_max,
                         int kernel, int support, double kparam, unsigned flags,
                         int64_t m, const float* u, const float* v, const float* w,
@@ -678,6 +688,8 @@ int64_t oracle_image_at(int n, int nw, double pixel_rad, double w_min, double w_
     or_cfg c;
     if (or_make_cfg(&c, n, nw, pixel_rad, w_min, w_max, kernel, support, kparam)) return -1;
     if (or_set_wsupport(&c, flags)) return -1;
+    for (int q = 0; q < npix; ++q)
+        if (pix[2 * q] < 0 || pix[2 * q] >= n || pix[2 * q + 1] < 0 || pix[2 * q + 1] >= n) return -1;
     or_prepare_wcorr(&c);
     or_fold_buf fold_buf;
     or_fold(flags, m, &u, &v, &w, &vis, &fold_buf);
@@ -688,16 +700,57 @@ int64_t oracle_image_at(int n, int nw, double pixel_rad, double w_min, double w_
     double* taper = (double*)malloc(sizeof(double) * n);
     or_taper(&c, taper);
     double complex* out = (double complex*)values_out;
-    /* per pixel: its n - 1 (or outside the sky) */
-    double* nm1 = (double*)malloc(sizeof(double) * (size_t)(npix > 0 ? npix : 1));
-    int* sky = (int*)malloc(sizeof(int) * (size_t)(npix > 0 ? npix : 1));
+    const int np1 = npix > 0 ? npix : 1;
+    /* per pixel: its n - 1 (or outside the sky), its column and row index */
+    double* nm1 = (double*)malloc(sizeof(double) * (size_t)np1);
+    int* sky = (int*)malloc(sizeof(int) * (size_t)np1);
+    int* xi = (int*)malloc(sizeof(int) * (size_t)np1);
+    int* yi = (int*)malloc(sizeof(int) * (size_t)np1);
+    int* xmap = (int*)malloc(sizeof(int) * (size_t)n);
+    int* ymap = (int*)malloc(sizeof(int) * (size_t)n);
+    int* xs = (int*)malloc(sizeof(int) * (size_t)np1);
+    int* ys = (int*)malloc(sizeof(int) * (size_t)np1);
+    int nx = 0, ny = 0;
+    for (int j = 0; j < n; ++j) xmap[j] = ymap[j] = -1;
+    for (int q = 0; q < npix; ++q) {
+        const int x = pix[2 * q], y = pix[2 * q + 1];
+        nm1[q] = or_nm1((x - n / 2) * pixel_rad, (y - n / 2) * pixel_rad, &sky[q]);
+        if (xmap[x] < 0) { xmap[x] = nx; xs[nx++] = x; }
+        if (ymap[y] < 0) { ymap[y] = ny; ys[ny++] = y; }
+        xi[q] = xmap[x];
+        yi[q] = ymap[y];
+    }
+    /* phase factor tables: eu[a * n + j] for column xs[a] and cell j (ev: rows) */
+    double complex* eu = (double complex*)malloc(sizeof(double complex) * (size_t)(nx > 0 ? nx : 1) * n);
+    double complex* ev = (double complex*)malloc(sizeof(double complex) * (size_t)(ny > 0 ? ny : 1) * n);
+#pragma omp parallel for schedule(static)
+    for (int a = 0; a < nx; ++a)
+        for (int j = 0; j < n; ++j) {
+            double au = OR_TWO_PI * (double)((long long)(j - n / 2) * (xs[a] - n / 2) % n) / n;
+            eu[(size_t)a * n + j] = cos(au) + I * sin(au);
+        }
+#pragma omp parallel for schedule(static)
+    for (int b = 0; b < ny; ++b)
+        for (int j = 0; j < n; ++j) {
+            double av = OR_TWO_PI * (double)((long long)(j - n / 2) * (ys[b] - n / 2) % n) / n;
+            ev[(size_t)b * n + j] = cos(av) + I * sin(av);
+        }
+    /* screen table: scr[q * nw + k] = e^{2 pi i w_k (n-1)} at pixel q */
+    double complex* scr = (double complex*)malloc(sizeof(double complex) * (size_t)np1 * nw);
     for (int q = 0; q < npix; ++q)
-        nm1[q] = or_nm1((pix[2 * q] - n / 2) * pixel_rad, (pix[2 * q + 1] - n / 2) * pixel_rad, &sky[q]);
-    double complex* sum = (double complex*)calloc((size_t)(npix > 0 ? npix : 1), sizeof(double complex));
-    /* measurement-outer: taps once per measurement, then every pixel */
+        for (int k = 0; k < nw; ++k) {
+            double ph = OR_TWO_PI * or_plane_w(&c, k) * nm1[q];
+            scr[(size_t)q * nw + k] = cos(ph) + I * sin(ph);
+        }
+    double complex* sum = (double complex*)calloc((size_t)np1, sizeof(double complex));
+    /* measurement-outer: taps and axis sums once per measurement, then every pixel */
 #pragma omp parallel
     {
-        double complex* part = (double complex*)calloc((size_t)(npix > 0 ? npix : 1), sizeof(double complex));
+        double complex* part = (double complex*)calloc((size_t)np1, sizeof(double complex));
+        double complex* su = (double complex*)malloc(sizeof(double complex) * (size_t)(nx > 0 ? nx : 1));
+        double complex* sv = (double complex*)malloc(sizeof(double complex) * (size_t)(ny > 0 ? ny : 1));
+        int kl[OR_MAX_SUPPORT];
+        double hl[OR_MAX_SUPPORT];
 #pragma omp for schedule(static)
         for (int64_t i = 0; i < m; ++i) {
             if (weff[i] == 0.0) continue;
@@ -707,34 +760,53 @@ int64_t oracle_image_at(int n, int nw, double pixel_rad, double w_min, double w_
             or_taps(&c, pl.fu, pl.pu, gu);
             or_taps(&c, pl.fv, pl.pv, gv);
             double complex a = weff[i] * ((double)vis[2 * i] + I * (double)vis[2 * i + 1]);
+            for (int b = 0; b < nx; ++b) {
+                const double complex* e = eu + (size_t)b * n + pl.fu;
+                double complex s = 0.0;
+                for (int t = 0; t < c.support; ++t) s += gu[t] * e[t];
+                su[b] = s;
+            }
+            for (int b = 0; b < ny; ++b) {
+                const double complex* e = ev + (size_t)b * n + pl.fv;
+                double complex s = 0.0;
+                for (int t = 0; t < c.support; ++t) s += gv[t] * e[t];
+                sv[b] = s;
+            }
+            /* the planes the measurement is gridded onto and their weights */
+            int nl = 0;
+            const int ka = c.sw == 1 ? pl.k : (pl.k > 0 ? pl.k : 0);
+            const int kb = c.sw == 1 ? pl.k + 1 : (pl.k + c.sw < nw ? pl.k + c.sw : nw);
+            for (int k = ka; k < kb; ++k) {
+                const double hk = or_plane_weight(&c, &pl, k);
+                if (hk == 0.0) continue;
+                kl[nl] = k;
+                hl[nl++] = hk;
+            }
             for (int q = 0; q < npix; ++q) {
                 if (!sky[q]) continue;
-                int x = pix[2 * q], y = pix[2 * q + 1];
-                double complex su = 0.0, sv = 0.0;
-                for (int t = 0; t < c.support; ++t) {
-                    double au = OR_TWO_PI * (double)((long long)(pl.fu + t - n / 2) * (x - n / 2) % n) / n;
-                    double av = OR_TWO_PI * (double)((long long)(pl.fv + t - n / 2) * (y - n / 2) % n) / n;
-                    su += gu[t] * (cos(au) + I * sin(au));
-                    sv += gv[t] * (cos(av) + I * sin(av));
-                }
-                /* the screens of the planes the measurement is gridded onto */
                 double complex sw_sum = 0.0;
-                for (int k = 0; k < c.nw; ++k) {
-                    const double hk = or_plane_weight(&c, &pl, k);
-                    if (hk == 0.0) continue;
-                    double ph = OR_TWO_PI * or_plane_w(&c, k) * nm1[q];
-                    sw_sum += hk * (cos(ph) + I * sin(ph));
-                }
-                part[q] += a * su * sv * sw_sum;
+                for (int r = 0; r < nl; ++r) sw_sum += hl[r] * scr[(size_t)q * nw + kl[r]];
+                part[q] += a * su[xi[q]] * sv[yi[q]] * sw_sum;
             }
         }
 #pragma omp critical
         for (int q = 0; q < npix; ++q) sum[q] += part[q];
+        free(sv);
+        free(su);
         free(part);
     }
     for (int q = 0; q < npix; ++q)
         out[q] = or_finalize_pixel(&c, flags, taper, sw, pix[2 * q], pix[2 * q + 1], sky[q] ? sum[q] : 0.0);
     free(sum);
+    free(scr);
+    free(ev);
+    free(eu);
+    free(ys);
+    free(xs);
+    free(ymap);
+    free(xmap);
+    free(yi);
+    free(xi);
     free(sky);
     free(nm1);
     free(taper);

@@ -1,19 +1,33 @@
 """Benchmark of the w-stacking imager hot path on GB300.
 
-One step = the whole path for one dirty image of the 4096^2 / 32 w-plane /
-1e7-visibility workload (256 antennas in a 20 km disk, 6 h Earth-rotation
-synthesis at dec -30, 10 s integrations, 1.4 GHz, 200-source sky + noise,
-Kaiser-Bessel support 7): reset, placement + counting sort, gridding of all
-planes, per-plane inverse FFT, phase-screen stack and finalisation.  Inputs
-are resident in HBM when the timed region starts; the planes (4.3 GB) are
-larger than L2, so no L2 flush is needed.
+One step = the whole path for one dirty image: reset, placement + counting
+sort (and the uniform-weighting density), gridding of every w-plane, the
+per-plane inverse FFT, the phase-screen stack and the finalisation.  Inputs
+are resident in HBM when the timed region starts; every step writes and reads
+all planes (hundreds of GB at the default size), far more than L2, so no L2
+flush is needed.
+
+Default workload (``--workload large``): a 16384^2 grid over a 5 degree
+field, 128 w-planes in plane groups, 2e8 visibilities of a 512-antenna,
+60 km, 8 h Earth-rotation synthesis at dec -45 (1.4 GHz), Kaiser-Bessel
+support 8, uniform weighting computed on the device.  ``--workload wstack``:
+the 4096^2 / 32-plane / 1e7-visibility image (256 antennas, 20 km, 6 h,
+dec -30, 200-source sky + noise, Kaiser-Bessel support 7).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload large|wstack|channels|adjoint|small]
 
-Multi-GPU (torchrun): every rank images its own copy of the workload (the path
-has no exchange step: replicas, weak scaling); value = all ranks' visibilities
-/ the slowest rank's time.  ``--impl reference`` times the FP64 CPU oracle on
-the host cores on a bounded sample of the same workload (rank 0 only).
+Multi-GPU (torchrun): every rank images its own copy of the workload (the
+path has no exchange step: replicas, weak scaling); value = all ranks'
+visibilities / the slowest rank's time.
+
+The line carries the gridder's roofline (``roofline``), the fused stack's
+(``roofline_other``), per-phase GB/s, NVML energy per image, the end-to-end
+rate through the C ABI with host buffers (``e2e``), and -- from the FP64
+oracle, on rank 0 at N = 1 -- the CPU baseline (``cpu_baseline``) and the
+error of the timed image against the oracle at sampled pixels (``parity``).
+``--impl reference`` times the FP64 oracle alone on the host cores, one
+bounded sample of the same workload per step (rank 0 only).
 """
 import argparse
 import ctypes
@@ -32,9 +46,34 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "visibilities/sec end-to-end (grid+FFT+w-stack), % roofline, J/solution"
-WORKLOAD = ("plain w-stacking, 4096x4096 grid, 32 w-planes, 1e7 visibilities (256 antennas, 20 km disk, "
-            "6 h synthesis, dec -30, 10 s, 1.4 GHz, 200 sources + noise), Kaiser-Bessel support 7, FP32")
-DATA = "synthetic: seeded Earth-rotation synthesis + point-source sky (the paper's LOFAR data is not available)"
+WORKLOADS = {
+    "large": ("plain w-stacking at SKA-like scale: 16384x16384 grid, 128 w-planes in plane groups, 2e8 "
+              "visibilities (512 antennas, 60 km disk, 8 h synthesis, dec -45, 1.4 GHz, 5 deg FOV), "
+              "Kaiser-Bessel support 8, uniform weighting computed on the device, FP32"),
+    "wstack": ("plain w-stacking, 4096x4096 grid, 32 w-planes, 1e7 visibilities (256 antennas, 20 km disk, "
+               "6 h synthesis, dec -30, 10 s, 1.4 GHz, 200 sources + noise), Kaiser-Bessel support 7, FP32"),
+}
+DATA = {
+    "large": "synthetic: seeded Earth-rotation synthesis, N(0,1) visibilities + a unit source at the phase "
+             "centre (the paper's LOFAR data is not available)",
+    "wstack": "synthetic: seeded Earth-rotation synthesis + point-source sky (the paper's LOFAR data is not "
+              "available)",
+}
+
+
+def make_problem(workload, device, nvis=None, nw=None):
+    """The seeded synthetic problem of a single-image workload and its flags."""
+    import synth
+    if workload == "large":
+        kw = {}
+        if nvis:
+            kw["m"] = nvis
+        if nw:
+            kw["nw"] = nw
+        prob = synth.config3(device=device, **kw)
+        return prob, dict(prob["params"])
+    prob = synth.config2(device=device, m=nvis or 10_000_000, nw=nw or 32)
+    return prob, dict(prob["params"], flags=synth.FLAG_CORRECT | synth.FLAG_REAL)
 
 
 def _peaks():
@@ -144,34 +183,148 @@ class Nvml:
 
 
 # ------------------------------------------------------------ CPU baseline
-def oracle_sample(prob_np, planes):
-    """Time the FP64 oracle on planes [k0, k1) of the full workload: gridding
-    (all measurements placed, those of the sample planes gridded) and the
-    FFT + stack of the sample planes; extrapolate to the whole workload
-    (gridding by the number of measurements, FFT + stack by the number of
-    planes).  Returns (visibilities/s, sample description, threads)."""
+ORACLE_SLICE = 2_000_000    # measurements of the placement and gridding sample
+ORACLE_MAX_FFT_N = 4096     # largest plane the FFT sample transforms
+
+
+def oracle_round(prob_np, plane):
+    """One bounded sample of the FP64 oracle on the host cores, the same
+    workload, each piece through the oracle's own entry points.  The oracle's
+    dirty image (oracle_dirty_image) computes the effective weights once (one
+    placement pass, two with uniform weighting), then for every plane places
+    all measurements again, grids those on the plane (taps + S^2 updates),
+    zeroes, transforms (FP64 FFT) and screens the plane, and finalises once.
+    Measured here:
+      t_pass  oracle.grid(slice, no plane): weights + one placement pass of a
+              slice of the measurements (1 thread)
+      t_zero  oracle.grid(no measurement, one plane): zeroing of one plane
+      t_grid  oracle.grid(slice, plane): the same + the gridding of the
+              slice's measurements on that plane (1 thread)
+      t_plane oracle.dirty_image(one measurement, plane) minus the same with
+              no plane, at n or at 4096 for larger n: one plane's zeroing,
+              FFT and screen (OpenMP)
+      t_fin   oracle.dirty_image(one measurement, no plane): the weights of
+              one measurement and the finalisation of n^2 pixels (OpenMP)
+    Returns the unit costs and the wall time of the round."""
     import numpy as np
 
     import oracle
     p = prob_np
     q = p["params"]
-    k0, k1 = planes
-    k, _, _ = oracle.place(q, p["u"], p["v"], p["w"])
-    m_all = int((k >= 0).sum())
-    m_s = int(((k >= k0) & (k < k1)).sum())
-    t0 = time.perf_counter()
-    oracle.grid(q, p["u"], p["v"], p["w"], p["wt"], p["vis"], k0=k0, k1=k1)
-    t_grid = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.dirty_image(q, p["u"], p["v"], p["w"], p["wt"], p["vis"], k0=k0, k1=k1)
-    t_full = time.perf_counter() - t0
-    t_rest = max(t_full - t_grid, 0.0)
-    t_est = t_grid * (m_all / max(m_s, 1)) + t_rest * (q["nw"] / (k1 - k0))
-    desc = (f"planes {k0}-{k1 - 1} of {q['nw']} ({m_s} of {m_all} visibilities gridded, all placed): "
-            f"grid {t_grid:.2f} s scaled x{m_all / max(m_s, 1):.1f}, FFT+stack {t_rest:.2f} s scaled "
-            f"x{q['nw'] / (k1 - k0):.0f}; measured {t_grid + t_full:.1f} s")
+    n, nw = int(q["n"]), int(q["nw"])
+    uniform = bool(int(q.get("flags", 0)) & 8)
+    m_all = p["u"].shape[0]
+    ms = min(m_all, ORACLE_SLICE)
+    sl = {k: p[k][:ms] for k in ("u", "v", "w", "wt", "vis")}
+    one = {k: p[k][:1] for k in ("u", "v", "w", "wt", "vis")}
+    none = {k: p[k][:0] for k in ("u", "v", "w", "wt", "vis")}
+    kk, _, _ = oracle.place(q, sl["u"], sl["v"], sl["w"])
+    on_plane = int((kk == plane).sum())
+    t_round = time.perf_counter()
+
+    def timed(fn, *a, **kw):
+        t0 = time.perf_counter()
+        fn(*a, **kw)
+        return time.perf_counter() - t0
+
+    args = lambda d: (d["u"], d["v"], d["w"], d["wt"], d["vis"])  # noqa: E731
+    t_pass = timed(oracle.grid, q, *args(sl), k0=0, k1=0)
+    t_zero = timed(oracle.grid, q, *args(none), k0=plane, k1=plane + 1)
+    t_grid = timed(oracle.grid, q, *args(sl), k0=plane, k1=plane + 1)
+    n_s = min(n, ORACLE_MAX_FFT_N)
+    qs = dict(q, n=n_s)
+    t_fin_s = timed(oracle.dirty_image, qs, *args(one), k0=0, k1=0)
+    t_pl_s = timed(oracle.dirty_image, qs, *args(one), k0=plane, k1=plane + 1) - t_fin_s
+    # an FFT of n^2 points costs ~ n^2 log n^2; the screen and finalisation ~ n^2
+    fft_scale = (n / n_s) ** 2 * math.log2(float(n) * n) / math.log2(float(n_s) * n_s)
+    passes = 3 if uniform else 2  # placement passes in t_pass: weights (1 or 2) + the grid call's own
+    c_place = t_pass / (ms * passes)
+    c_grid = max(t_grid - t_pass - t_zero, 0.0) / max(on_plane, 1)
     del np
-    return m_all / t_est, desc, oracle.num_threads(), t_grid + t_full
+    return {"c_place": c_place, "c_grid": c_grid, "t_plane": max(t_pl_s, 0.0) * fft_scale,
+            "t_fin": t_fin_s * (n / n_s) ** 2, "n_s": n_s, "fft_scale": fft_scale, "slice": ms,
+            "on_plane": on_plane, "plane": plane, "wall": time.perf_counter() - t_round,
+            "passes_w": passes - 1}
+
+
+def oracle_image_seconds(r, m_all, m_gridded, nw):
+    """Seconds of the oracle's whole dirty image from one round's unit costs:
+    weights (1 or 2 placement passes) + nw x (a placement pass + one plane's
+    zeroing, FFT and screen) + the gridding of every gridded measurement +
+    the finalisation."""
+    return (r["passes_w"] * m_all * r["c_place"] + nw * (m_all * r["c_place"] + r["t_plane"]) +
+            m_gridded * r["c_grid"] + r["t_fin"])
+
+
+def oracle_sample(prob_np, m_gridded, rounds=3):
+    """The FP64 oracle's rate on this workload (visibilities/s) from the median
+    of `rounds` bounded samples (oracle_round) on a plane holding a typical
+    number of measurements.  Returns (value, description, threads, seconds)."""
+    import numpy as np
+
+    import oracle
+    p = prob_np
+    q = p["params"]
+    n, nw = int(q["n"]), int(q["nw"])
+    m_all = p["u"].shape[0]
+    ms = min(m_all, ORACLE_SLICE)
+    kk, _, _ = oracle.place(q, p["u"][:ms], p["v"][:ms], p["w"][:ms])
+    cnt = np.bincount(kk[kk >= 0], minlength=nw)
+    plane = int(np.argmin(np.abs(cnt - cnt.mean())))  # the plane closest to the mean count
+    t0 = time.perf_counter()
+    rs = [oracle_round(p, plane) for _ in range(max(rounds, 1))]
+    wall = time.perf_counter() - t0
+    secs = [oracle_image_seconds(r, m_all, m_gridded, nw) for r in rs]
+    med = statistics.median(secs)
+    r = rs[secs.index(med)] if med in secs else rs[0]
+    threads = oracle.num_threads()
+    desc = (f"median of {len(rs)} rounds (image estimates {', '.join('%.0f' % x for x in secs)} s); per round: "
+            f"weights + placement of {r['slice']} measurements ({r['c_place'] * 1e9:.0f} ns per measurement "
+            f"and pass, 1 thread), gridding of plane {plane}'s {r['on_plane']} of them ({r['c_grid'] * 1e6:.2f} "
+            f"us per measurement, 1 thread), one plane's zeroing + FFT + screen at {r['n_s']}^2 "
+            f"({r['t_plane'] / r['fft_scale']:.2f} s, {threads} threads"
+            + (f", x{r['fft_scale']:.1f} for {n}^2 by n^2 log n^2" if r['n_s'] != n else "") +
+            f"); image = {r['passes_w']} weight pass(es) + {nw} x (placement pass of {m_all} + plane) + "
+            f"gridding of {m_gridded} + finalisation; measured {wall:.1f} s")
+    del np
+    return m_all / med, desc, threads, wall, {"placement_and_gridding": 1, "fft_and_screen": threads}
+
+
+def parity_check(prob_np, params, image, side=8):
+    """Error of a GPU image against the FP64 oracle (oracle_image_at: the same
+    discrete algorithm evaluated per pixel) at a side x side lattice of
+    pixels spanning the image edge to edge, the phase centre and the GPU
+    image's brightest pixel.  With grid correction both sides are compared
+    before the division by the taper (the GPU pixel times c(x) c(y)).
+    Returns max |gpu - oracle| / max |oracle| over the sampled pixels."""
+    import numpy as np
+
+    import oracle
+    q = dict(params)
+    n = int(q["n"])
+    flags = int(params["flags"])
+    img = np.asarray(image)
+    lat = np.unique(np.linspace(0, n - 1, side).round().astype(np.int64))
+    pix = [(int(x), int(y)) for y in lat for x in lat]
+    pk = int(np.argmax(np.abs(img)))
+    pix += [(n // 2, n // 2), (pk % n, pk // n)]
+    pix = np.array(sorted(set(pix)), dtype=np.int32)
+    t0 = time.perf_counter()
+    ref = oracle.image_at(q, prob_np["u"], prob_np["v"], prob_np["w"], prob_np["wt"], prob_np["vis"], pix,
+                          flags=flags & ~1)
+    secs = time.perf_counter() - t0
+    got = img[pix[:, 1], pix[:, 0]]
+    if flags & 1:
+        c = oracle.taper(n, int(q["kernel"]), int(q["support"]), float(q.get("kernel_param", 0.0) or 0.0))
+        got = got * c[pix[:, 0]] * c[pix[:, 1]]
+    if flags & 2:
+        ref = ref.real
+    err = float(np.max(np.abs(got - ref)) / max(np.max(np.abs(ref)), 1e-300))
+    del np
+    return {"max_abs_err_over_peak": err, "bound": 1e-4, "ok": err <= 1e-4, "pixels": int(pix.shape[0]),
+            "reference": "FP64 oracle (oracle_image_at) at a %dx%d pixel lattice edge to edge + phase centre + "
+                         "brightest pixel, before the taper division" % (len(lat), len(lat)),
+            "oracle_seconds": secs}
 
 
 # ------------------------------------------------------------------ main
@@ -192,11 +345,11 @@ def aggregate(ms_local, units_per_step, steps, world, device):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--nvis", type=int, default=10_000_000)
-    ap.add_argument("--nw", type=int, default=32, help="w-planes (profiling cases)")
+    ap.add_argument("--nvis", type=int, default=0, help="measurements (0: the workload's own count)")
+    ap.add_argument("--nw", type=int, default=0, help="w-planes (0: the workload's own count)")
     ap.add_argument("--tile", type=int, default=0, help="gridder tile side (0 = automatic)")
     ap.add_argument("--fold", action="store_true",
                     help="Hermitian fold (real image): measurements with w < 0 mirrored, half the w-planes "
@@ -204,55 +357,82 @@ def main():
     ap.add_argument("--w-support", type=int, default=0,
                     help="planes per measurement (Eq. 3's kernel in w); the plane range is padded by "
                          "nw / (nw - w_support) so every footprint lies on the planes")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="skip the FP64 oracle (CPU baseline and parity of the timed image)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--workload", choices=["wstack", "channels", "adjoint", "large", "small"], default="wstack",
-                    help="wstack: the 4096^2 / 32-plane / 1e7 image (default); channels: 64 channels "
-                         "batched vs imaged one by one; adjoint: image + loss gradient through the "
-                         "adjoint degridder on the same workload; large: 16384^2 / 128 planes / 2e8 "
-                         "measurements with uniform weighting, in plane groups; small: 256^2 / 8 planes / "
-                         "1e5, microseconds per image")
+    ap.add_argument("--workload", choices=["large", "wstack", "channels", "adjoint", "small"], default="large",
+                    help="large: 16384^2 / 128 planes / 2e8 measurements with uniform weighting, in plane "
+                         "groups (default); wstack: the 4096^2 / 32-plane / 1e7 image; channels: 64 channels "
+                         "batched vs imaged one by one; adjoint: image + loss gradient through the adjoint "
+                         "degridder on the wstack workload; small: 256^2 / 8 planes / 1e5, microseconds per "
+                         "image")
     args = ap.parse_args()
-
-    import torch
-    import torch.distributed as dist
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
     if args.workload == "channels":
         return run_channels(args, rank, world)
     if args.workload == "adjoint":
         return run_adjoint(args, rank, world)
-    if args.workload == "large":
-        return run_large(args, rank, world)
     if args.workload == "small":
         return run_small(args, rank, world)
+    return run_image(args, rank, world)
+
+
+def workload_config(wl, params, m, world, args):
+    """The `config` object of a single-image workload's line (the same in the
+    GPU arm and the reference arm)."""
+    n, nw = int(params["n"]), int(params["nw"])
+    desc = WORKLOADS[wl]
+    if args.fold:
+        desc += "; Hermitian fold: %d w-planes over [0, max |w|]" % nw
+    if args.w_support > 1:
+        desc += "; w-support %d on %d planes" % (args.w_support, nw)
+    return {"workload": desc, "n": n, "nw": nw, "nvis": int(m), "kernel": "kaiser-bessel",
+            "support": int(params["support"]), "uniform_weighting": bool(int(params["flags"]) & 8),
+            "l2": "inputs larger than L2 (%.2f GB of planes written and read every step)" % (8.0 * nw * n * n / 1e9),
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
+def _nvml_for(dev):
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    uuid = str(getattr(props, "uuid", ""))
+    uuid = uuid if uuid.startswith("GPU-") else ("GPU-" + uuid if uuid else "")
+    return (Nvml(uuid) if uuid else None), (uuid if uuid else dev.index)
+
+
+def run_image(args, rank, world):
+    """One dirty image per step of a single-image workload (large or wstack)."""
+    import torch
+    import torch.distributed as dist
 
     import synth
     import paper_2504_00959_gb300 as rick
     from paper_2504_00959_gb300 import build as rick_build
     rick_build.build()
-
+    local = int(os.environ.get("LOCAL_RANK", "0"))
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    prob = synth.config2(device=dev, m=args.nvis, nw=args.nw)
-    params = dict(prob["params"], flags=synth.FLAG_CORRECT | synth.FLAG_REAL, tile=args.tile)
+    wl = args.workload
+    prob, params = make_problem(wl, dev, args.nvis or None, args.nw or None)
+    params["tile"] = args.tile
     if args.fold:
         wabs = max(abs(params["w_min"]), abs(params["w_max"]))
-        params = dict(params, nw=max(args.nw // 2, 1), w_min=0.0, w_max=wabs,
+        params = dict(params, nw=max(params["nw"] // 2, 1), w_min=0.0, w_max=wabs,
                       flags=params["flags"] | synth.FLAG_FOLD)
     if args.w_support > 1:
         lo, hi, nwp = params["w_min"], params["w_max"], params["nw"]
         mid, half = 0.5 * (lo + hi), 0.5 * (hi - lo) * nwp / (nwp - args.w_support)
         params = dict(params, w_min=mid - half, w_max=mid + half, w_support=args.w_support)
     im = rick.Imager(params, device=dev)
-    img = torch.empty((params["n"], params["n"]), dtype=torch.float32, device=dev)
+    n, nw = params["n"], params["nw"]
+    img = torch.empty((n, n), dtype=torch.float32, device=dev)
     m = prob["u"].numel()
 
     def step():
@@ -265,11 +445,8 @@ def main():
     torch.cuda.synchronize()
     st = im.stats()
 
-    props = torch.cuda.get_device_properties(dev)
-    uuid = str(getattr(props, "uuid", ""))
-    uuid = uuid if uuid.startswith("GPU-") else ("GPU-" + uuid if uuid else "")
-    nvml = Nvml(uuid) if uuid else None
-    clocks = ClockSampler(uuid if uuid else local)
+    nvml, clock_id = _nvml_for(dev)
+    clocks = ClockSampler(clock_id)
     im.set_timing(True)
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
@@ -289,33 +466,60 @@ def main():
     clk = clocks.stop()
     ms = start.elapsed_time(end)
     tm = im.timing()
+    st = im.stats()  # raises if a bounded wait of the fused column kernel ran out
     ms, value = aggregate(ms, m, args.steps, world, dev)
-    ms_step = ms / max(args.steps, 1)
+    steps = max(args.steps, 1)
+    ms_step = ms / steps
 
-    # ------------------------------------------------ roofline (gridder)
+    # ------------------------------------------------ rooflines and phases
+    # algorithmic bytes per step: the gridder reads each gridded measurement
+    # once (u, v, w, weight, visibility: 24 B) and writes every plane cell
+    # once (8 B); cuFFT at least two read + write passes over the planes;
+    # the stack reads every plane once and writes the image (4 B per pixel,
+    # plus the complex accumulator between plane groups); the prep reads the
+    # measurements twice (count, scatter; a third time for the uniform-
+    # weighting density) and writes one 16 B entry per (measurement, tile)
     peak, peak_kind = _peaks()
-    n, nw = params["n"], params["nw"]
-    grid_launch_ms = tm["grid_ms"] / max(tm["grid_calls"], 1)
-    grid_bytes = 16.0 * st["n_gridded"] + 8.0 * nw * n * n
-    achieved = grid_bytes / (grid_launch_ms / 1e3) / 1e9
-    # the committed DRAM counters were taken on the 4096^2 x 32 x 1e7 workload only
-    default_size = (n, nw, m) == (4096, 32, 10_000_000) and params.get("w_support", 1) <= 1 \
-        and not params["flags"] & synth.FLAG_FOLD
-    traffic = _traffic("rick_grid.cu", "k_grid@4096x32x1e7") if default_size else None
-    stack_ms = tm["stack_ms"] / max(tm["stack_calls"], 1)
-    stack_bytes = 8.0 * nw * n * n + 4.0 * n * n
-    fft_ms = tm["fft_ms"] / max(tm["fft_calls"], 1)
-    fft_bytes = 2 * 2 * 8.0 * nw * n * n  # two passes, read + write
-    prep_ms = tm["prep_ms"] / max(tm["prep_calls"], 1)
-    prep_bytes = 2 * 24.0 * m + 16.0 * st["n_entries"]
+    cells = float(nw) * n * n
+    groups = -(-nw // max(st["plane_group"], 1))
+    uniform = bool(params["flags"] & synth.FLAG_UNIFORM)
+    grid_ms = tm["grid_ms"] / steps
+    grid_bytes = 24.0 * st["n_gridded"] + 8.0 * cells
+    stack_ms = tm["stack_ms"] / steps
+    stack_bytes = 8.0 * cells + 4.0 * n * n + (2 * 8.0 * n * n * (groups - 1) if groups > 1 else 0.0)
+    fft_ms = tm["fft_ms"] / steps
+    fft_bytes = 2 * 2 * 8.0 * cells
+    prep_ms = tm["prep_ms"] / steps
+    prep_bytes = (3 if uniform else 2) * 24.0 * m + 16.0 * st["n_entries"]
     phases = {
-        "prep": {"ms": prep_ms, "algorithmic_gb": prep_bytes / 1e9, "gbs": prep_bytes / prep_ms / 1e6},
-        "grid": {"ms": grid_launch_ms, "algorithmic_gb": grid_bytes / 1e9, "gbs": achieved},
-        "fft_cufft": {"ms": fft_ms, "algorithmic_gb": fft_bytes / 1e9, "gbs": fft_bytes / fft_ms / 1e6},
-        "stack": {"ms": stack_ms, "algorithmic_gb": stack_bytes / 1e9, "gbs": stack_bytes / stack_ms / 1e6},
+        "prep": {"ms": prep_ms, "algorithmic_gb": prep_bytes / 1e9},
+        "grid": {"ms": grid_ms, "algorithmic_gb": grid_bytes / 1e9},
+        "fft_cufft": {"ms": fft_ms, "algorithmic_gb": fft_bytes / 1e9},
+        "stack": {"ms": stack_ms, "algorithmic_gb": stack_bytes / 1e9},
     }
     for v in phases.values():
-        v["frac_of_" + peak_kind] = v["gbs"] / peak
+        v["gbs"] = v["algorithmic_gb"] / v["ms"] * 1e3 if v["ms"] > 0 else None
+        v["frac_of_" + peak_kind] = v["gbs"] / peak if v["gbs"] else None
+    # the committed DRAM counters were taken on the 4096^2 x 32 x 1e7 workload only
+    default_size = wl == "wstack" and (n, nw, m) == (4096, 32, 10_000_000) and \
+        params.get("w_support", 1) <= 1 and not params["flags"] & synth.FLAG_FOLD
+    traffic = _traffic("rick_grid.cu", "k_grid@4096x32x1e7") if default_size else None
+    split = n == 4096  # the library's default transform path at this size (cuFFT + k_colstack)
+    stack_name = ("k_colstack (last 16-point column factor + w-screen + stack, Eq. 1)" if split
+                  else "k_stack (w-screen + stack, Eq. 1)")
+    stack_traffic = _traffic("rick_stack.cu", "k_colstack@4096x32x1e7") if (default_size and split) else None
+    launches_grid = max(tm["grid_calls"] / steps, 1)
+    launches_stack = max(tm["stack_calls"] / steps, 1)
+    rl_grid = {"kernel": "k_grid_tiles + k_grid_chunks (gridding, Eq. 3)", "bound": "hbm",
+               "achieved": grid_bytes / grid_ms / 1e6, "peak": peak, "unit": "GB/s",
+               "frac": grid_bytes / grid_ms / 1e6 / peak, "traffic": traffic, "peak_kind": peak_kind,
+               "algorithmic_bytes_per_launch": grid_bytes / launches_grid, "launch_ms": grid_ms / launches_grid,
+               "launches_per_step": launches_grid}
+    rl_stack = {"kernel": stack_name, "bound": "hbm", "achieved": stack_bytes / stack_ms / 1e6, "peak": peak,
+                "unit": "GB/s", "frac": stack_bytes / stack_ms / 1e6 / peak, "traffic": stack_traffic,
+                "peak_kind": peak_kind, "algorithmic_bytes_per_launch": stack_bytes / launches_stack,
+                "launch_ms": stack_ms / launches_stack, "launches_per_step": launches_stack}
+    rl, rl_other = (rl_stack, rl_grid) if stack_ms > grid_ms else (rl_grid, rl_stack)
 
     # ------------------------------------------------ end to end, host buffers
     e2e = None
@@ -327,7 +531,7 @@ def main():
         im.image_host(hv, hu, hvv, hw, hwt, out=himg)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ksteps = max(min(args.steps, 5), 1)
+        ksteps = max(min(args.steps, 3), 1)
         for _ in range(ksteps):
             im.image_host(hv, hu, hvv, hw, hwt, out=himg)
         te_sync = (time.perf_counter() - t0) / ksteps
@@ -346,60 +550,42 @@ def main():
                "h2d_bytes_per_step": int(m * (8 + 4 + 4 + 4 + 4)), "d2h_bytes_per_step": int(n * n * 4),
                "api": "rick_image_host_async over %d images, then rick_synchronize (pinned host buffers)" % ksteps,
                "unpipelined_ms_per_step": te_sync * 1e3}
+        del hv, hu, hvv, hw, hwt
 
-    cpu = None
+    # ------------------------------------------------ FP64 oracle: CPU baseline and parity
+    cpu = parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        image_cpu = img.cpu().numpy()
+        im.close()
         prob_np = synth.to_numpy(prob)
-        v, desc, threads, secs = oracle_sample(prob_np, (15, 17))
-        cpu = {"value": v, "unit": "vis/s", "cores": threads, "kind": "oracle", "sample": desc}
+        prob_np["params"] = dict(params)
+        del prob
+        parity = parity_check(prob_np, params, image_cpu)
+        v, desc, threads, secs, by_phase = oracle_sample(prob_np, st["n_gridded"])
+        cpu = {"value": v, "unit": "vis/s", "cores": threads, "kind": "oracle", "sample": desc,
+               "threads_by_phase": by_phase, "seconds": secs}
+    else:
+        im.close()
 
     energy = None
     if e0 is not None and e1 is not None:
-        energy = (e1 - e0) / 1e3 / max(args.steps, 1)
+        energy = (e1 - e0) / 1e3 / steps
 
+    config = workload_config(wl, params, m, world, args)
+    # whole step against HBM: prep + gridder + FFT (2 passes) + stack
+    step_bytes = prep_bytes + grid_bytes + fft_bytes + stack_bytes
     out = {
         "metric": METRIC, "value": value, "unit": "vis/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": DATA,
-        "config": {"workload": WORKLOAD + ("; Hermitian fold: %d w-planes over [0, max |w|]" % nw if args.fold
-                                           else "") +
-                   ("; w-support %d on %d planes" % (args.w_support, nw) if args.w_support > 1 else ""),
-                   "n": n, "nw": nw, "nvis": m, "kernel": "kaiser-bessel", "support": 7,
-                   "tile": st["tile"], "plane_group": st["plane_group"],
-                   "l2": "inputs larger than L2 (%.2f GB of planes written and read every step)" % (8.0 * nw * n * n / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": None,
-        "roofline_other": None,
-        "phases": phases,
-        "energy_j_per_solution": energy,
-        "e2e": e2e,
-        "cpu_baseline": cpu,
-        "gpu_launches": int(tm["kernel_launches"]),
-        "clocks": clk,
-        "roofline_frac_end_to_end": None,
+        "vs_baseline": None, "dtype": "f32", "data": DATA[wl], "config": config,
+        "roofline": rl, "roofline_other": rl_other, "phases": phases,
+        "roofline_frac_end_to_end": step_bytes / (ms_step / 1e3) / 1e9 / peak,
+        "energy_j_per_solution": energy, "e2e": e2e, "cpu_baseline": cpu, "parity": parity,
+        "gpu_launches": int(tm["kernel_launches"]), "clocks": clk,
+        "launch": {"tile": st["tile"], "plane_group": st["plane_group"], "plane_groups": groups},
     }
-    # roofline of our dominant kernel (the longer of the gridder and the stack)
-    # in `roofline`, the other in `roofline_other`
-    rl_grid = {"kernel": "k_grid_tiles + k_grid_chunks (gridding, Eq. 3)", "bound": "hbm", "achieved": achieved,
-               "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-               "algorithmic_bytes_per_launch": grid_bytes, "launch_ms": grid_launch_ms}
-    split = n == 4096  # the library's default transform path at this size (cuFFT + k_colstack)
-    stack_name = ("k_colstack (last 16-point column factor + w-screen + stack, Eq. 1)" if split
-                  else "k_stack (w-screen + stack, Eq. 1)")
-    stack_traffic = _traffic("rick_stack.cu", "k_colstack@4096x32x1e7") if (default_size and split) else None
-    rl_stack = {"kernel": stack_name, "bound": "hbm", "achieved": stack_bytes / stack_ms / 1e6, "peak": peak,
-                "unit": "GB/s", "frac": stack_bytes / stack_ms / 1e6 / peak, "traffic": stack_traffic,
-                "peak_kind": peak_kind, "algorithmic_bytes_per_launch": stack_bytes, "launch_ms": stack_ms}
-    if stack_ms > grid_launch_ms:
-        out["roofline"], out["roofline_other"] = rl_stack, rl_grid
-    else:
-        out["roofline"], out["roofline_other"] = rl_grid, rl_stack
-    # whole step against HBM: inputs + plane write + FFT (2 passes) + stack read + image
-    step_bytes = 24.0 * m + 8.0 * nw * n * n + fft_bytes + stack_bytes
-    out["roofline_frac_end_to_end"] = step_bytes / (ms_step / 1e3) / 1e9 / peak
     if rank == 0:
         print(json.dumps(out))
-    im.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -510,7 +696,7 @@ def run_adjoint(args, rank, world):
     rick_build.build()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
-    prob = synth.config2(device=dev, m=args.nvis, nw=args.nw)
+    prob = synth.config2(device=dev, m=args.nvis or 10_000_000, nw=args.nw or 32)
     params = dict(prob["params"], flags=synth.FLAG_CORRECT | synth.FLAG_REAL, tile=args.tile)
     im = rick.Imager(params, device=dev)
     m = prob["u"].numel()
@@ -562,8 +748,8 @@ def run_adjoint(args, rank, world):
         print(json.dumps({
             "metric": "visibilities/sec, dirty image + loss gradient through the adjoint degridder",
             "value": m / (ms / 1e3), "unit": "vis/s", "higher_is_better": True, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "dtype": "f32", "data": DATA,
-            "config": {"workload": "differentiable imaging: " + WORKLOAD, "n": n, "nw": nw, "nvis": m,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "dtype": "f32", "data": DATA["wstack"],
+            "config": {"workload": "differentiable imaging: " + WORKLOADS["wstack"], "n": n, "nw": nw, "nvis": m,
                        "tile": st["tile"], "plane_group": st["plane_group"],
                        "loss": "sum (D - t)^2, t = image of V (1 + 0.1 N(0,1))"},
             "phases": {"forward_ms": fwd_ms, "backward_degrid_ms": deg_ms,
@@ -574,93 +760,6 @@ def run_adjoint(args, rank, world):
             else None,
             "gpu_launches": int(tm["kernel_launches"]), "clocks": clk}))
     im.close()
-
-
-def run_large(args, rank, world):
-    """The 16384^2 / 128-plane / 2e8-measurement image with uniform weighting
-    (5 degree field, Kaiser-Bessel support 8): the planes (275 GB) do not fit
-    at once, so every step grids, transforms and stacks plane group after
-    plane group, re-reading the measurements for each group.  Reported
-    beside the default line, not instead of it."""
-    import torch
-
-    import synth
-    import paper_2504_00959_gb300 as rick
-    from paper_2504_00959_gb300 import build as rick_build
-    rick_build.build()
-    if rank != 0:
-        return
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
-    torch.cuda.set_device(dev)
-    prob = synth.config3(device=dev)
-    params = dict(prob["params"], tile=args.tile)
-    im = rick.Imager(params, device=dev)
-    n, nw = params["n"], params["nw"]
-    m = prob["u"].numel()
-    img = torch.empty((n, n), dtype=torch.float32, device=dev)
-
-    def step():
-        im.reset()
-        im.grid(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"])
-        im.image(out=img)
-
-    for _ in range(max(args.warmup, 1)):
-        step()
-    torch.cuda.synchronize()
-    props = torch.cuda.get_device_properties(dev)
-    uuid = str(getattr(props, "uuid", ""))
-    uuid = uuid if uuid.startswith("GPU-") else ("GPU-" + uuid if uuid else "")
-    nvml = Nvml(uuid) if uuid else None
-    clocks = ClockSampler(uuid if uuid else 0)
-    im.set_timing(True)
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    clocks.start()
-    j0 = nvml.energy_mj() if nvml else None
-    s0.record()
-    for _ in range(args.steps):
-        step()
-    s1.record()
-    torch.cuda.synchronize()
-    j1 = nvml.energy_mj() if nvml else None
-    clk = clocks.stop()
-    ms = s0.elapsed_time(s1) / max(args.steps, 1)
-    tm = im.timing()
-    st = im.stats()
-    im.close()
-    peak, peak_kind = _peaks()
-    steps = max(args.steps, 1)
-    groups = -(-nw // max(st["plane_group"], 1))
-    cells = float(nw) * n * n
-    grid_ms = tm["grid_ms"] / steps
-    grid_bytes = 16.0 * st["n_gridded"] + 8.0 * cells
-    phases = {
-        # every plane group sorts all measurements again: two passes of 24 B each
-        "prep": (tm["prep_ms"] / steps, groups * 2 * 24.0 * m + 16.0 * st["n_entries"]),
-        "grid": (grid_ms, grid_bytes),
-        "fft_cufft": (tm["fft_ms"] / steps, 2 * 2 * 8.0 * cells),
-        "stack": (tm["stack_ms"] / steps, 8.0 * cells + 2 * 8.0 * n * n * groups),
-    }
-    ph = {k: {"ms": t, "algorithmic_gb": b / 1e9, "gbs": b / t / 1e6, "frac_of_" + peak_kind: b / t / 1e6 / peak}
-          for k, (t, b) in phases.items() if t > 0}
-    print(json.dumps({
-        "metric": "visibilities/sec end-to-end (grid+FFT+w-stack), 16384^2 x 128 planes, uniform weighting",
-        "value": m / (ms / 1e3), "unit": "vis/s", "higher_is_better": True, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "dtype": "f32",
-        "data": "synthetic: seeded Earth-rotation synthesis (512 antennas, 60 km, 8 h, dec -45, 1.4 GHz), "
-                "N(0,1) visibilities + a unit source at the phase centre",
-        "config": {"workload": "16384x16384 grid, 128 w-planes in groups, 2e8 visibilities, 5 degree field, "
-                               "Kaiser-Bessel support 8, uniform weighting, FP32",
-                   "n": n, "nw": nw, "nvis": m, "support": params["support"], "tile": st["tile"],
-                   "plane_group": st["plane_group"], "plane_groups": groups,
-                   "l2": "inputs larger than L2 (%.0f GB of planes per step)" % (8.0 * cells / 1e9)},
-        "roofline": {"kernel": "k_grid (gridding, Eq. 3)", "bound": "hbm", "achieved": grid_bytes / grid_ms / 1e6,
-                     "peak": peak, "unit": "GB/s", "frac": grid_bytes / grid_ms / 1e6 / peak, "traffic": None,
-                     "peak_kind": peak_kind, "algorithmic_bytes_per_step": grid_bytes, "grid_ms_per_step": grid_ms},
-        "phases": ph,
-        "roofline_frac_end_to_end": sum(b for _, b in phases.values()) / (ms / 1e3) / 1e9 / peak,
-        "energy_j_per_solution": (j1 - j0) / 1e3 / steps if j0 is not None and j1 is not None else None,
-        "gpu_launches": int(tm["kernel_launches"]), "clocks": clk}))
 
 
 def run_small(args, rank, world):
@@ -724,33 +823,68 @@ def run_small(args, rank, world):
 
 
 def run_reference(args, rank, world):
-    """The FP64 oracle on the host cores: every step images a bounded sample
-    (one w-plane of the full workload), extrapolated to the whole workload."""
+    """The FP64 oracle on the host cores, on the same workload as the GPU arm:
+    every step is one bounded sample (oracle_round: placement and gridding of
+    a slice of the measurements, one plane's transform and screen), and the
+    value is the whole image's rate from the median step's unit costs
+    (oracle_image_seconds).  ms_per_step is the measured time of a sample
+    step.  Rank 0 only; the other ranks exit without work."""
     if rank != 0:
         return
+    wl = args.workload
+    if wl not in WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle baseline covers the single-image "
+                                                               "workloads (large, wstack) only"}))
+        return
+    import numpy as np
+
     import synth
     import oracle
     oracle.lib()
-    prob = synth.to_numpy(synth.config2(device="cpu", m=args.nvis))
-    vals = []
-    t_all = 0.0
-    desc = ""
-    threads = oracle.num_threads()
+    prob, params = make_problem(wl, "cpu", args.nvis or None, args.nw or None)
+    prob_np = synth.to_numpy(prob)
+    del prob
+    prob_np["params"] = dict(params)
+    q = prob_np["params"]
+    m = prob_np["u"].shape[0]
+    k, _, _ = oracle.place(q, prob_np["u"], prob_np["v"], prob_np["w"])
+    ok = (k >= 0) & np.isfinite(prob_np["wt"]) & np.isfinite(prob_np["vis"].real) & \
+        np.isfinite(prob_np["vis"].imag)
+    m_gridded = int(ok.sum())
+    nw = int(q["nw"])
+    ms_sample = min(m, ORACLE_SLICE)
+    cnt = np.bincount(k[:ms_sample][k[:ms_sample] >= 0], minlength=nw)
+    plane = int(np.argmin(np.abs(cnt - cnt.mean())))
+    secs, walls, rounds = [], [], []
     for i in range(args.warmup + args.steps):
-        v, desc, threads, secs = oracle_sample(prob, (16, 17))
+        r = oracle_round(prob_np, plane)
         if i >= args.warmup:
-            vals.append(v)
-            t_all += secs
-    value = statistics.median(vals) if vals else None
-    m = prob["u"].shape[0]
+            rounds.append(r)
+            secs.append(oracle_image_seconds(r, m, m_gridded, nw))
+            walls.append(r["wall"])
+    med = statistics.median(secs) if secs else None
+    value = m / med if med else None
+    threads = oracle.num_threads()
+    r = rounds[secs.index(med)] if med in secs else (rounds[0] if rounds else None)
+    desc = ("per step: weights + placement of %d measurements (1 thread), gridding of plane %d's %d of them "
+            "(1 thread), one plane's zeroing + FFT + screen at %d^2 (%d threads%s); value from the median step's "
+            "unit costs: image = %d weight pass(es) + %d x (placement pass of %d + plane) + gridding of %d + "
+            "finalisation (estimates %s s)" % (
+                r["slice"], plane, r["on_plane"], r["n_s"], threads,
+                (", x%.1f for %d^2 by n^2 log n^2" % (r["fft_scale"], q["n"])) if r["n_s"] != q["n"] else "",
+                r["passes_w"], nw, m, m_gridded, ", ".join("%.0f" % x for x in secs))) if r else ""
+    ms_step = statistics.mean(walls) * 1e3 if walls else None
     out = {
         "metric": METRIC, "value": value, "unit": "vis/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": (m / value * 1e3) if value else None, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": DATA, "impl": "reference",
-        "config": {"workload": WORKLOAD, "n": prob["params"]["n"], "nw": prob["params"]["nw"], "nvis": m},
-        "cpu_baseline": {"value": value, "unit": "vis/s", "cores": threads, "kind": "oracle", "sample": desc},
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": DATA[wl], "impl": "reference",
+        "config": workload_config(wl, params, m, world, args),
+        "cpu_baseline": {"value": value, "unit": "vis/s", "cores": threads, "kind": "oracle", "sample": desc,
+                         "threads_by_phase": {"placement_and_gridding": 1, "fft_and_screen": threads},
+                         "image_seconds_estimate": med},
         "e2e": {"value": value, "unit": "vis/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    del np
     print(json.dumps(out))
 
 

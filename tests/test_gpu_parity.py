@@ -391,11 +391,21 @@ def config2_gpu():
     return synth.config2(device="cuda")
 
 
+def _lattice(n, side, extra=()):
+    """side x side pixels spanning the image edge to edge, plus extras."""
+    xs = np.unique(np.linspace(0, n - 1, side).round().astype(np.int64))
+    pix = {(int(x), int(y)) for y in xs for x in xs} | {tuple(int(t) for t in e) for e in extra}
+    return np.array(sorted(pix), np.int32)
+
+
 def test_config2_full_size_sampled(rick, oracle_mod, config2_gpu):
     """4096^2, 32 planes, 1e7 Earth-rotation visibilities, KB support 7: in the
-    bench's launch configuration (automatic tile and plane group), sampled
-    pixels against the oracle's per-pixel evaluation, and the gridded-sum
-    invariant over all planes."""
+    bench's launch configuration (automatic tile and plane group), a 16 x 16
+    pixel lattice spanning the image edge to edge (plus the phase centre and
+    the brightest pixel) against the oracle's per-pixel evaluation, before
+    the taper division (the grid-corrected image times c(x) c(y)) and from an
+    imager without grid correction; and the gridded-sum invariant over all
+    planes."""
     prob = config2_gpu
     params = dict(prob["params"], flags=CORRECT | REAL)
     im = rick.Imager(params)
@@ -403,25 +413,20 @@ def test_config2_full_size_sampled(rick, oracle_mod, config2_gpu):
     img = im.image()
     st = im.stats()
     n = params["n"]
-    peak_gpu = img.abs().max().item()
     flat = int(torch.argmax(img.abs()).item())
-    rng = np.random.default_rng(17)
-    pix = [(flat % n, flat // n), (n // 2, n // 2), (0, 0), (n - 1, n - 1), (n // 2 + 7, n // 3)]
-    pix += [tuple(rng.integers(n // 4, 3 * n // 4, 2)) for _ in range(5)]
+    pix = _lattice(n, 16, [(flat % n, flat // n), (n // 2, n // 2)])
+    assert pix.shape[0] >= 256
     p = synth.to_numpy(prob)
-    ref = oracle_mod.image_at(params, p["u"], p["v"], p["w"], p["wt"], p["vis"], np.array(pix, np.int32),
-                              flags=CORRECT)
-    got = img.cpu().numpy()[[y for (_, y) in pix], [x for (x, _) in pix]]
-    # corners are divided by the taper twice over; compare them before the division too
+    ref0 = oracle_mod.image_at(params, p["u"], p["v"], p["w"], p["wt"], p["vis"], pix, flags=0).real
+    c = oracle_mod.taper(n, synth.KERNEL_KB, 7, 0.0)
+    got = img.cpu().numpy()[pix[:, 1], pix[:, 0]] * c[pix[:, 0]] * c[pix[:, 1]]
+    peak0 = np.max(np.abs(ref0))
+    assert np.max(np.abs(got - ref0)) <= TOL * peak0
     uncorrected = rick.Imager(dict(prob["params"], flags=REAL))
     uncorrected.grid(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"])
     img0 = uncorrected.image()
-    ref0 = oracle_mod.image_at(params, p["u"], p["v"], p["w"], p["wt"], p["vis"], np.array(pix, np.int32), flags=0)
-    got0 = img0.cpu().numpy()[[y for (_, y) in pix], [x for (x, _) in pix]]
-    peak0 = img0.abs().max().item()
-    assert np.max(np.abs(got0 - ref0.real)) <= TOL * peak0
-    central = [i for i, (x, y) in enumerate(pix) if n // 4 <= x < 3 * n // 4 and n // 4 <= y < 3 * n // 4]
-    assert np.max(np.abs(got[central] - ref[central].real)) <= TOL * peak_gpu
+    got0 = img0.cpu().numpy()[pix[:, 1], pix[:, 0]]
+    assert np.max(np.abs(got0 - ref0)) <= TOL * peak0
     assert st["n_dropped"] == 0 and st["n_gridded"] == prob["u"].numel()
     # Eq. 3 keeps the weighted visibility sum: over all planes
     tot = 0.0

@@ -1,8 +1,9 @@
 """The 16384^2 / 128 w-plane / 2e8 measurement configuration with uniform
 weighting on the GPU, in the plane-group launch configuration the library
 picks for it (the planes do not all fit at once): sampled pixels against the
-FP64 oracle's per-pixel evaluation (1e-4 of the image peak, before and after
-grid correction), no drops, and the uniform-weighting weight sum equal to
+FP64 oracle's per-pixel evaluation at a 16 x 16 pixel lattice spanning the
+image edge to edge (1e-4 of the image peak, compared before the taper
+division), no drops, and the uniform-weighting weight sum equal to
 the number of occupied cells."""
 import numpy as np
 import pytest
@@ -30,7 +31,7 @@ def test_config3_plane_groups_uniform_weighting(rick, oracle_mod):
     prob = synth.config3(device="cuda")
     q = prob["params"]
     n = q["n"]
-    im = rick.Imager(dict(q, flags=REAL | UNIFORM))
+    im = rick.Imager(dict(q, flags=CORRECT | REAL | UNIFORM))
     im.grid(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"])
     img = im.image()
     torch.cuda.synchronize()
@@ -47,17 +48,20 @@ def test_config3_plane_groups_uniform_weighting(rick, oracle_mod):
     assert abs(st["sum_weights"] - occupied) <= 1e-5 * occupied
     del cu, cv
     flat = int(torch.argmax(img.abs()).item())
-    rng = np.random.default_rng(23)
-    pix = [(flat % n, flat // n), (n // 2, n // 2), (n // 2 + 1234, n // 2 - 777)]
-    pix += [tuple(rng.integers(n // 4, 3 * n // 4, 2)) for _ in range(2)]
-    pix = np.array(pix, np.int32)
+    xs = np.unique(np.linspace(0, n - 1, 16).round().astype(np.int64))
+    pix = {(int(x), int(y)) for y in xs for x in xs} | {(flat % n, flat // n), (n // 2, n // 2),
+                                                       (n // 2 + 1234, n // 2 - 777)}
+    pix = np.array(sorted(pix), np.int32)
+    assert pix.shape[0] >= 256
     got = img.cpu().numpy()[pix[:, 1], pix[:, 0]]
-    peak = img.abs().max().item()
     del img
     p = synth.to_numpy(prob)
     del prob
-    ref = oracle_mod.image_at(dict(q), p["u"], p["v"], p["w"], p["wt"], p["vis"], pix, flags=UNIFORM)
-    assert np.max(np.abs(got - ref.real)) <= 1e-4 * peak, (got, ref.real, peak)
+    # the oracle before the taper division; the GPU image times c(x) c(y)
+    ref = oracle_mod.image_at(dict(q), p["u"], p["v"], p["w"], p["wt"], p["vis"], pix, flags=UNIFORM).real
+    c = oracle_mod.taper(n, synth.KERNEL_KB, q["support"], 0.0)
+    got = got * c[pix[:, 0]] * c[pix[:, 1]]
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref)), (np.max(np.abs(got - ref)), np.max(np.abs(ref)))
 
 
 def test_maximum_grid_side(rick, oracle_mod):

@@ -187,39 +187,40 @@ ORACLE_SLICE = 2_000_000    # measurements of the placement and gridding sample
 ORACLE_MAX_FFT_N = 4096     # largest plane the FFT sample transforms
 
 
-def oracle_round(prob_np, plane):
+def oracle_round(prob_np, plane, on_plane_idx):
     """One bounded sample of the FP64 oracle on the host cores, the same
     workload, each piece through the oracle's own entry points.  The oracle's
     dirty image (oracle_dirty_image) computes the effective weights once (one
     placement pass, two with uniform weighting), then for every plane places
     all measurements again, grids those on the plane (taps + S^2 updates),
     zeroes, transforms (FP64 FFT) and screens the plane, and finalises once.
-    Measured here:
+    Measured here (the unit costs do not depend on the weights, so the
+    samples run without uniform weighting and its n^2 density array):
       t_pass  oracle.grid(slice, no plane): weights + one placement pass of a
-              slice of the measurements (1 thread)
+              slice of the measurements (two passes, 1 thread)
       t_zero  oracle.grid(no measurement, one plane): zeroing of one plane
-      t_grid  oracle.grid(slice, plane): the same + the gridding of the
-              slice's measurements on that plane (1 thread)
+      t_k0    oracle.grid(measurements on the plane, no plane)
+      t_k     oracle.grid(measurements on the plane, the plane): t_k0 + t_zero
+              + their gridding (1 thread)
       t_plane oracle.dirty_image(one measurement, plane) minus the same with
               no plane, at n or at 4096 for larger n: one plane's zeroing,
               FFT and screen (OpenMP)
-      t_fin   oracle.dirty_image(one measurement, no plane): the weights of
-              one measurement and the finalisation of n^2 pixels (OpenMP)
+      t_fin   oracle.dirty_image(one measurement, no plane): the
+              finalisation of n^2 pixels (OpenMP)
     Returns the unit costs and the wall time of the round."""
-    import numpy as np
-
     import oracle
     p = prob_np
     q = p["params"]
-    n, nw = int(q["n"]), int(q["nw"])
+    q0 = dict(q, flags=int(q.get("flags", 0)) & ~8)
+    n = int(q["n"])
     uniform = bool(int(q.get("flags", 0)) & 8)
     m_all = p["u"].shape[0]
     ms = min(m_all, ORACLE_SLICE)
-    sl = {k: p[k][:ms] for k in ("u", "v", "w", "wt", "vis")}
-    one = {k: p[k][:1] for k in ("u", "v", "w", "wt", "vis")}
-    none = {k: p[k][:0] for k in ("u", "v", "w", "wt", "vis")}
-    kk, _, _ = oracle.place(q, sl["u"], sl["v"], sl["w"])
-    on_plane = int((kk == plane).sum())
+    keys = ("u", "v", "w", "wt", "vis")
+    sl = {k: p[k][:ms] for k in keys}
+    on = {k: p[k][on_plane_idx] for k in keys}
+    one = {k: p[k][:1] for k in keys}
+    none = {k: p[k][:0] for k in keys}
     t_round = time.perf_counter()
 
     def timed(fn, *a, **kw):
@@ -228,23 +229,21 @@ def oracle_round(prob_np, plane):
         return time.perf_counter() - t0
 
     args = lambda d: (d["u"], d["v"], d["w"], d["wt"], d["vis"])  # noqa: E731
-    t_pass = timed(oracle.grid, q, *args(sl), k0=0, k1=0)
-    t_zero = timed(oracle.grid, q, *args(none), k0=plane, k1=plane + 1)
-    t_grid = timed(oracle.grid, q, *args(sl), k0=plane, k1=plane + 1)
+    t_pass = timed(oracle.grid, q0, *args(sl), k0=0, k1=0)
+    t_zero = timed(oracle.grid, q0, *args(none), k0=plane, k1=plane + 1)
+    t_k0 = timed(oracle.grid, q0, *args(on), k0=0, k1=0)
+    t_k = timed(oracle.grid, q0, *args(on), k0=plane, k1=plane + 1)
     n_s = min(n, ORACLE_MAX_FFT_N)
-    qs = dict(q, n=n_s)
+    qs = dict(q0, n=n_s)
     t_fin_s = timed(oracle.dirty_image, qs, *args(one), k0=0, k1=0)
     t_pl_s = timed(oracle.dirty_image, qs, *args(one), k0=plane, k1=plane + 1) - t_fin_s
     # an FFT of n^2 points costs ~ n^2 log n^2; the screen and finalisation ~ n^2
     fft_scale = (n / n_s) ** 2 * math.log2(float(n) * n) / math.log2(float(n_s) * n_s)
-    passes = 3 if uniform else 2  # placement passes in t_pass: weights (1 or 2) + the grid call's own
-    c_place = t_pass / (ms * passes)
-    c_grid = max(t_grid - t_pass - t_zero, 0.0) / max(on_plane, 1)
-    del np
-    return {"c_place": c_place, "c_grid": c_grid, "t_plane": max(t_pl_s, 0.0) * fft_scale,
-            "t_fin": t_fin_s * (n / n_s) ** 2, "n_s": n_s, "fft_scale": fft_scale, "slice": ms,
-            "on_plane": on_plane, "plane": plane, "wall": time.perf_counter() - t_round,
-            "passes_w": passes - 1}
+    m_on = int(on_plane_idx.shape[0])
+    return {"c_place": t_pass / (2 * ms), "c_grid": max(t_k - t_k0 - t_zero, 0.0) / max(m_on, 1),
+            "t_plane": max(t_pl_s, 0.0) * fft_scale, "t_fin": t_fin_s * (n / n_s) ** 2, "n_s": n_s,
+            "fft_scale": fft_scale, "slice": ms, "on_plane": m_on, "plane": plane,
+            "wall": time.perf_counter() - t_round, "passes_w": 2 if uniform else 1}
 
 
 def oracle_image_seconds(r, m_all, m_gridded, nw):
@@ -254,6 +253,26 @@ def oracle_image_seconds(r, m_all, m_gridded, nw):
     the finalisation."""
     return (r["passes_w"] * m_all * r["c_place"] + nw * (m_all * r["c_place"] + r["t_plane"]) +
             m_gridded * r["c_grid"] + r["t_fin"])
+
+
+def oracle_plane_sample(prob_np):
+    """The sampled plane (the one holding the mean number of the first
+    ORACLE_SLICE measurements) and the indices of the measurements on it among
+    the first 10 x ORACLE_SLICE."""
+    import numpy as np
+
+    import oracle
+    p = prob_np
+    q = p["params"]
+    nw = int(q["nw"])
+    m_all = p["u"].shape[0]
+    mm = min(m_all, 10 * ORACLE_SLICE)
+    kk, _, _ = oracle.place(q, p["u"][:mm], p["v"][:mm], p["w"][:mm])
+    cnt = np.bincount(kk[:ORACLE_SLICE][kk[:ORACLE_SLICE] >= 0], minlength=nw)
+    plane = int(np.argmin(np.abs(cnt - cnt.mean())))
+    idx = np.nonzero(kk == plane)[0]
+    del np
+    return plane, idx
 
 
 def oracle_sample(prob_np, m_gridded, rounds=3):
@@ -267,12 +286,9 @@ def oracle_sample(prob_np, m_gridded, rounds=3):
     q = p["params"]
     n, nw = int(q["n"]), int(q["nw"])
     m_all = p["u"].shape[0]
-    ms = min(m_all, ORACLE_SLICE)
-    kk, _, _ = oracle.place(q, p["u"][:ms], p["v"][:ms], p["w"][:ms])
-    cnt = np.bincount(kk[kk >= 0], minlength=nw)
-    plane = int(np.argmin(np.abs(cnt - cnt.mean())))  # the plane closest to the mean count
+    plane, idx = oracle_plane_sample(p)
     t0 = time.perf_counter()
-    rs = [oracle_round(p, plane) for _ in range(max(rounds, 1))]
+    rs = [oracle_round(p, plane, idx) for _ in range(max(rounds, 1))]
     wall = time.perf_counter() - t0
     secs = [oracle_image_seconds(r, m_all, m_gridded, nw) for r in rs]
     med = statistics.median(secs)
@@ -280,8 +296,9 @@ def oracle_sample(prob_np, m_gridded, rounds=3):
     threads = oracle.num_threads()
     desc = (f"median of {len(rs)} rounds (image estimates {', '.join('%.0f' % x for x in secs)} s); per round: "
             f"weights + placement of {r['slice']} measurements ({r['c_place'] * 1e9:.0f} ns per measurement "
-            f"and pass, 1 thread), gridding of plane {plane}'s {r['on_plane']} of them ({r['c_grid'] * 1e6:.2f} "
-            f"us per measurement, 1 thread), one plane's zeroing + FFT + screen at {r['n_s']}^2 "
+            f"and pass, 1 thread), gridding of {r['on_plane']} measurements on plane {plane} "
+            f"({r['c_grid'] * 1e6:.2f} us per measurement, 1 thread), one plane's zeroing + FFT + screen at "
+            f"{r['n_s']}^2 "
             f"({r['t_plane'] / r['fft_scale']:.2f} s, {threads} threads"
             + (f", x{r['fft_scale']:.1f} for {n}^2 by n^2 log n^2" if r['n_s'] != n else "") +
             f"); image = {r['passes_w']} weight pass(es) + {nw} x (placement pass of {m_all} + plane) + "
@@ -357,6 +374,8 @@ def main():
     ap.add_argument("--w-support", type=int, default=0,
                     help="planes per measurement (Eq. 3's kernel in w); the plane range is padded by "
                          "nw / (nw - w_support) so every footprint lies on the planes")
+    ap.add_argument("--fft2d", action="store_true",
+                    help="cuFFT's 2D plan + a separate stack pass (RICK_FFT_2D) instead of the split transform")
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the FP64 oracle (CPU baseline and parity of the timed image)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
@@ -422,6 +441,8 @@ def run_image(args, rank, world):
     wl = args.workload
     prob, params = make_problem(wl, dev, args.nvis or None, args.nw or None)
     params["tile"] = args.tile
+    if args.fft2d:
+        params["flags"] = params["flags"] | rick.FFT_2D
     if args.fold:
         wabs = max(abs(params["w_min"]), abs(params["w_max"]))
         params = dict(params, nw=max(params["nw"] // 2, 1), w_min=0.0, w_max=wabs,
@@ -487,16 +508,21 @@ def run_image(args, rank, world):
     grid_bytes = 24.0 * st["n_gridded"] + 8.0 * cells
     stack_ms = tm["stack_ms"] / steps
     stack_bytes = 8.0 * cells + 4.0 * n * n + (2 * 8.0 * n * n * (groups - 1) if groups > 1 else 0.0)
+    split = tm["colfft_calls"] > 0  # the split transform: cuFFT rows, k_colfft, k_colstack
     fft_ms = tm["fft_ms"] / steps
-    fft_bytes = 2 * 2 * 8.0 * cells
+    fft_bytes = (1 if split else 2) * 2 * 8.0 * cells  # one read + write pass per dimension
+    colfft_ms = tm["colfft_ms"] / steps
+    colfft_bytes = 2 * 8.0 * cells if split else 0.0
     prep_ms = tm["prep_ms"] / steps
     prep_bytes = (3 if uniform else 2) * 24.0 * m + 16.0 * st["n_entries"]
     phases = {
         "prep": {"ms": prep_ms, "algorithmic_gb": prep_bytes / 1e9},
         "grid": {"ms": grid_ms, "algorithmic_gb": grid_bytes / 1e9},
-        "fft_cufft": {"ms": fft_ms, "algorithmic_gb": fft_bytes / 1e9},
+        ("fft_cufft_rows" if split else "fft_cufft"): {"ms": fft_ms, "algorithmic_gb": fft_bytes / 1e9},
         "stack": {"ms": stack_ms, "algorithmic_gb": stack_bytes / 1e9},
     }
+    if split:
+        phases["colfft"] = {"ms": colfft_ms, "algorithmic_gb": colfft_bytes / 1e9}
     for v in phases.values():
         v["gbs"] = v["algorithmic_gb"] / v["ms"] * 1e3 if v["ms"] > 0 else None
         v["frac_of_" + peak_kind] = v["gbs"] / peak if v["gbs"] else None
@@ -504,7 +530,6 @@ def run_image(args, rank, world):
     default_size = wl == "wstack" and (n, nw, m) == (4096, 32, 10_000_000) and \
         params.get("w_support", 1) <= 1 and not params["flags"] & synth.FLAG_FOLD
     traffic = _traffic("rick_grid.cu", "k_grid@4096x32x1e7") if default_size else None
-    split = n == 4096  # the library's default transform path at this size (cuFFT + k_colstack)
     stack_name = ("k_colstack (last 16-point column factor + w-screen + stack, Eq. 1)" if split
                   else "k_stack (w-screen + stack, Eq. 1)")
     stack_traffic = _traffic("rick_stack.cu", "k_colstack@4096x32x1e7") if (default_size and split) else None
@@ -519,7 +544,17 @@ def run_image(args, rank, world):
                 "unit": "GB/s", "frac": stack_bytes / stack_ms / 1e6 / peak, "traffic": stack_traffic,
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": stack_bytes / launches_stack,
                 "launch_ms": stack_ms / launches_stack, "launches_per_step": launches_stack}
-    rl, rl_other = (rl_stack, rl_grid) if stack_ms > grid_ms else (rl_grid, rl_stack)
+    own = [(grid_ms, rl_grid), (stack_ms, rl_stack)]
+    if split:
+        launches_cf = max(tm["colfft_calls"] / steps, 1)
+        own.append((colfft_ms, {
+            "kernel": "k_colfft (first n/16-point column factor of the plane transform, TMA-fed)", "bound": "hbm",
+            "achieved": colfft_bytes / colfft_ms / 1e6, "peak": peak, "unit": "GB/s",
+            "frac": colfft_bytes / colfft_ms / 1e6 / peak, "traffic": None, "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": colfft_bytes / launches_cf, "launch_ms": colfft_ms / launches_cf,
+            "launches_per_step": launches_cf}))
+    own.sort(key=lambda t: -t[0])
+    rl, rl_other = own[0][1], [o[1] for o in own[1:]]
 
     # ------------------------------------------------ end to end, host buffers
     e2e = None
@@ -550,7 +585,9 @@ def run_image(args, rank, world):
                "h2d_bytes_per_step": int(m * (8 + 4 + 4 + 4 + 4)), "d2h_bytes_per_step": int(n * n * 4),
                "api": "rick_image_host_async over %d images, then rick_synchronize (pinned host buffers)" % ksteps,
                "unpipelined_ms_per_step": te_sync * 1e3}
-        del hv, hu, hvv, hw, hwt
+        del hv, hu, hvv, hw, hwt, himg, himg2
+        if hasattr(torch._C, "_host_emptyCache"):
+            torch._C._host_emptyCache()  # return the pinned staging memory before the CPU leg
 
     # ------------------------------------------------ FP64 oracle: CPU baseline and parity
     cpu = parity = None
@@ -573,7 +610,7 @@ def run_image(args, rank, world):
 
     config = workload_config(wl, params, m, world, args)
     # whole step against HBM: prep + gridder + FFT (2 passes) + stack
-    step_bytes = prep_bytes + grid_bytes + fft_bytes + stack_bytes
+    step_bytes = prep_bytes + grid_bytes + fft_bytes + colfft_bytes + stack_bytes
     out = {
         "metric": METRIC, "value": value, "unit": "vis/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -852,12 +889,10 @@ def run_reference(args, rank, world):
         np.isfinite(prob_np["vis"].imag)
     m_gridded = int(ok.sum())
     nw = int(q["nw"])
-    ms_sample = min(m, ORACLE_SLICE)
-    cnt = np.bincount(k[:ms_sample][k[:ms_sample] >= 0], minlength=nw)
-    plane = int(np.argmin(np.abs(cnt - cnt.mean())))
+    plane, idx = oracle_plane_sample(prob_np)
     secs, walls, rounds = [], [], []
     for i in range(args.warmup + args.steps):
-        r = oracle_round(prob_np, plane)
+        r = oracle_round(prob_np, plane, idx)
         if i >= args.warmup:
             rounds.append(r)
             secs.append(oracle_image_seconds(r, m, m_gridded, nw))
@@ -866,11 +901,11 @@ def run_reference(args, rank, world):
     value = m / med if med else None
     threads = oracle.num_threads()
     r = rounds[secs.index(med)] if med in secs else (rounds[0] if rounds else None)
-    desc = ("per step: weights + placement of %d measurements (1 thread), gridding of plane %d's %d of them "
-            "(1 thread), one plane's zeroing + FFT + screen at %d^2 (%d threads%s); value from the median step's "
-            "unit costs: image = %d weight pass(es) + %d x (placement pass of %d + plane) + gridding of %d + "
+    desc = ("per step: weights + placement of %d measurements (1 thread), gridding of the %d measurements on "
+            "plane %d (1 thread), one plane's zeroing + FFT + screen at %d^2 (%d threads%s); value from the median "
+            "step's unit costs: image = %d weight pass(es) + %d x (placement pass of %d + plane) + gridding of %d + "
             "finalisation (estimates %s s)" % (
-                r["slice"], plane, r["on_plane"], r["n_s"], threads,
+                r["slice"], r["on_plane"], plane, r["n_s"], threads,
                 (", x%.1f for %d^2 by n^2 log n^2" % (r["fft_scale"], q["n"])) if r["n_s"] != q["n"] else "",
                 r["passes_w"], nw, m, m_gridded, ", ".join("%.0f" % x for x in secs))) if r else ""
     ms_step = statistics.mean(walls) * 1e3 if walls else None

@@ -66,10 +66,10 @@ typedef int32_t rick_status;
 #define RICK_FFT_2D 64u         /* transform the planes with cuFFT's 2D plan and stack them in a
                                   separate pass, also where the library would otherwise split
                                   the column transform and fuse its last factor with the
-                                  w-screen and the stack (single images with n = 4096) */
-#define RICK_FFT_SPLIT 128u     /* the split transform for any power-of-two n in [64, 4096]
-                                  (single images; slower than the 2D plan below 4096, for tests
-                                  and measurement).  Not with RICK_FFT_2D.  Either way the
+                                  w-screen and the stack (single images with n >= 4096) */
+#define RICK_FFT_SPLIT 128u     /* the split transform for any power-of-two n in [64, 16384]
+                                  (single images; the default from n = 4096 on, for tests and
+                                  measurement below).  Not with RICK_FFT_2D.  Either way the
                                   result is the same up to rounding */
 
 /* Problem statement of Sec. 2.1: grid size, pixel scale, w-planes, kernel.
@@ -158,11 +158,14 @@ rick_status rick_add_density(rick_handle h, const float* vis, const float* u, co
  * (cuFFT, unnormalised, exponent +), multiply by the phase screen
  * exp(+2 pi i w_k (n-1)) and sum over planes (Eq. 1); then divide by the
  * weight sum and, per flags, by the taper and times n.  image: float[n*n]
- * (RICK_REAL_IMAGE) or float[2*n*n] complex, fully overwritten.  At n = 4096
- * (or with RICK_FFT_SPLIT) cuFFT transforms the rows and the first factor of
- * the columns and one kernel does the last 16-point column factor together
- * with the screen and the sum, reading each plane once more; otherwise
- * cuFFT's 2D plan and a separate screen-and-sum pass (RICK_FFT_2D). */
+ * (RICK_REAL_IMAGE) or float[2*n*n] complex, fully overwritten.  For
+ * power-of-two n from 4096 to 16384 (or with RICK_FFT_SPLIT) the column
+ * transform is split, n = 16 * (n / 16): cuFFT transforms the rows, one
+ * library kernel the first (n / 16-point) column factor of every plane of
+ * the group in place, and one kernel the last 16-point column factor
+ * together with the screen and the sum, reading each plane once more;
+ * otherwise cuFFT's 2D plan and a separate screen-and-sum pass
+ * (RICK_FFT_2D). */
 rick_status rick_fft_and_stack(rick_handle h, float* image);
 
 /* Eq. 3 alone: the gridded planes k0 .. k0+nk-1 as complex float
@@ -308,15 +311,19 @@ rick_status rick_get_stats(rick_handle h, rick_stats* out);
 /* Per-phase device time of the library's own work, from CUDA events recorded
  * on the handle's stream around each phase (no synchronisation while timing
  * is on).  Phases: prep = placement + counting sort (rick_grid); grid = the
- * gridding kernel (Eq. 3); fft = cuFFT plane transforms; stack = phase screen
- * + plane reduction + finalisation; degrid = the whole adjoint.  Times are
- * sums over all calls since timing was enabled; *_calls count the phase
- * executions; kernel_launches counts librick's own kernel launches (cuFFT's
- * not included). */
+ * gridding kernel (Eq. 3); fft = cuFFT plane transforms (the rows only when
+ * the column transform is split); colfft = the first column factor of the
+ * split transform (the library's own kernel); stack = phase screen + plane
+ * reduction + finalisation (with the split: the last column factor too);
+ * degrid = the whole adjoint.  Times are sums over all calls since timing
+ * was enabled; *_calls count the phase executions; kernel_launches counts
+ * librick's own kernel launches (cuFFT's not included). */
 typedef struct rick_timing {
     double prep_ms, grid_ms, fft_ms, stack_ms, degrid_ms;
     int64_t prep_calls, grid_calls, fft_calls, stack_calls, degrid_calls;
     int64_t kernel_launches;
+    double colfft_ms;
+    int64_t colfft_calls;
 } rick_timing;
 
 /* Turn phase timing on (enable != 0, resets the sums) or off. */

@@ -44,7 +44,7 @@ class RickTiming(ctypes.Structure):
                 ("stack_ms", ctypes.c_double), ("degrid_ms", ctypes.c_double),
                 ("prep_calls", ctypes.c_int64), ("grid_calls", ctypes.c_int64), ("fft_calls", ctypes.c_int64),
                 ("stack_calls", ctypes.c_int64), ("degrid_calls", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("colfft_ms", ctypes.c_double), ("colfft_calls", ctypes.c_int64)]
 
 
 # exported symbol -> (restype, argtypes); kept in the order of include/rick.h

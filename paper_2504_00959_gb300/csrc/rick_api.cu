@@ -111,7 +111,7 @@ rick_status check_params(const rick_params* p, GridCfg* c, double* kparam, char*
     {
         int n1 = 0, n2 = 0;
         if ((p->flags & RICK_FFT_SPLIT) && !colstack_shape(p->n, &n1, &n2)) {
-            snprintf(msg, msglen, "RICK_FFT_SPLIT needs a power-of-two n in [64, 4096] (got %d)", p->n);
+            snprintf(msg, msglen, "RICK_FFT_SPLIT needs a power-of-two n in [64, 16384] (got %d)", p->n);
             return RICK_ERR_ARG;
         }
     }
@@ -169,10 +169,9 @@ size_t plane_bytes(const rick_params* p) { return (size_t)p->n * p->n * sizeof(f
 // Plans of a handle, one per (kind, batch):
 //   kPlan2D    2D n x n transforms of `batch` planes
 //   kPlanRows  1D n-point transforms of the rows of `batch` planes
-//   kPlanColA  the first column factor of one plane for k_colstack: n1-point
-//              transforms along the column at a stride of n2 rows, for each
-//              of the n2 * n (row in block, column) pairs (batch unused)
-enum { kPlan2D = 0, kPlanRows = 1, kPlanColA = 2 };
+// (the first column factor of the split transform is k_colfft's, the last
+// k_colstack's or k_spreadcol's)
+enum { kPlan2D = 0, kPlanRows = 1 };
 // smallest n for the split column transform without RICK_FFT_SPLIT: measured
 // at 2048^2 x 16 planes it is still 4 % slower than cuFFT's 2D plan + k_stack
 // (the 2D plan keeps more of a 34 MB plane in L2, and the first column factor
@@ -207,17 +206,9 @@ rick_status get_plan(rick_handle h, int batch, cufftHandle* out, int kind = kPla
     if (kind == kPlan2D) {
         int dims[2] = {n, n};
         r = cufftMakePlanMany(plan, 2, dims, nullptr, 1, (int)dist, nullptr, 1, (int)dist, CUFFT_C2C, batch, &work);
-    } else if (kind == kPlanRows) {
+    } else {
         int dims[1] = {n};
         r = cufftMakePlanMany(plan, 1, dims, nullptr, 1, n, nullptr, 1, n, CUFFT_C2C, batch * n, &work);
-    } else {
-        int n1 = 0, n2 = 0;
-        if (!colstack_shape(n, &n1, &n2)) {
-            cufftDestroy(plan);
-            return fail(h, RICK_ERR_ARG, "no column split for n=%d", n);
-        }
-        int dims[1] = {n1}, emb[1] = {n1};
-        r = cufftMakePlanMany(plan, 1, dims, emb, n2 * n, 1, emb, n2 * n, 1, CUFFT_C2C, n2 * n, &work);
     }
     if (r != CUFFT_SUCCESS) {
         cufftDestroy(plan);
@@ -310,6 +301,28 @@ rick_status check_vis_args(rick_handle h, const float* vis, const float* u, cons
     if (nvis < 0) return fail(h, RICK_ERR_ARG, "nvis must be >= 0 (got %lld)", (long long)nvis);
     if (nvis > 0 && (!vis || !u || !v || !w)) return fail(h, RICK_ERR_ARG, "vis, u, v, w must not be NULL");
     if (nvis > (int64_t)1 << 30) return fail(h, RICK_ERR_ARG, "at most 2^30 measurements per call");
+    return RICK_OK;
+}
+
+// The twiddle table and tensor map of k_colfft (the first column factor of
+// the split transform), made on first use: exp(+2 pi i j / N1), j < N1, in
+// FP64 rounded once to binary32.
+rick_status colfft_ready(rick_handle h)
+{
+    if (h->cfmap_ready) return RICK_OK;
+    const int n1 = h->p.n / 16;
+    std::vector<float2> tw(n1);
+    for (int j = 0; j < n1; ++j) {
+        const double a = 6.283185307179586476925 * (double)j / (double)n1;
+        tw[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    if (!h->cf_tw) {
+        RICK_CU(h, cudaMalloc((void**)&h->cf_tw, sizeof(float2) * n1));
+        h->bytes_held += sizeof(float2) * n1;
+    }
+    RICK_CU(h, cudaMemcpy(h->cf_tw, tw.data(), sizeof(float2) * n1, cudaMemcpyHostToDevice));
+    RICK_CU(h, encode_colfft_map(h->cfmap, h->planes, h->p.n, h->G));
+    h->cfmap_ready = true;
     return RICK_OK;
 }
 
@@ -644,6 +657,7 @@ rick_status rick_destroy(rick_handle h)
         cudaEventDestroy(ev.second);
     }
     cudaFree(h->taper);
+    cudaFree(h->cf_tw);
     cudaFree(h->planes);
     cudaFree(h->acc);
     cudaFree(h->cursor);
@@ -799,7 +813,6 @@ rick_status rick_fft_and_stack(rick_handle h, float* image)
     // cuFFT's 2D plan and k_stack
     int n1 = 0, n2 = 0;
     const bool split = use_split(p, &n1, &n2);
-    const int64_t nn = (int64_t)p.n * p.n;
     for (int k0 = 0; k0 < p.nw; k0 += h->G) {
         const int nk = (p.nw - k0 < h->G) ? p.nw - k0 : h->G;
         rick_status s = grid_pass(h, k0, nk, true, h->planes);
@@ -810,14 +823,18 @@ rick_status rick_fft_and_stack(rick_handle h, float* image)
         a.first = (k0 == 0);
         a.last = (k0 + nk >= p.nw);
         if (split) {
-            cufftHandle rows, cola;
+            cufftHandle rows;
             if ((s = get_plan(h, nk, &rows, kPlanRows))) return s;
-            if ((s = get_plan(h, 1, &cola, kPlanColA))) return s;
+            if ((s = colfft_ready(h))) return s;
             {
                 PhaseScope fs(h, kPhaseFft);
                 RICK_FFT(h, cufftExecC2C(rows, planes, planes, CUFFT_INVERSE));
-                for (int kl = 0; kl < nk; ++kl)
-                    RICK_FFT(h, cufftExecC2C(cola, planes + kl * nn, planes + kl * nn, CUFFT_INVERSE));
+            }
+            {
+                PhaseScope cs(h, kPhaseColfft);
+                RICK_CU(h, launch_colfft(h->cfmap, h->cf_tw, h->planes, p.n, nk, +1, h->dbg_wait_ns, &h->ctr->err,
+                                         h->stream));
+                count_launches(h, 1);
             }
             if (!h->colmap_ready) {
                 RICK_CU(h, encode_colstack_map(h->colmap, h->planes, p.n, h->G));
@@ -891,7 +908,6 @@ static rick_status degrid_impl(rick_handle h, const GridCfg& c, const double* su
     // k_spread and cuFFT's forward 2D plan
     int n1 = 0, n2 = 0;
     const bool split = use_split(p, &n1, &n2);
-    const int64_t nn = (int64_t)p.n * p.n;
     cufftComplex* planes = reinterpret_cast<cufftComplex*>(h->planes);
     for (int k0 = 0; !st && k0 < p.nw; k0 += h->G) {
         const int nk = (p.nw - k0 < h->G) ? p.nw - k0 : h->G;
@@ -905,12 +921,16 @@ static rick_status degrid_impl(rick_handle h, const GridCfg& c, const double* su
         }
         cufftResult r = CUFFT_SUCCESS;
         if (split) {
-            cufftHandle cola, rows;
-            if ((st = get_plan(h, 1, &cola, kPlanColA))) break;
+            cufftHandle rows;
             if ((st = get_plan(h, nk, &rows, kPlanRows))) break;
-            for (int kl = 0; kl < nk && r == CUFFT_SUCCESS; ++kl)
-                r = cufftExecC2C(cola, planes + kl * nn, planes + kl * nn, CUFFT_FORWARD);
-            if (r == CUFFT_SUCCESS) r = cufftExecC2C(rows, planes, planes, CUFFT_FORWARD);
+            if ((st = colfft_ready(h))) break;
+            e = launch_colfft(h->cfmap, h->cf_tw, h->planes, p.n, nk, -1, h->dbg_wait_ns, &h->ctr->err, h->stream);
+            if (e != cudaSuccess) {
+                st = fail(h, RICK_ERR_CUDA, "k_colfft: %s", cudaGetErrorString(e));
+                break;
+            }
+            count_launches(h, 1);
+            r = cufftExecC2C(rows, planes, planes, CUFFT_FORWARD);
         } else {
             cufftHandle plan;
             if ((st = get_plan(h, nk, &plan))) break;
@@ -1149,6 +1169,8 @@ rick_status rick_get_timing(rick_handle h, rick_timing* out)
     out->stack_calls = h->timer.calls[kPhaseStack];
     out->degrid_calls = h->timer.calls[kPhaseDegrid];
     out->kernel_launches = h->timer.launches;
+    out->colfft_ms = h->timer.ms[kPhaseColfft];
+    out->colfft_calls = h->timer.calls[kPhaseColfft];
     return RICK_OK;
 }
 

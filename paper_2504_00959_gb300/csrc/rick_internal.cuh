@@ -204,7 +204,7 @@ struct ChunkList {
 // Device-resident counters of a handle.
 struct Counters {
     unsigned long long gridded, dropped, entries;
-    unsigned long long err;          // bit 0: a bounded wait of k_colstack ran out
+    unsigned long long err;          // bit 0: a bounded wait of k_colstack ran out; bit 1: of k_colfft
     double sum_w;
 };
 
@@ -270,7 +270,7 @@ __device__ __forceinline__ float wcorr_at(const StackArgs& a, float nm1)
 
 // sum_w: the weight sum the image is normalised by (device)
 // n = n1 * n2 split of the column transform for k_colstack (power-of-two n in
-// [64, 4096]: n2 = 64 from n = 512 on, else 16); false: use cuFFT 2D + k_stack
+// [64, 16384]: n2 = 16, n1 = n / 16); false: use cuFFT 2D + k_stack
 bool colstack_shape(int n, int* n1, int* n2);
 // screen + stack of a group whose rows and first column factor are transformed
 // (cuFFT), the last column factor done here; err: Counters::err
@@ -282,6 +282,13 @@ cudaError_t launch_colstack(const void* map, const StackArgs& a, int n1, int n2,
 // adjoint of launch_colstack: planes of the group from the image gradient
 // (rows 16 f1 + b after the last column factor's adjoint); cuFFT's forward
 // first column factor and rows complete the forward 2D transform
+// the first column factor of the split transform for a group of nk planes
+// (k_colfft, rick_colfft.cu): rows 16 a + b -> rows 16 f1 + b in place, the
+// N1 = n / 16-point DFT with exponent sign (+1 imaging, -1 adjoint); map
+// from encode_colfft_map for the plane buffer, tw = exp(+2 pi i j / N1)
+cudaError_t encode_colfft_map(void* map, const float2* planes, int n, int planes_in_buffer);
+cudaError_t launch_colfft(const void* map, const float2* tw, float2* planes, int n, int nk, int sign,
+                          unsigned long long wait_ns, unsigned long long* err, cudaStream_t s);
 cudaError_t launch_spreadcol(const StackArgs& a, int n1, int n2, const void* rimg, const float* taper,
                              const double* sum_w, float2* planes, cudaStream_t s);
 cudaError_t launch_stack(const StackArgs& a, const float2* planes, float2* acc, const float* taper,
@@ -308,7 +315,7 @@ rick_status validate_params(const rick_params* p, GridCfg* c, double* kparam, ch
 }  // namespace rick
 
 namespace rick {
-enum Phase { kPhasePrep = 0, kPhaseGrid, kPhaseFft, kPhaseStack, kPhaseDegrid, kNumPhases };
+enum Phase { kPhasePrep = 0, kPhaseGrid, kPhaseFft, kPhaseStack, kPhaseDegrid, kPhaseColfft, kNumPhases };
 
 // CUDA-event timer per phase: events are recorded on the stream and only
 // resolved (elapsed time summed) when the caller asks for the totals.
@@ -316,10 +323,10 @@ struct PhaseTimer {
     bool on = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[kNumPhases];
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spare;
-    double ms[kNumPhases] = {0, 0, 0, 0, 0};
-    int64_t calls[kNumPhases] = {0, 0, 0, 0, 0};
+    double ms[kNumPhases] = {};
+    int64_t calls[kNumPhases] = {};
     int64_t launches = 0;
-    cudaEvent_t open_start[kNumPhases] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t open_start[kNumPhases] = {};
 };
 }  // namespace rick
 
@@ -347,6 +354,9 @@ struct rick_imager {
     std::map<int, cufftHandle> plans;// (kind, batch) -> plan
     alignas(64) unsigned char colmap[128];  // tensor map of `planes` for k_colstack
     bool colmap_ready;
+    alignas(64) unsigned char cfmap[128];   // tensor map of `planes` for k_colfft
+    bool cfmap_ready;
+    float2* cf_tw;                   // [n / 16] exp(+2 pi i j / (n / 16)) for k_colfft
     struct Chunk {
         uint32_t* off;
         float4* ent;

@@ -11,6 +11,7 @@
 // even when |w (n - 1)| reaches hundreds of turns; the screen is advanced by a
 // complex rotation per plane and re-evaluated directly every kResync planes.
 #include "rick_internal.cuh"
+#include "rick_tma.cuh"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -276,69 +277,6 @@ constexpr unsigned long long kColWaitNs = 1000000000ull;  // default bound of on
 // planes summed by Horner's rule between direct evaluations of the screen
 // (the rotation per plane is applied in binary32, relative error ~1e-7 each)
 constexpr int kColResync = 32;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-// one 2D tensor copy (TMA) of the box at (x, y) into shared memory,
-// completing its bytes on the mbarrier
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int xc, int yc, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-            "r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(xc), "r"(yc), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// wait for the phase of the given parity to complete; false once limit_ns
-// have passed without it or another warp has given up (*abort set).  The
-// result is per lane: callers make it warp-uniform (__all_sync) before
-// acting on it.
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
-{
-    uint32_t done;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(done)
-                 : "r"(bar), "r"(parity)
-                 : "memory");
-    return done != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort,
-                                          unsigned long long limit_ns)
-{
-    if (mbar_try(bar, parity)) return true;  // the common case: no clock reads
-    const unsigned long long t0 = global_ns();
-    for (;;) {
-        if (mbar_try(bar, parity)) return true;
-        if (*abort || global_ns() - t0 > limit_ns) return false;
-    }
-}
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -693,7 +631,7 @@ cudaError_t launch_spreadcol(const StackArgs& a, int n1, int n2, const void* rim
 
 bool colstack_shape(int n, int* n1, int* n2)
 {
-    if (n < 64 || n > 4096 || (n & (n - 1))) return false;
+    if (n < 64 || n > 16384 || (n & (n - 1))) return false;
     *n2 = kColN2;
     *n1 = n / kColN2;
     return true;

@@ -112,12 +112,12 @@ def test_workspace_size_and_parameter_checks(lib):
 
 def test_transform_path_flags(lib):
     """RICK_FFT_2D and RICK_FFT_SPLIT exclude each other; the split needs a
-    power-of-two n in [64, 4096]."""
+    power-of-two n in [64, 16384]."""
     from paper_2504_00959_gb300 import _lib
     size = ctypes.c_size_t(0)
     for n, flags, ok in ((256, _lib.FFT_2D, True), (256, _lib.FFT_SPLIT, True), (4096, _lib.FFT_SPLIT, True),
                          (256, _lib.FFT_2D | _lib.FFT_SPLIT, False), (34, _lib.FFT_SPLIT, False),
-                         (8192, _lib.FFT_SPLIT, False), (32, _lib.FFT_SPLIT, False), (34, _lib.FFT_2D, True)):
+                         (8192, _lib.FFT_SPLIT, True), (32768, _lib.FFT_SPLIT, False), (32, _lib.FFT_SPLIT, False), (34, _lib.FFT_2D, True)):
         q = _lib.RickParams()
         lib.rick_params_default(ctypes.byref(q))
         q.n, q.flags = n, flags | _lib.REAL_IMAGE

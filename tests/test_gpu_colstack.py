@@ -1,6 +1,7 @@
-"""The split plane transform of single images (the default at n = 4096,
-RICK_FFT_SPLIT for any power-of-two n in [64, 4096]): cuFFT on the rows and
-on the first column factor, then k_colstack for the last 16-point factor
+"""The split plane transform of single images (the default from n = 4096 on,
+RICK_FFT_SPLIT for any power-of-two n in [64, 16384]): cuFFT on the rows,
+k_colfft for the first (n / 16-point) column factor of every plane of the
+group, then k_colstack for the last 16-point factor
 together with the w-screen and the plane sum.  Checked against the FP64
 oracle (1e-4 of the image peak after weighting by the taper, as every image
 comparison) and against cuFFT's 2D plan with the separate stack
@@ -68,6 +69,10 @@ def test_matches_oracle(rick, oracle_mod, flags, extra):
     (4096, 12, 300000, CORRECT | REAL, {"plane_group": 5}),
     (2048, 16, 300000, CORRECT, {"plane_group": 7}),
     (2048, 8, 200000, CORRECT | REAL | APPLY_N, {}),
+    (16384, 4, 400000, CORRECT | REAL, {}),
+    (8192, 6, 300000, CORRECT, {"plane_group": 4}),
+    (256, 6, 20000, CORRECT | REAL, {}),
+    (128, 4, 5000, CORRECT | REAL, {"plane_group": 3}),
 ])
 def test_split_equals_2d_plan(rick, n, nw, m, flags, extra):
     prob = synth.config2(m=m, n=n, nw=nw)
@@ -115,10 +120,12 @@ def test_repeated_images_reuse_the_tensor_map(rick):
         assert (o - outs[0]).abs().max().item() <= 1e-5 * peak
 
 
-def test_default_at_4096_is_the_split(rick):
-    """Without either flag, n = 4096 takes the split transform: the image
-    equals the one RICK_FFT_SPLIT gives, up to the gridder's atomic rounding."""
-    prob = synth.config2(m=300000, n=4096, nw=8)
+@pytest.mark.parametrize("n", [4096, 16384])
+def test_default_from_4096_is_the_split(rick, n):
+    """Without either flag, n = 4096 .. 16384 takes the split transform: the
+    image equals the one RICK_FFT_SPLIT gives, up to the gridder's atomic
+    rounding."""
+    prob = synth.config2(m=300000, n=n, nw=4)
     a, _ = _image(rick, prob, CORRECT | REAL)
     b, _ = _image(rick, prob, CORRECT | REAL | rick.FFT_SPLIT)
     assert np.max(np.abs(a - b)) <= 1e-5 * np.max(np.abs(b))
@@ -168,6 +175,8 @@ def test_degrid_matches_oracle(rick, oracle_mod, flags, extra):
 @pytest.mark.parametrize("n,nw,flags,extra", [
     (4096, 16, CORRECT | REAL, {}),
     (2048, 12, CORRECT, {"plane_group": 5}),
+    (16384, 3, CORRECT | REAL, {}),
+    (512, 6, CORRECT | REAL, {"plane_group": 4}),
 ])
 def test_degrid_split_equals_2d_plan(rick, n, nw, flags, extra):
     prob = synth.config2(m=300000, n=n, nw=nw)

@@ -91,3 +91,72 @@ def test_the_two_splits_are_adjoint():
     lhs = np.vdot(r, forward_split(x, n1))
     rhs = np.vdot(adjoint_split(r, n1), x)
     assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
+
+
+# -------------------------------------------------------------------------
+# The first column factor as k_colfft computes it in shared memory: the
+# N1-point DFT of the rows 16 a + b of one column, N1 = 16 Q, through its
+# passes and in-block positions, written out with the kernel's thread roles.
+
+def _dft(v, sign):
+    k = np.arange(v.size)
+    return np.exp(sign * 2j * np.pi * np.outer(k, k) / v.size) @ v
+
+
+def colfft_block(x, sign):
+    """x: the N1 samples x[16 a + b] of one (b, column), a = 0 .. N1-1.
+    Returns Y indexed by f1 (what the kernel stores at row 16 f1 + b)."""
+    n1 = x.size
+    tw = np.exp(sign * 2j * np.pi * np.arange(n1) / n1)  # w_N1^e with the kernel's sign
+    buf = x.astype(complex).copy()                       # shared memory, position a
+    out = np.empty(n1, complex)
+    if n1 < 16:                                          # one pass
+        return _dft(buf, sign)
+    q = n1 // 16
+    for a2 in range(q):                                  # pass A: thread (x, a2)
+        v = _dft(buf[[q * a1 + a2 for a1 in range(16)]], sign)
+        for k1 in range(16):
+            buf[q * k1 + a2] = v[k1] * tw[a2 * k1]
+    if q <= 16:                                          # pass B: thread (x, k1)
+        for k1 in range(16):
+            v = _dft(buf[[q * k1 + a2 for a2 in range(q)]], sign) if q > 1 else buf[[k1]]
+            for kq in range(q):
+                out[k1 + 16 * kq] = v[kq]
+        return out
+    r = q // 16
+    for k1 in range(16):                                 # pass B1: the warp owning block k1
+        stage = {}
+        for c2 in range(r):
+            v = _dft(buf[[q * k1 + r * c1 + c2 for c1 in range(16)]], sign)
+            for j1 in range(16):
+                stage[q * k1 + 16 * c2 + j1] = v[j1] * tw[16 * c2 * j1]
+        for pos, val in stage.items():                   # written after the warp's reads
+            buf[pos] = val
+    for k1 in range(16):                                 # pass B2: thread (x, k1, j1)
+        for j1 in range(16):
+            v = _dft(buf[[q * k1 + 16 * c2 + j1 for c2 in range(r)]], sign)
+            for j2 in range(r):
+                out[k1 + 16 * (j1 + 16 * j2)] = v[j2]
+    return out
+
+
+@pytest.mark.parametrize("n1", [4, 8, 16, 32, 64, 128, 256, 512, 1024])
+@pytest.mark.parametrize("sign", [1, -1])
+def test_colfft_passes_are_the_n1_point_dft(n1, sign):
+    rng = np.random.default_rng(n1 + (sign > 0))
+    x = rng.standard_normal(n1) + 1j * rng.standard_normal(n1)
+    ref = np.fft.ifft(x) * n1 if sign > 0 else np.fft.fft(x)
+    assert np.max(np.abs(colfft_block(x, sign) - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+def test_colfft_block_positions_are_a_permutation():
+    """Every pass reads and writes each in-block position exactly once."""
+    for n1 in (256, 512, 1024):
+        q = n1 // 16
+        pa = sorted(q * a1 + a2 for a2 in range(q) for a1 in range(16))
+        assert pa == list(range(n1))
+        if q > 16:
+            r = q // 16
+            reads = sorted(q * k1 + r * c1 + c2 for k1 in range(16) for c2 in range(r) for c1 in range(16))
+            writes = sorted(q * k1 + 16 * c2 + j1 for k1 in range(16) for c2 in range(r) for j1 in range(16))
+            assert reads == writes == list(range(n1))

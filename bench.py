@@ -17,9 +17,10 @@ dec -30, 200-source sky + noise, Kaiser-Bessel support 7).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload large|wstack|channels|adjoint|small]
 
-Multi-GPU (torchrun): every rank images its own copy of the workload (the
-path has no exchange step: replicas, weak scaling); value = all ranks'
-visibilities / the slowest rank's time.
+Multi-GPU (torchrun): one image over all ranks -- every rank takes all
+measurements and transforms and stacks its share of the w-planes, and one
+NCCL all-reduce per step sums the images (strong scaling); value = the
+image's visibilities per step / the slowest rank's time per step.
 
 The line carries the gridder's roofline (``roofline``), the fused stack's
 (``roofline_other``), per-phase GB/s, NVML energy per image, the end-to-end
@@ -345,10 +346,10 @@ def parity_check(prob_np, params, image, side=8):
 
 
 # ------------------------------------------------------------------ main
-def aggregate(ms_local, units_per_step, steps, world, device):
+def aggregate(ms_local, job_units_per_step, steps, world, device):
     """Slowest rank's timed-region milliseconds and the whole-job throughput:
-    every rank processes units_per_step units per step (replicas, weak
-    scaling), value = world * units_per_step * steps / slowest time."""
+    the job (all ranks together) processes job_units_per_step units per
+    step, value = job_units_per_step * steps / slowest time."""
     import torch
     import torch.distributed as dist
     ms = float(ms_local)
@@ -356,7 +357,7 @@ def aggregate(ms_local, units_per_step, steps, world, device):
         t = torch.tensor([ms], device=device, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    return ms, world * units_per_step * steps / (ms / 1e3)
+    return ms, job_units_per_step * steps / (ms / 1e3)
 
 
 def main():
@@ -412,7 +413,8 @@ def workload_config(wl, params, m, world, args):
     return {"workload": desc, "n": n, "nw": nw, "nvis": int(m), "kernel": "kaiser-bessel",
             "support": int(params["support"]), "uniform_weighting": bool(int(params["flags"]) & 8),
             "l2": "inputs larger than L2 (%.2f GB of planes written and read every step)" % (8.0 * nw * n * n / 1e9),
-            "parallelism": "replicas" if world > 1 else "single GPU"}
+            "parallelism": ("%d GPUs: w-planes sharded, NCCL all-reduce of the image" % world) if world > 1
+            else "single GPU"}
 
 
 def _nvml_for(dev):
@@ -455,11 +457,20 @@ def run_image(args, rank, world):
     n, nw = params["n"], params["nw"]
     img = torch.empty((n, n), dtype=torch.float32, device=dev)
     m = prob["u"].numel()
+    k0, k1 = 0, nw
+    if world > 1:
+        # one image over all ranks: rank r transforms and stacks the w-planes
+        # of its share, and one all-reduce sums the images
+        from paper_2504_00959_gb300.sharded import plane_share
+        k0, k1 = plane_share(nw, rank, world)
+        im.set_plane_range(k0, k1)
 
     def step():
         im.reset()
         im.grid(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"])
         im.image(out=img)
+        if world > 1:
+            dist.all_reduce(img)
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -489,6 +500,10 @@ def run_image(args, rank, world):
     tm = im.timing()
     st = im.stats()  # raises if a bounded wait of the fused column kernel ran out
     ms, value = aggregate(ms, m, args.steps, world, dev)
+    if world > 1 and e0 is not None and e1 is not None:
+        ej = torch.tensor([float(e1 - e0)], dtype=torch.float64, device=dev)
+        dist.all_reduce(ej)  # the job's energy: every rank's GPU
+        e0, e1 = 0, float(ej.item())
     steps = max(args.steps, 1)
     ms_step = ms / steps
 
@@ -501,8 +516,8 @@ def run_image(args, rank, world):
     # measurements twice (count, scatter; a third time for the uniform-
     # weighting density) and writes one 16 B entry per (measurement, tile)
     peak, peak_kind = _peaks()
-    cells = float(nw) * n * n
-    groups = -(-nw // max(st["plane_group"], 1))
+    cells = float(k1 - k0) * n * n  # this rank's planes
+    groups = -(-(k1 - k0) // max(st["plane_group"], 1))
     uniform = bool(params["flags"] & synth.FLAG_UNIFORM)
     grid_ms = tm["grid_ms"] / steps
     grid_bytes = 24.0 * st["n_gridded"] + 8.0 * cells
@@ -558,7 +573,40 @@ def run_image(args, rank, world):
 
     # ------------------------------------------------ end to end, host buffers
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and world > 1:
+        # every rank uploads the inputs, images its share, the ranks sum the
+        # images and every rank downloads the image
+        hv = prob["vis"].cpu().pin_memory()
+        hu, hvv, hw, hwt = (prob[k].cpu().pin_memory() for k in ("u", "v", "w", "wt"))
+        himg = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        dv, du, dvv, dww, dwt = (torch.empty_like(prob[k]) for k in ("vis", "u", "v", "w", "wt"))
+
+        def e2e_step():
+            for d, h_ in ((dv, hv), (du, hu), (dvv, hvv), (dww, hw), (dwt, hwt)):
+                d.copy_(h_, non_blocking=True)
+            im.reset()
+            im.grid(dv, du, dvv, dww, dwt)
+            im.image(out=img)
+            dist.all_reduce(img)
+            himg.copy_(img, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        dist.barrier()
+        ksteps = max(min(args.steps, 5), 1)
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            e2e_step()
+        torch.cuda.synchronize()
+        te_t = torch.tensor([(time.perf_counter() - t0) / ksteps], dtype=torch.float64, device=dev)
+        dist.all_reduce(te_t, op=dist.ReduceOp.MAX)
+        te = float(te_t.item())
+        e2e = {"value": m / te, "unit": "vis/s", "ms_per_step": te * 1e3,
+               "h2d_bytes_per_step": int(world * m * (8 + 4 + 4 + 4 + 4)), "d2h_bytes_per_step": int(world * n * n * 4),
+               "api": "Imager.grid + image on each rank's plane share from pinned host copies, NCCL all-reduce, "
+                      "image download; %d steps, slowest rank" % ksteps}
+        del hv, hu, hvv, hw, hwt, himg, dv, du, dvv, dww, dwt
+    elif not args.no_e2e:
         hv = prob["vis"].cpu().pin_memory()
         hu, hvv, hw, hwt = (prob[k].cpu().pin_memory() for k in ("u", "v", "w", "wt"))
         himg = torch.empty((n, n), dtype=torch.float32).pin_memory()
@@ -613,13 +661,14 @@ def run_image(args, rank, world):
     step_bytes = prep_bytes + grid_bytes + fft_bytes + colfft_bytes + stack_bytes
     out = {
         "metric": METRIC, "value": value, "unit": "vis/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "f32", "data": DATA[wl], "config": config,
         "roofline": rl, "roofline_other": rl_other, "phases": phases,
         "roofline_frac_end_to_end": step_bytes / (ms_step / 1e3) / 1e9 / peak,
         "energy_j_per_solution": energy, "e2e": e2e, "cpu_baseline": cpu, "parity": parity,
         "gpu_launches": int(tm["kernel_launches"]), "clocks": clk,
-        "launch": {"tile": st["tile"], "plane_group": st["plane_group"], "plane_groups": groups},
+        "launch": {"tile": st["tile"], "plane_group": st["plane_group"], "plane_groups": groups,
+                   "planes_of_rank0": [k0, k1]},
     }
     if rank == 0:
         print(json.dumps(out))

@@ -290,6 +290,31 @@ rick_status rick_grid_planes_static(const rick_params* p, const float* vis, cons
                                     int64_t nvis, float* planes, void* cuda_stream, char* err,
                                     size_t err_len);
 
+/* Sharding one image over several GPUs (the paper reduces the gridded
+ * w-planes of its sectors across ranks, Sec. 2.2; here each rank finishes its
+ * share of the image and the ranks sum images).  Every step of imaging is
+ * linear in the planes and in the measurements, and the finalisation (sign,
+ * 1 / weight sum, taper, n) is per pixel, so images of disjoint shares made
+ * with the same weight sum add up to the image of everything.
+ *
+ * rick_set_plane_range: this handle grids, transforms and stacks only the
+ * w-planes k0 .. k1-1 (0 <= k0 < k1 <= nw; the default is all of them); every
+ * measurement is still placed, weighted (uniform weighting counts all) and
+ * counted in the weight sum, so ranks that each see all measurements and
+ * take disjoint plane ranges produce images that sum to the full image.
+ * rick_degrid then covers the same planes (its gradients sum likewise).
+ * Call it after rick_create or rick_reset, before rick_grid (RICK_ERR_STATE
+ * otherwise).  Not for batched handles. */
+rick_status rick_set_plane_range(rick_handle h, int32_t k0, int32_t k1);
+
+/* rick_set_weight_sum: normalise images (and the adjoint) by sum_w instead
+ * of the handle's own weight sum -- for ranks that each grid a share of the
+ * measurements: the caller sums the ranks' weight sums (rick_get_stats)
+ * and sets the total on every rank before rick_fft_and_stack.  sum_w < 0
+ * returns to the handle's own sum.  Synchronises the handle's stream.  Not
+ * for batched handles. */
+rick_status rick_set_weight_sum(rick_handle h, double sum_w);
+
 /* Test hook of the error path of the fused column-transform kernel (the
  * split transform of rick_fft_and_stack; the paper has no counterpart).
  * Every wait of that kernel on its shared-memory pipeline is bounded; with

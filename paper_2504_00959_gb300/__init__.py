@@ -216,6 +216,17 @@ class Imager:
         """Wait for everything enqueued on this imager (rick_synchronize)."""
         _lib.check(self._L.rick_synchronize(self._h), self._h)
 
+    def set_plane_range(self, k0, k1):
+        """Grid, transform and stack only w-planes k0 .. k1-1 (rick_set_plane_range);
+        call before grid (after reset)."""
+        _lib.check(self._L.rick_set_plane_range(self._h, int(k0), int(k1)), self._h)
+
+    def set_weight_sum(self, sum_w):
+        """Normalise by sum_w instead of this imager's own weight sum
+        (rick_set_weight_sum); sum_w < 0 returns to the own sum."""
+        self._sync_stream()
+        _lib.check(self._L.rick_set_weight_sum(self._h, float(sum_w)), self._h)
+
     def debug_colstack(self, skip_slot=-1, wait_ns=0):
         """Test hook of the fused column kernel's bounded waits
         (rick_debug_colstack): skip_slot >= 0 leaves that pipeline slot's copy

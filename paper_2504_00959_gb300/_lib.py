@@ -75,6 +75,8 @@ SIGNATURES = {
                                  ctypes.POINTER(ctypes.c_double)]),
     "rick_grid_planes_static": (_S, [ctypes.POINTER(RickParams), _P, _P, _P, _P, _P, ctypes.c_int64, _P, _P,
                                      ctypes.c_char_p, ctypes.c_size_t]),
+    "rick_set_plane_range": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),
+    "rick_set_weight_sum": (_S, [_H, ctypes.c_double]),
     "rick_debug_colstack": (_S, [_H, ctypes.c_int32, ctypes.c_int64]),
     "rick_get_stats": (_S, [_H, ctypes.POINTER(RickStats)]),
     "rick_set_timing": (_S, [_H, ctypes.c_int32]),

@@ -154,6 +154,8 @@ rick_status check_params(const rick_params* p, GridCfg* c, double* kparam, char*
     c->nw_chan = p->nw;
     c->chan_w = nullptr;
     c->chan_off = nullptr;
+    c->plane_lo = 0;
+    c->plane_hi = p->nw;
     (void)is_pow2;
     return RICK_OK;
 }
@@ -303,6 +305,10 @@ rick_status check_vis_args(rick_handle h, const float* vis, const float* u, cons
     if (nvis > (int64_t)1 << 30) return fail(h, RICK_ERR_ARG, "at most 2^30 measurements per call");
     return RICK_OK;
 }
+
+// The weight sum images are normalised by: the caller's (rick_set_weight_sum)
+// or the handle's own (device).
+const double* norm_sum(rick_handle h) { return h->sw_given ? h->sw_dev : &h->ctr->sum_w; }
 
 // The twiddle table and tensor map of k_colfft (the first column factor of
 // the split transform), made on first use: exp(+2 pi i j / N1), j < N1, in
@@ -462,6 +468,7 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
         h->cfg.nchan = nchan;
         h->cfg.nw_chan = p->nw;
         h->cfg.nw = nchan * p->nw;
+        h->cfg.plane_hi = h->cfg.nw;
         h->cfg.cstride = counter_stride((int64_t)h->cfg.nw * h->cfg.ntp);
         h->nchan = nchan;
         h->chan_wmin.assign(w_min, w_min + nchan);
@@ -658,6 +665,7 @@ rick_status rick_destroy(rick_handle h)
     }
     cudaFree(h->taper);
     cudaFree(h->cf_tw);
+    cudaFree(h->sw_dev);
     cudaFree(h->planes);
     cudaFree(h->acc);
     cudaFree(h->cursor);
@@ -813,15 +821,16 @@ rick_status rick_fft_and_stack(rick_handle h, float* image)
     // cuFFT's 2D plan and k_stack
     int n1 = 0, n2 = 0;
     const bool split = use_split(p, &n1, &n2);
-    for (int k0 = 0; k0 < p.nw; k0 += h->G) {
-        const int nk = (p.nw - k0 < h->G) ? p.nw - k0 : h->G;
+    const int lo = h->cfg.plane_lo, hi = h->cfg.plane_hi;
+    for (int k0 = lo; k0 < hi; k0 += h->G) {
+        const int nk = (hi - k0 < h->G) ? hi - k0 : h->G;
         rick_status s = grid_pass(h, k0, nk, true, h->planes);
         if (s) return s;
         cufftComplex* planes = reinterpret_cast<cufftComplex*>(h->planes);
         a.k0 = k0;
         a.nk = nk;
-        a.first = (k0 == 0);
-        a.last = (k0 + nk >= p.nw);
+        a.first = (k0 == lo);
+        a.last = (k0 + nk >= hi);
         if (split) {
             cufftHandle rows;
             if ((s = get_plan(h, nk, &rows, kPlanRows))) return s;
@@ -841,7 +850,7 @@ rick_status rick_fft_and_stack(rick_handle h, float* image)
                 h->colmap_ready = true;
             }
             PhaseScope ss(h, kPhaseStack);
-            RICK_CU(h, launch_colstack(h->colmap, a, n1, n2, h->acc, h->taper, &h->ctr->sum_w, image, &h->ctr->err,
+            RICK_CU(h, launch_colstack(h->colmap, a, n1, n2, h->acc, h->taper, norm_sum(h), image, &h->ctr->err,
                                        h->stream));
         } else {
             cufftHandle plan;
@@ -851,7 +860,7 @@ rick_status rick_fft_and_stack(rick_handle h, float* image)
                 RICK_FFT(h, cufftExecC2C(plan, planes, planes, CUFFT_INVERSE));
             }
             PhaseScope ss(h, kPhaseStack);
-            RICK_CU(h, launch_stack(a, h->planes, h->acc, h->taper, &h->ctr->sum_w, image, h->stream));
+            RICK_CU(h, launch_stack(a, h->planes, h->acc, h->taper, norm_sum(h), image, h->stream));
         }
         count_launches(h, 1);
     }
@@ -909,8 +918,8 @@ static rick_status degrid_impl(rick_handle h, const GridCfg& c, const double* su
     int n1 = 0, n2 = 0;
     const bool split = use_split(p, &n1, &n2);
     cufftComplex* planes = reinterpret_cast<cufftComplex*>(h->planes);
-    for (int k0 = 0; !st && k0 < p.nw; k0 += h->G) {
-        const int nk = (p.nw - k0 < h->G) ? p.nw - k0 : h->G;
+    for (int k0 = c.plane_lo; !st && k0 < c.plane_hi; k0 += h->G) {
+        const int nk = (c.plane_hi - k0 < h->G) ? c.plane_hi - k0 : h->G;
         a.k0 = k0;
         a.nk = nk;
         e = split ? launch_spreadcol(a, n1, n2, image_grad, h->taper, sum_w, h->planes, h->stream)
@@ -964,7 +973,7 @@ rick_status rick_degrid(rick_handle h, const float* image_grad, const float* u, 
     if (h->chunks.empty())
         return fail(h, RICK_ERR_STATE, "rick_degrid needs the weight sum of a forward pass: call rick_grid first");
     if (nvis == 0) return RICK_OK;
-    return degrid_impl(h, h->cfg, &h->ctr->sum_w, h->density, image_grad, u, v, w, weights, nvis, vis_grad);
+    return degrid_impl(h, h->cfg, norm_sum(h), h->density, image_grad, u, v, w, weights, nvis, vis_grad);
 }
 
 rick_status rick_predict(rick_handle h, const float* model, const float* u, const float* v, const float* w,
@@ -1463,6 +1472,40 @@ rick_status rick_autotune_batch(const rick_params* p, int32_t nchan, const doubl
             fclose(f);
         }
     }
+    return RICK_OK;
+}
+
+rick_status rick_set_plane_range(rick_handle h, int32_t k0, int32_t k1)
+{
+    if (!h) return RICK_ERR_ARG;
+    if (h->batch) return fail(h, RICK_ERR_STATE, "batched handle: the plane range is single-image");
+    if (!(0 <= k0 && k0 < k1 && k1 <= h->p.nw))
+        return fail(h, RICK_ERR_ARG, "plane range [%d, %d) not within [0, %d)", (int)k0, (int)k1, (int)h->p.nw);
+    if (!h->chunks.empty())
+        return fail(h, RICK_ERR_STATE, "set the plane range before rick_grid (after rick_reset)");
+    h->cfg.plane_lo = k0;
+    h->cfg.plane_hi = k1;
+    return RICK_OK;
+}
+
+rick_status rick_set_weight_sum(rick_handle h, double sum_w)
+{
+    if (!h) return RICK_ERR_ARG;
+    if (h->batch) return fail(h, RICK_ERR_STATE, "batched handle: weight sums are per channel");
+    if (std::isnan(sum_w) || std::isinf(sum_w)) return fail(h, RICK_ERR_ARG, "sum_w must be finite");
+    if (sum_w < 0.0) {
+        h->sw_given = false;
+        return RICK_OK;
+    }
+    if (!h->sw_dev) {
+        RICK_CU(h, cudaMalloc((void**)&h->sw_dev, sizeof(double)));
+        h->bytes_held += sizeof(double);
+    }
+    // the host value is kept in the handle: the copy is ordered on the stream
+    RICK_CU(h, cudaStreamSynchronize(h->stream));
+    h->sw_host = sum_w;
+    RICK_CU(h, cudaMemcpy(h->sw_dev, &h->sw_host, sizeof(double), cudaMemcpyHostToDevice));
+    h->sw_given = true;
     return RICK_OK;
 }
 

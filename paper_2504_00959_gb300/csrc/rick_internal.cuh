@@ -49,6 +49,10 @@ struct GridCfg {
     int Sw;
     float half_sw, wkp, two_over_sw; // Sw/2; Gaussian 1/(2 sigma_w^2) or KB beta_w; 2/Sw
     int fold;                        // RICK_HERMITIAN_FOLD: mirror measurements with w < 0
+    // planes this handle grids and transforms: [plane_lo, plane_hi) of the nw
+    // (rick_set_plane_range; all by default).  Measurements on other planes
+    // are placed, weighted and counted but list no entries.
+    int plane_lo, plane_hi;
     // batched imaging: nchan channels with nw_chan w-planes each, channel c
     // owning planes c*nw_chan .. (c+1)*nw_chan-1 and measurements
     // chan_off[c] .. chan_off[c+1]-1; chan_w[c] = (w_min, 1/dw) in binary32.
@@ -406,6 +410,11 @@ struct rick_imager {
     cudaGraphExec_t graph;
     const void* graph_key[7];
     int64_t graph_m;
+    // normalisation weight sum supplied by the caller (rick_set_weight_sum):
+    // used instead of the handle's own sum when sw_given
+    bool sw_given;
+    double sw_host;
+    double* sw_dev;
     // test hook of k_colstack's bounded waits (rick_debug_colstack)
     int dbg_skip_slot1;
     unsigned long long dbg_wait_ns;

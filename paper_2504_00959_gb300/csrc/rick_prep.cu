@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_count(GridCfg c, Inputs in, in
                 // the measurement's planes: its own (Sw = 1) or its w-footprint
                 for (int tw = 0; tw < c.Sw; ++tw) {
                     const int plane = p[q].k + tw;
-                    if (plane < 0 || plane >= c.nw) continue;
+                    if (plane < c.plane_lo || plane >= c.plane_hi) continue;
                     int64_t t[4];
                     footprint_tiles(c, p[q], plane, t);
 #pragma unroll
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_scatter(GridCfg c, Inputs in, 
                     const float hn = w_tap_norm(c, p[q]);
                     for (int tw = 0; tw < c.Sw; ++tw) {
                         const int plane = p[q].k + tw;
-                        if (plane < 0 || plane >= c.nw) continue;
+                        if (plane < c.plane_lo || plane >= c.plane_hi) continue;
                         const float ht = w_kernel(c, __fsub_rn((float)plane, p[q].pw)) * hn;
                         const float4 rw = make_float4(rec[q].x, rec[q].y, ht * rec[q].z, ht * rec[q].w);
                         int64_t tt[4];
@@ -233,6 +233,10 @@ __global__ void __launch_bounds__(kPrepThreads) k_scatter(GridCfg c, Inputs in, 
                             }
                     }
                     ok[q] = false;  // written: skip the nearest-plane stores below
+                    continue;
+                }
+                if (p[q].k < c.plane_lo || p[q].k >= c.plane_hi) {
+                    ok[q] = false;  // weighted and counted, no entries: another rank's plane
                     continue;
                 }
                 footprint_tiles(c, p[q], p[q].k, t[q]);

@@ -1,7 +1,6 @@
 // rick_api.cu -- the C ABI of librick (include/rick.h): handle, parameter
 // checks, device memory plan, cuFFT plans and the step sequence of the
 // workflow in Sec. 2.1 (grid -> per-plane FFT -> w-correction + reduction).
-#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -157,7 +156,6 @@ rick_status check_params(const rick_params* p, GridCfg* c, double* kparam, char*
     c->chan_off = nullptr;
     c->plane_lo = 0;
     c->plane_hi = p->nw;
-    c->stats = 1;
     (void)is_pow2;
     return RICK_OK;
 }
@@ -296,10 +294,6 @@ void resolve_timer(rick_handle h, bool accumulate)
         h->timer.pending[ph].clear();
     }
 }
-
-// per-tile counters one count / scatter pass keeps in L2 (of 129 MB, shared
-// by the two dies' halves)
-constexpr int64_t kSortCounterBytes = int64_t(32) << 20;
 
 int64_t entries_bound(const GridCfg& c, int64_t nvis) { return nvis * (c.S > 1 ? 4 : 1) * c.Sw; }
 
@@ -797,35 +791,13 @@ rick_status rick_grid(rick_handle h, const float* vis, const float* u, const flo
     }
     // the chunk is registered only once every kernel that fills it is enqueued,
     // so a failed call never leaves unfilled offsets for the gridder to read
-    // The per-tile counters of a large grid do not fit in L2 (134 MB at
-    // 16384^2 x 128 planes), and every count and scatter atomic would then go
-    // to DRAM in random order; count and scatter run instead over ranges of
-    // planes whose counters do fit, reading the measurements once per range
-    // (the weight sum and counters are taken in the first range only).
-    const int64_t per_plane = c.ntp * c.cstride * (int64_t)sizeof(uint32_t);
-    const int span = c.plane_hi - c.plane_lo;
-    const int most = (int)std::min<int64_t>(span, std::max<int64_t>(1, kSortCounterBytes / per_plane));
-    const int npass = (span + most - 1) / most;
-    const int per_pass = (span + npass - 1) / npass;  // balanced ranges
     e = cudaMemsetAsync(h->cursor, 0, (size_t)ntiles * c.cstride * sizeof(uint32_t), h->stream);
-    for (int lo = c.plane_lo; e == cudaSuccess && lo < c.plane_hi; lo += per_pass) {
-        GridCfg cc = c;
-        cc.plane_lo = lo;
-        cc.plane_hi = std::min(c.plane_hi, lo + per_pass);
-        e = launch_count(cc, u, v, w, weights, vis2, nvis, h->cursor, h->stream);
-        count_launches(h, 1);
-    }
+    if (e == cudaSuccess) e = launch_count(c, u, v, w, weights, vis2, nvis, h->cursor, h->stream);
     if (e == cudaSuccess)
         e = launch_scan(h->cursor, ntiles, c.cstride, ch.off, h->cursor, h->block_sums, h->stream);
-    for (int lo = c.plane_lo; e == cudaSuccess && lo < c.plane_hi; lo += per_pass) {
-        GridCfg cc = c;
-        cc.plane_lo = lo;
-        cc.plane_hi = std::min(c.plane_hi, lo + per_pass);
-        cc.stats = lo == c.plane_lo;
-        e = launch_scatter(cc, u, v, w, weights, vis2, nvis, h->density, h->cursor, ch.ent, h->ctr, nullptr,
+    if (e == cudaSuccess)
+        e = launch_scatter(c, u, v, w, weights, vis2, nvis, h->density, h->cursor, ch.ent, h->ctr, nullptr,
                            h->stream);
-        count_launches(h, 1);
-    }
     if (e != cudaSuccess) {
         cudaFreeAsync(ch.off, h->stream);
         cudaFreeAsync(ch.ent, h->stream);
@@ -833,7 +805,7 @@ rick_status rick_grid(rick_handle h, const float* vis, const float* u, const flo
     }
     h->chunks.push_back(ch);
     h->bytes_held += off_bytes + ent_bytes;
-    count_launches(h, 3);  // the scan (count and scatter counted above)
+    count_launches(h, 5);
     return RICK_OK;
 }
 

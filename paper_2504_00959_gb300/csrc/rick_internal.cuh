@@ -53,9 +53,6 @@ struct GridCfg {
     // (rick_set_plane_range; all by default).  Measurements on other planes
     // are placed, weighted and counted but list no entries.
     int plane_lo, plane_hi;
-    // k_scatter accumulates the weight sum and the gridded / dropped counters
-    // (1), or only lists entries (0: a later pass over another plane range)
-    int stats;
     // batched imaging: nchan channels with nw_chan w-planes each, channel c
     // owning planes c*nw_chan .. (c+1)*nw_chan-1 and measurements
     // chan_off[c] .. chan_off[c+1]-1; chan_w[c] = (w_min, 1/dw) in binary32.

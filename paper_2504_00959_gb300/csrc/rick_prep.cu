@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_scatter(GridCfg c, Inputs in, 
                 ok[q] = false;
                 if (i < i1) {
                     ok[q] = load_and_place(c, in, i, chan, p[q], wi[q], V[q]);
-                    if (!ok[q] && c.stats) ++dropped;
+                    if (!ok[q]) ++dropped;
                 }
             }
             // the gridder reads the visibility already weighted and divided by
@@ -213,10 +213,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_scatter(GridCfg c, Inputs in, 
                 }
                 const float scale = wi[q] / (tap_sum(c, p[q].pu, p[q].fu) * tap_sum(c, p[q].pv, p[q].fv));
                 rec[q] = make_float4(p[q].pu, p[q].pv, scale * V[q].x, scale * V[q].y);
-                if (c.stats) {
-                    sw += wi[q];
-                    ++gridded;
-                }
+                sw += wi[q];
+                ++gridded;
                 if (c.Sw > 1) {
                     // w-footprint: one set of entries per plane, the w-tap in the scale
                     const float hn = w_tap_norm(c, p[q]);

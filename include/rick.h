@@ -67,9 +67,6 @@ typedef int32_t rick_status;
                                   separate pass, also where the library would otherwise split
                                   the column transform and fuse its last factor with the
                                   w-screen and the stack (single images with n >= 4096) */
-#define RICK_FFT_CUFFT_ROWS 256u /* with the split transform, cuFFT transforms the rows also at
-                                  n = 8192 and 16384, where the library's one-pass row kernel
-                                  would (for tests and measurement) */
 #define RICK_FFT_SPLIT 128u     /* the split transform for any power-of-two n in [64, 16384]
                                   (single images; the default from n = 4096 on, for tests and
                                   measurement below).  Not with RICK_FFT_2D.  Either way the
@@ -163,11 +160,9 @@ rick_status rick_add_density(rick_handle h, const float* vis, const float* u, co
  * weight sum and, per flags, by the taper and times n.  image: float[n*n]
  * (RICK_REAL_IMAGE) or float[2*n*n] complex, fully overwritten.  For
  * power-of-two n from 4096 to 16384 (or with RICK_FFT_SPLIT) the column
- * transform is split, n = 16 * (n / 16): the rows are transformed by cuFFT
- * (by the library's one-pass row kernel at n = 8192 and 16384, unless
- * RICK_FFT_CUFFT_ROWS), one library kernel the first (n / 16-point) column
- * factor of every plane of the group in place, and one kernel the last
- * 16-point column factor
+ * transform is split, n = 16 * (n / 16): cuFFT transforms the rows, one
+ * library kernel the first (n / 16-point) column factor of every plane of
+ * the group in place, and one kernel the last 16-point column factor
  * together with the screen and the sum, reading each plane once more;
  * otherwise cuFFT's 2D plan and a separate screen-and-sum pass
  * (RICK_FFT_2D). */

@@ -18,14 +18,13 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import (APPLY_N, FFT_2D, FFT_CUFFT_ROWS, FFT_SPLIT, GRID_CORRECT, HERMITIAN_FOLD, KERNEL_GAUSS, KERNEL_KB,  # noqa: F401
+from ._lib import (APPLY_N, FFT_2D, FFT_SPLIT, GRID_CORRECT, HERMITIAN_FOLD, KERNEL_GAUSS, KERNEL_KB,  # noqa: F401
                    REAL_IMAGE, UNIFORM_WEIGHT,
                    RickError)
 
 __all__ = ["Imager", "BatchImager", "autotune_batch", "DirtyImage", "dirty_image", "RickError", "load",
            "KERNEL_GAUSS", "KERNEL_KB",
-           "GRID_CORRECT", "REAL_IMAGE", "APPLY_N", "UNIFORM_WEIGHT", "HERMITIAN_FOLD", "FFT_2D", "FFT_SPLIT",
-           "FFT_CUFFT_ROWS"]
+           "GRID_CORRECT", "REAL_IMAGE", "APPLY_N", "UNIFORM_WEIGHT", "HERMITIAN_FOLD", "FFT_2D", "FFT_SPLIT"]
 
 
 def load():

@@ -23,7 +23,6 @@ UNIFORM_WEIGHT = 8
 HERMITIAN_FOLD = 32
 FFT_2D = 64
 FFT_SPLIT = 128
-FFT_CUFFT_ROWS = 256
 
 
 class RickParams(ctypes.Structure):

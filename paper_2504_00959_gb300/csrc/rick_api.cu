@@ -99,7 +99,7 @@ rick_status check_params(const rick_params* p, GridCfg* c, double* kparam, char*
         T = 32;
     }
     const uint32_t known = RICK_GRID_CORRECT | RICK_REAL_IMAGE | RICK_APPLY_N | RICK_UNIFORM_WEIGHT |
-                           RICK_HERMITIAN_FOLD | RICK_FFT_2D | RICK_FFT_SPLIT | RICK_FFT_CUFFT_ROWS;
+                           RICK_HERMITIAN_FOLD | RICK_FFT_2D | RICK_FFT_SPLIT;
     if (p->flags & ~known) {
         snprintf(msg, msglen, "unknown flags 0x%x", p->flags & ~known);
         return RICK_ERR_ARG;
@@ -306,9 +306,6 @@ rick_status check_vis_args(rick_handle h, const float* vis, const float* u, cons
     return RICK_OK;
 }
 
-// Whether the split transform's rows run in the library's one-pass kernel.
-bool own_rows(rick_handle h) { return rowfft_supported(h->p.n) && !(h->p.flags & RICK_FFT_CUFFT_ROWS); }
-
 // The weight sum images are normalised by: the caller's (rick_set_weight_sum)
 // or the handle's own (device).
 const double* norm_sum(rick_handle h) { return h->sw_given ? h->sw_dev : &h->ctr->sum_w; }
@@ -331,13 +328,6 @@ rick_status colfft_ready(rick_handle h)
     }
     RICK_CU(h, cudaMemcpy(h->cf_tw, tw.data(), sizeof(float2) * n1, cudaMemcpyHostToDevice));
     RICK_CU(h, encode_colfft_map(h->cfmap, h->planes, h->p.n, h->G));
-    if (own_rows(h) && !h->rf_tw) {
-        float2 t2[256];
-        rowfft_tables(h->p.n, t2);
-        RICK_CU(h, cudaMalloc((void**)&h->rf_tw, sizeof(t2)));
-        h->bytes_held += sizeof(t2);
-        RICK_CU(h, cudaMemcpy(h->rf_tw, t2, sizeof(t2), cudaMemcpyHostToDevice));
-    }
     h->cfmap_ready = true;
     return RICK_OK;
 }
@@ -641,21 +631,17 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
             for (int j = 0; j < kPolyTerms; ++j) h->cfg.coef[t][j] = (t < c.S) ? coef[t * kPolyTerms + j] : 0.0f;
         set_tap_sum(h->cfg);
     }
-    // the cuFFT plans this handle's transform path uses (none when the
-    // library's own kernels do the whole transform)
+    // the cuFFT plans this handle's transform path uses
     {
         cufftHandle plan;
         int n1 = 0, n2 = 0;
         const bool split = !h->batch && use_split(*p, &n1, &n2);
-        const bool rows_own = split && rowfft_supported(p->n) && !(p->flags & RICK_FFT_CUFFT_ROWS);
-        if (!rows_own) {
-            const int kind = split ? kPlanRows : kPlan2D;
-            s = get_plan(h, G, &plan, kind);
+        const int kind = split ? kPlanRows : kPlan2D;
+        s = get_plan(h, G, &plan, kind);
+        if (s) return cleanup(s);
+        if (NW % G) {
+            s = get_plan(h, NW % G, &plan, kind);
             if (s) return cleanup(s);
-            if (NW % G) {
-                s = get_plan(h, NW % G, &plan, kind);
-                if (s) return cleanup(s);
-            }
         }
     }
     if (cudaDeviceSynchronize() != cudaSuccess) return cleanup(RICK_ERR_CUDA);
@@ -685,7 +671,6 @@ rick_status rick_destroy(rick_handle h)
     }
     cudaFree(h->taper);
     cudaFree(h->cf_tw);
-    cudaFree(h->rf_tw);
     cudaFree(h->sw_dev);
     cudaFree(h->planes);
     cudaFree(h->acc);
@@ -853,18 +838,12 @@ rick_status rick_fft_and_stack(rick_handle h, float* image)
         a.first = (k0 == lo);
         a.last = (k0 + nk >= hi);
         if (split) {
-            cufftHandle rows = 0;
-            if (!own_rows(h) && (s = get_plan(h, nk, &rows, kPlanRows))) return s;
+            cufftHandle rows;
+            if ((s = get_plan(h, nk, &rows, kPlanRows))) return s;
             if ((s = colfft_ready(h))) return s;
             {
                 PhaseScope fs(h, kPhaseFft);
-                if (own_rows(h)) {
-                    RICK_CU(h, launch_rowfft(h->planes, p.n, nk, +1, h->rf_tw, h->dbg_wait_ns, &h->ctr->err,
-                                             h->stream));
-                    count_launches(h, 1);
-                } else {
-                    RICK_FFT(h, cufftExecC2C(rows, planes, planes, CUFFT_INVERSE));
-                }
+                RICK_FFT(h, cufftExecC2C(rows, planes, planes, CUFFT_INVERSE));
             }
             {
                 PhaseScope cs(h, kPhaseColfft);
@@ -957,8 +936,8 @@ static rick_status degrid_impl(rick_handle h, const GridCfg& c, const double* su
         }
         cufftResult r = CUFFT_SUCCESS;
         if (split) {
-            cufftHandle rows = 0;
-            if (!own_rows(h) && (st = get_plan(h, nk, &rows, kPlanRows))) break;
+            cufftHandle rows;
+            if ((st = get_plan(h, nk, &rows, kPlanRows))) break;
             if ((st = colfft_ready(h))) break;
             e = launch_colfft(h->cfmap, h->cf_tw, h->planes, p.n, nk, -1, h->dbg_wait_ns, &h->ctr->err, h->stream);
             if (e != cudaSuccess) {
@@ -966,16 +945,7 @@ static rick_status degrid_impl(rick_handle h, const GridCfg& c, const double* su
                 break;
             }
             count_launches(h, 1);
-            if (own_rows(h)) {
-                e = launch_rowfft(h->planes, p.n, nk, -1, h->rf_tw, h->dbg_wait_ns, &h->ctr->err, h->stream);
-                if (e != cudaSuccess) {
-                    st = fail(h, RICK_ERR_CUDA, "k_rowfft: %s", cudaGetErrorString(e));
-                    break;
-                }
-                count_launches(h, 1);
-            } else {
-                r = cufftExecC2C(rows, planes, planes, CUFFT_FORWARD);
-            }
+            r = cufftExecC2C(rows, planes, planes, CUFFT_FORWARD);
         } else {
             cufftHandle plan;
             if ((st = get_plan(h, nk, &plan))) break;

@@ -154,11 +154,12 @@ __device__ __forceinline__ void dft_small(float2 (&v)[R])
     }
 }
 
-// twiddle w_N1^e with the kernel's sign from the table of exp(+2 pi i j / N1)
+// twiddle w_N1^e with the kernel's sign from the block's shared copy of the
+// table of exp(+2 pi i j / N1)
 template <int SIGN>
-__device__ __forceinline__ float2 twid(const float2* __restrict__ tw, int e)
+__device__ __forceinline__ float2 twid(const float2* tw, int e)
 {
-    float2 t = __ldg(tw + e);
+    float2 t = tw[e];
     if (SIGN < 0) t.y = -t.y;
     return t;
 }
@@ -166,7 +167,7 @@ __device__ __forceinline__ float2 twid(const float2* __restrict__ tw, int e)
 // The N1 = 16 Q-point transform (N1 >= 16) of the block in shared memory
 // ([N1][W] complex values), written to rows 16 f1 + b of the plane at P.
 template <int N1, int W, int SIGN>
-__device__ __forceinline__ void colfft_two_pass(float2* __restrict__ buf, const float2* __restrict__ tw,
+__device__ __forceinline__ void colfft_two_pass(float2* __restrict__ buf, const float2* tw,
                                                 float2* __restrict__ P, int n, int b, int t)
 {
     constexpr int Q = N1 / 16;
@@ -242,8 +243,9 @@ __device__ __forceinline__ void colfft_two_pass(float2* __restrict__ buf, const 
 }
 
 // grid (n / W, 16, planes of the group); block kCfThreads; dynamic shared
-// memory N1 * W complex values + one mbarrier.  tw: exp(+2 pi i j / N1),
-// j < N1.  err: bit 1 set when the load wait ran out.
+// memory N1 * W complex values, the N1 twiddles and one mbarrier.  tw:
+// exp(+2 pi i j / N1), j < N1 (device; copied in with the block's data).
+// err: bit 1 set when the load wait ran out.
 template <int N1, int W, int SIGN>
 __global__ void __launch_bounds__(kCfThreads) k_colfft(const __grid_constant__ CUtensorMap map,
                                                        const float2* __restrict__ tw, float2* __restrict__ planes,
@@ -253,7 +255,8 @@ __global__ void __launch_bounds__(kCfThreads) k_colfft(const __grid_constant__ C
     constexpr int kBox = N1 < kCfBoxRows ? N1 : kCfBoxRows;
     extern __shared__ __align__(128) unsigned char cf_smem[];
     float2* buf = reinterpret_cast<float2*>(cf_smem);  // [N1][W]
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(cf_smem + (size_t)N1 * W * sizeof(float2));
+    float2* tws = buf + (size_t)N1 * W;                 // [N1] twiddles
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(tws + N1);
     __shared__ int s_abort;
 
     const int t = threadIdx.x;
@@ -266,10 +269,11 @@ __global__ void __launch_bounds__(kCfThreads) k_colfft(const __grid_constant__ C
     }
     __syncthreads();
     if (t == 0) {
-        mbar_expect(smem_u32(bar), (uint32_t)(N1 * W * sizeof(float2)));
+        mbar_expect(smem_u32(bar), (uint32_t)((N1 * W + N1) * sizeof(float2)));
 #pragma unroll
         for (int a0 = 0; a0 < N1; a0 += kBox)
             tma_load_3d(smem_u32(buf + (size_t)a0 * W), &map, x0, b, plane * N1 + a0, smem_u32(bar));
+        bulk_load(smem_u32(tws), tw, (uint32_t)(N1 * sizeof(float2)), smem_u32(bar));
     }
     const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(bar), 0, &s_abort, limit));
     if (!ok) s_abort = 1;
@@ -298,7 +302,7 @@ __global__ void __launch_bounds__(kCfThreads) k_colfft(const __grid_constant__ C
             for (int f1 = 0; f1 < N1; ++f1) P[(size_t)(16 * f1 + b) * n + it] = v[f1];
         }
     } else {
-        colfft_two_pass<N1, W, SIGN>(buf, tw, P, n, b, t);
+        colfft_two_pass<N1, W, SIGN>(buf, tws, P, n, b, t);
     }
 }
 
@@ -306,7 +310,7 @@ template <int N1, int W, int SIGN>
 cudaError_t launch_cf(const void* map, const float2* tw, float2* planes, int n, int nk, unsigned long long wait_ns,
                       unsigned long long* err, cudaStream_t s)
 {
-    const size_t smem = (size_t)N1 * W * sizeof(float2) + 16;
+    const size_t smem = (size_t)(N1 * W + N1) * sizeof(float2) + 16;
     static bool attr_done[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);

@@ -208,7 +208,7 @@ struct ChunkList {
 // Device-resident counters of a handle.
 struct Counters {
     unsigned long long gridded, dropped, entries;
-    unsigned long long err;          // a bounded wait ran out: bit 0 k_colstack, 1 k_colfft, 2 k_rowfft
+    unsigned long long err;          // a bounded wait ran out: bit 0 k_colstack, 1 k_colfft
     double sum_w;
 };
 
@@ -293,13 +293,6 @@ cudaError_t launch_colstack(const void* map, const StackArgs& a, int n1, int n2,
 cudaError_t encode_colfft_map(void* map, const float2* planes, int n, int planes_in_buffer);
 cudaError_t launch_colfft(const void* map, const float2* tw, float2* planes, int n, int nk, int sign,
                           unsigned long long wait_ns, unsigned long long* err, cudaStream_t s);
-// the row transforms of nk planes in one pass (k_rowfft, rick_rowfft.cu),
-// for n = 8192 and 16384 only (rowfft_supported); tw from rowfft_tables
-// (256 values, device)
-bool rowfft_supported(int n);
-void rowfft_tables(int n, float2* tw256);
-cudaError_t launch_rowfft(float2* planes, int n, int nk, int sign, const float2* tw, unsigned long long wait_ns,
-                          unsigned long long* err, cudaStream_t s);
 cudaError_t launch_spreadcol(const StackArgs& a, int n1, int n2, const void* rimg, const float* taper,
                              const double* sum_w, float2* planes, cudaStream_t s);
 cudaError_t launch_stack(const StackArgs& a, const float2* planes, float2* acc, const float* taper,
@@ -368,7 +361,6 @@ struct rick_imager {
     alignas(64) unsigned char cfmap[128];   // tensor map of `planes` for k_colfft
     bool cfmap_ready;
     float2* cf_tw;                   // [n / 16] exp(+2 pi i j / (n / 16)) for k_colfft
-    float2* rf_tw;                   // [256] twiddle tables of k_rowfft (n = 8192, 16384)
     struct Chunk {
         uint32_t* off;
         float4* ent;

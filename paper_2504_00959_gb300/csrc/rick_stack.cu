@@ -266,13 +266,20 @@ constexpr int kColWarps = kColW / 8;         // a warp owns 8 columns x kColQ va
 constexpr int kColThreads = 32 * kColWarps;
 constexpr int kColStages = 4;
 constexpr int kColPitch = kColW;             // complex values per staged row (the TMA box, dense)
-constexpr int kColExPitch = 36;              // complex values per g of a warp's exchange (2-way reads)
+// lanes: column cl = lane % 8 of the warp's 8, j = lane / 8; a half warp then
+// reads two rows of 8 columns of a stage (2-way bank conflict, the dense TMA
+// rows being 256 bytes apart) and, with this exchange pitch (two rows 320
+// bytes apart: 16 banks), writes and reads the exchange without conflicts
+constexpr int kColExPitch = 40;              // complex values per g of a warp's exchange
 constexpr size_t kColStageBytes = (size_t)kColN2 * kColPitch * sizeof(float2);
 constexpr size_t kColExBytes = (size_t)kColWarps * kColQ * kColExPitch * sizeof(float2);
+// each thread's 4 pixels: the screen's phase coefficients (A.hi, A.lo, B.hi,
+// B.lo) and n - 1, evaluated once per block
+constexpr size_t kColScrBytes = (size_t)kColQ * kColThreads * (sizeof(float4) + sizeof(float));
 // stages (TMA destinations, at the 128-byte aligned start) | full and empty
-// mbarriers | the warps' exchange buffers | abort flag and issue count
-constexpr size_t kColSmem =
-    kColStages * kColStageBytes + 2 * kColStages * sizeof(unsigned long long) + kColExBytes + 2 * sizeof(int);
+// mbarriers | the warps' exchange buffers | pixel screens | abort flag and issue count
+constexpr size_t kColSmem = kColStages * kColStageBytes + 2 * kColStages * sizeof(unsigned long long) + kColExBytes +
+                            kColScrBytes + 2 * sizeof(int);
 constexpr unsigned long long kColWaitNs = 1000000000ull;  // default bound of one wait: 1 s
 // planes summed by Horner's rule between direct evaluations of the screen
 // (the rotation per plane is applied in binary32, relative error ~1e-7 each)
@@ -314,11 +321,13 @@ __global__ void __launch_bounds__(kColThreads, 6) k_colstack(const __grid_consta
     unsigned long long* empty = full + kColStages;
     float2* exw = reinterpret_cast<float2*>(col_smem + kColStages * kColStageBytes +
                                             2 * kColStages * sizeof(unsigned long long));
-    int& s_abort = *reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(exw) + kColExBytes);
+    float4* scr = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(exw) + kColExBytes);  // [g][t]
+    float* snm1 = reinterpret_cast<float*>(scr + kColQ * kColThreads);                              // [g][t]
+    int& s_abort = *reinterpret_cast<int*>(snm1 + kColQ * kColThreads);
     int& s_issued = (&s_abort)[1];
 
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int j = lane & (kColQ - 1), cl = lane >> 2;
+    const int cl = lane & 7, j = lane >> 3;
     const int cw = 8 * w + cl;  // column in the CTA's strip
     const int n = a.n, nk = a.nk;
     const int x0 = blockIdx.x * kColW, x = x0 + cw;
@@ -375,9 +384,13 @@ __global__ void __launch_bounds__(kColThreads, 6) k_colstack(const __grid_consta
     // the thread's output pixels (x, y_g), y_g = f1 + N1 (j + 4 g): the screen's
     // rotation per plane, the Horner sum of the current block and the total
     float2 rho[kColQ], h[kColQ], sum[kColQ];
+    unsigned sky = 0;
 #pragma unroll
     for (int g = 0; g < kColQ; ++g) {
         const PixelScreen ps = pixel_screen(a, x, f1 + n1 * (j + kColQ * g));
+        scr[g * kColThreads + t] = make_float4(ps.A.hi, ps.A.lo, ps.B.hi, ps.B.lo);
+        snm1[g * kColThreads + t] = ps.nm1;
+        sky |= (ps.sky ? 1u : 0u) << g;
         rho[g] = turns_to_phasor(ps.B.hi, ps.B.lo);
         h[g] = make_float2(0.f, 0.f);
         sum[g] = make_float2(0.f, 0.f);
@@ -415,8 +428,8 @@ __global__ void __launch_bounds__(kColThreads, 6) k_colstack(const __grid_consta
         if (p % kColResync == 0) {
 #pragma unroll
             for (int g = 0; g < kColQ; ++g) {
-                const PixelScreen ps = pixel_screen(a, x, f1 + n1 * (j + kColQ * g));
-                const float2 r = cmul(h[g], screen(ps.A, ps.B, a.k0 + p));
+                const float4 ab = scr[g * kColThreads + t];
+                const float2 r = cmul(h[g], screen(FF{ab.x, ab.y}, FF{ab.z, ab.w}, a.k0 + p));
                 sum[g] = cadd(sum[g], r);
                 h[g] = make_float2(0.f, 0.f);
             }
@@ -459,8 +472,8 @@ __global__ void __launch_bounds__(kColThreads, 6) k_colstack(const __grid_consta
         const int64_t pix = (int64_t)y * n + x;
         float2 r = sum[g];
         if ((x + y) & 1) r = make_float2(-r.x, -r.y);  // fftshift sign (-1)^(x + y)
-        const PixelScreen ps = pixel_screen(a, x, y);
-        if (!ps.sky) r = make_float2(0.f, 0.f);
+        if (!((sky >> g) & 1u)) r = make_float2(0.f, 0.f);
+        const float nm1 = snm1[g * kColThreads + t];
         if (!a.first) {
             const float2 prev = acc[pix];
             r.x += prev.x;
@@ -472,8 +485,8 @@ __global__ void __launch_bounds__(kColThreads, 6) k_colstack(const __grid_consta
         }
         float f = inv_sw;
         if (a.flags & RICK_GRID_CORRECT) f = f / (__ldg(taper + x) * __ldg(taper + y));
-        if (a.flags & RICK_APPLY_N) f *= 1.0f + ps.nm1;
-        if (a.wcorr) f /= wcorr_at(a, ps.nm1);
+        if (a.flags & RICK_APPLY_N) f *= 1.0f + nm1;
+        if (a.wcorr) f /= wcorr_at(a, nm1);
         if (a.flags & RICK_REAL_IMAGE)
             reinterpret_cast<float*>(image)[pix] = r.x * f;
         else

@@ -261,20 +261,3 @@ def test_bounded_wait_times_out_and_handle_recovers(rick):
         im.stats()
         assert np.max(np.abs(got - want)) <= 1e-5 * np.max(np.abs(want))
     im.close()
-
-
-@pytest.mark.parametrize("n,nw,extra", [(8192, 5, {}), (16384, 3, {}), (16384, 5, {"plane_group": 2})])
-def test_own_row_kernel_equals_cufft_rows(rick, n, nw, extra):
-    """At n = 8192 and 16384 the split transform's rows run in the library's
-    one-pass kernel (k_rowfft): the image equals the one with cuFFT's rows
-    (RICK_FFT_CUFFT_ROWS), and so does the adjoint (both FP32
-    factorisations of the same DFT)."""
-    prob = synth.config2(m=300000, n=n, nw=nw)
-    a, _ = _image(rick, prob, CORRECT | REAL | rick.FFT_SPLIT, **extra)
-    b, _ = _image(rick, prob, CORRECT | REAL | rick.FFT_SPLIT | rick.FFT_CUFFT_ROWS, **extra)
-    assert np.max(np.abs(a - b)) <= 1e-5 * np.max(np.abs(b))
-    rng = np.random.default_rng(23)
-    r = rng.standard_normal((n, n)).astype(np.float32)
-    ga = _degrid(rick, prob, CORRECT | REAL | rick.FFT_SPLIT, r, **extra)
-    gb = _degrid(rick, prob, CORRECT | REAL | rick.FFT_SPLIT | rick.FFT_CUFFT_ROWS, r, **extra)
-    assert np.max(np.abs(ga - gb)) <= 1e-4 * np.max(np.abs(gb))

@@ -160,75 +160,3 @@ def test_colfft_block_positions_are_a_permutation():
             reads = sorted(q * k1 + r * c1 + c2 for k1 in range(16) for c2 in range(r) for c1 in range(16))
             writes = sorted(q * k1 + 16 * c2 + j1 for k1 in range(16) for c2 in range(r) for j1 in range(16))
             assert reads == writes == list(range(n1))
-
-
-# -------------------------------------------------------------------------
-# The one-pass row transform as k_rowfft computes it (n = 8192, 16384): four
-# passes over one row in shared memory, blocks of Q1 = n / 16 padded by one
-# element, written out with the kernel's positions and thread roles.
-
-def rowfft_row(x, sign):
-    n = x.size
-    q1, q2 = n // 16, n // 256
-    r = q2 // 16
-    tw = np.exp(sign * 2j * np.pi * np.arange(n) / n)
-    pad = lambda p: p + p // q1  # noqa: E731
-    buf = np.zeros(n + 16, complex)
-    buf[:n] = x                                          # the bulk copy, natural order
-    new = {}
-    for a in range(q1):                                  # pass 1: thread a'
-        v = _dft(buf[[q1 * a1 + a for a1 in range(16)]], sign)
-        for k in range(16):
-            new[pad(q1 * k + a)] = v[k] * tw[a * k]
-    for pos, val in new.items():
-        buf[pos] = val
-    new = {}
-    for k1 in range(16):                                 # pass 2: thread (k1, a'')
-        for u in range(q2):
-            base = pad(q1 * k1) + u
-            v = _dft(buf[[base + q2 * a2 for a2 in range(16)]], sign)
-            for k in range(16):
-                new[base + q2 * k] = v[k] * tw[16 * u * k]
-    for pos, val in new.items():
-        buf[pos] = val
-    new = {}
-    for k1 in range(16):                                 # pass 3: thread (k1, k2, a''')
-        for u in range(q2):
-            k2, a3p = u % 16, u // 16
-            base = pad(q1 * k1) + q2 * k2 + a3p
-            v = _dft(buf[[base + r * a3 for a3 in range(16)]], sign)
-            for k in range(16):
-                new[base + r * k] = v[k] * tw[256 * a3p * k]
-    for pos, val in new.items():
-        buf[pos] = val
-    out = np.empty(n, complex)
-    for k1 in range(16):                                 # pass 4: groups (k1, k2, k3)
-        for gi in range(256):
-            base = pad(q1 * k1) + q2 * (gi % 16) + r * (gi // 16)
-            v = _dft(buf[base:base + r], sign)
-            for k4 in range(r):
-                out[k1 + 16 * gi + 4096 * k4] = v[k4]
-    return out
-
-
-@pytest.mark.parametrize("n", [8192, 16384])
-@pytest.mark.parametrize("sign", [1, -1])
-def test_rowfft_passes_are_the_row_dft(n, sign):
-    rng = np.random.default_rng(n + (sign > 0))
-    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
-    ref = np.fft.ifft(x) * n if sign > 0 else np.fft.fft(x)
-    assert np.max(np.abs(rowfft_row(x, sign) - ref)) <= 1e-10 * np.max(np.abs(ref))
-
-
-@pytest.mark.parametrize("n", [8192, 16384])
-def test_rowfft_twiddle_tables_cover_the_exponents(n):
-    """w_n^e = lo[e % 128] hi[e // 128] for every exponent the passes use."""
-    q1, q2 = n // 16, n // 256
-    r = q2 // 16
-    es = {a * k for a in range(q1) for k in range(16)} | {16 * u * k for u in range(q2) for k in range(16)} | \
-        {256 * a * k for a in range(r) for k in range(16)}
-    assert max(es) < min(n, 128 * 128)
-    lo = np.exp(2j * np.pi * np.arange(128) / n)
-    hi = np.exp(2j * np.pi * 128 * np.arange(128) / n)
-    e = np.array(sorted(es))
-    assert np.max(np.abs(lo[e % 128] * hi[e // 128] - np.exp(2j * np.pi * e / n))) < 1e-12

@@ -668,7 +668,7 @@ def run_image(args, rank, world):
         "energy_j_per_solution": energy, "e2e": e2e, "cpu_baseline": cpu, "parity": parity,
         "gpu_launches": int(tm["kernel_launches"]), "clocks": clk,
         "launch": {"tile": st["tile"], "plane_group": st["plane_group"], "plane_groups": groups,
-                   "planes_of_rank0": [k0, k1]},
+                   "planes_of_rank0": [k0, k1], "workspace_gb": st["workspace_bytes"] / 1e9},
     }
     if rank == 0:
         print(json.dumps(out))

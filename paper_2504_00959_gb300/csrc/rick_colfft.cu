@@ -204,12 +204,12 @@ __device__ __forceinline__ void colfft_two_pass(float2* __restrict__ buf, const 
     } else {
         // Q = 16 r.  Pass B1: the warp owning block k1 (Q rows) runs 16-point
         // DFTs over c1 (rows Q k1 + r c1 + c2), times w_Q^(c2 j1), and stores
-        // them transposed, row Q k1 + 16 c2 + (j1 ^ c2): the XOR puts the r
-        // values of one j1 in r different (row mod r) slots, so the half warps
-        // of this pass (W columns x r values of c2) and of pass B2 (W columns x
-        // r consecutive j1) each touch r consecutive rows' worth of banks
+        // them transposed, row Q k1 + 16 c2 + (j1 ^ c2): the XOR puts the
+        // values of one j1 in different (row mod r) slots, so the half warps
+        // of this pass (W columns x 2 values of c2) and of pass B2 (W columns
+        // x 2 consecutive j1) each touch two adjacent rows' worth of banks
         constexpr int r = Q / 16;
-        static_assert(r * W == 32 || r * W == 16, "one warp (or half) per block of Q rows");
+        static_assert(r * W * 16 == 16 * 32 || r * W * 16 == 16 * 16, "one warp (or half) per block of Q rows");
         constexpr int kLanesPerBlock = r * W;  // 32 or 16
         const int lane = t & 31, wid = t >> 5;
         const int sub = lane / kLanesPerBlock, l = lane % kLanesPerBlock;
@@ -245,96 +245,67 @@ __device__ __forceinline__ void colfft_two_pass(float2* __restrict__ buf, const 
     }
 }
 
-// Persistent: grid = blocks resident on the GPU; block j takes the tiles
-// j, j + gridDim.x, ... of the group (tile = (strip of W columns, b, plane),
-// strips fastest, so blocks running together read adjacent strips of the
-// same rows).  Dynamic shared memory: two tile buffers of N1 * W complex
-// values, the N1 twiddles and two mbarriers; the copy of tile i + 1 is
-// issued into the other buffer as soon as tile i's data has arrived, so a
-// load is always in flight while a tile is transformed.  tw: exp(+2 pi i j /
-// N1), j < N1 (device; copied in with the first tile).  err: bit 1 set when a
-// load wait ran out.
+// grid (n / W, 16, planes of the group); block kCfThreads; dynamic shared
+// memory N1 * W complex values, the N1 twiddles and one mbarrier.  tw:
+// exp(+2 pi i j / N1), j < N1 (device; copied in with the block's data).
+// err: bit 1 set when the load wait ran out.
 template <int N1, int W, int SIGN>
-__global__ void __launch_bounds__(kCfThreads, 3) k_colfft(const __grid_constant__ CUtensorMap map,
+__global__ void __launch_bounds__(kCfThreads) k_colfft(const __grid_constant__ CUtensorMap map,
                                                        const float2* __restrict__ tw, float2* __restrict__ planes,
-                                                       int n, int64_t ntiles, unsigned long long wait_ns,
+                                                       int n, unsigned long long wait_ns,
                                                        unsigned long long* __restrict__ err)
 {
     constexpr int kBox = N1 < kCfBoxRows ? N1 : kCfBoxRows;
-    constexpr uint32_t kTileBytes = (uint32_t)(N1 * W * sizeof(float2));
     extern __shared__ __align__(128) unsigned char cf_smem[];
-    float2* bufs = reinterpret_cast<float2*>(cf_smem);  // [2][N1][W]
-    float2* tws = bufs + (size_t)2 * N1 * W;            // [N1] twiddles
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(tws + N1);  // [2]
+    float2* buf = reinterpret_cast<float2*>(cf_smem);  // [N1][W]
+    float2* tws = buf + (size_t)N1 * W;                 // [N1] twiddles
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(tws + N1);
     __shared__ int s_abort;
 
     const int t = threadIdx.x;
-    const int nstrips = n / W;
+    const int x0 = blockIdx.x * W, b = blockIdx.y, plane = blockIdx.z;
     const unsigned long long limit = wait_ns ? wait_ns : kCfWaitNs;
-    int64_t tile = blockIdx.x;
-    if (tile >= ntiles) return;
-    auto issue = [&](int64_t tl, int slot, uint32_t extra) {  // thread 0
-        const int strip = (int)(tl % nstrips);
-        const int b = (int)((tl / nstrips) & 15);
-        const int plane = (int)(tl / ((int64_t)nstrips * 16));
-        const uint32_t bb = smem_u32(bar + slot);
-        mbar_expect(bb, kTileBytes + extra);
-        float2* dst = bufs + (size_t)slot * N1 * W;
-#pragma unroll
-        for (int a0 = 0; a0 < N1; a0 += kBox)
-            tma_load_3d(smem_u32(dst + (size_t)a0 * W), &map, strip * W, b, plane * N1 + a0, bb);
-    };
     if (t == 0) {
         s_abort = 0;
         mbar_init(smem_u32(bar), 1);
-        mbar_init(smem_u32(bar + 1), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        issue(tile, 0, (uint32_t)(N1 * sizeof(float2)));
-        bulk_load(smem_u32(tws), tw, (uint32_t)(N1 * sizeof(float2)), smem_u32(bar));
     }
     __syncthreads();
-    uint32_t phase = 0;  // bit s: parity of buffer s's next completion
-    int s = 0;
-    for (; tile < ntiles; tile += gridDim.x) {
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(bar + s), (phase >> s) & 1u, &s_abort, limit));
-        if (!ok) s_abort = 1;
-        __syncthreads();
-        if (s_abort) break;
-        phase ^= 1u << s;
-        // the other buffer was released by the __syncthreads closing the
-        // previous tile: bring the next tile in while this one is transformed
-        if (t == 0 && tile + gridDim.x < ntiles) issue(tile + gridDim.x, s ^ 1, 0);
-        const int strip = (int)(tile % nstrips);
-        const int b = (int)((tile / nstrips) & 15);
-        const int plane = (int)(tile / ((int64_t)nstrips * 16));
-        float2* buf = bufs + (size_t)s * N1 * W;
-        float2* P = planes + (size_t)plane * n * n + (size_t)strip * W;
-        if constexpr (N1 < 16) {
-            // a single N1-point DFT per column (n = 64, 128)
-            for (int it = t; it < W; it += kCfThreads) {
-                float2 v[N1];
+    if (t == 0) {
+        mbar_expect(smem_u32(bar), (uint32_t)((N1 * W + N1) * sizeof(float2)));
 #pragma unroll
-                for (int a = 0; a < N1; ++a) v[a] = buf[a * W + it];
-                dft_small<N1, SIGN>(v);
-#pragma unroll
-                for (int f1 = 0; f1 < N1; ++f1) P[(size_t)(16 * f1 + b) * n + it] = v[f1];
-            }
-        } else {
-            colfft_two_pass<N1, W, SIGN>(buf, tws, P, n, b, t);
-        }
-        __syncthreads();  // this buffer's reads are done: it may be refilled
-        s ^= 1;
+        for (int a0 = 0; a0 < N1; a0 += kBox)
+            tma_load_3d(smem_u32(buf + (size_t)a0 * W), &map, x0, b, plane * N1 + a0, smem_u32(bar));
+        bulk_load(smem_u32(tws), tw, (uint32_t)(N1 * sizeof(float2)), smem_u32(bar));
     }
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(bar), 0, &s_abort, limit));
+    if (!ok) s_abort = 1;
+    __syncthreads();
     if (s_abort) {
-        // leave no bulk copy in flight into this block's shared memory: the
-        // one this wait gave up on (the other buffer's copy is not issued yet)
+        // leave no bulk copy in flight into this block's shared memory
         if (t == 0) {
             atomicOr(err, 2ull);
             const unsigned long long t0 = global_ns();
-            while (!mbar_try(smem_u32(bar + s), (phase >> s) & 1u) && global_ns() - t0 <= limit) {
+            while (!mbar_try(smem_u32(bar), 0) && global_ns() - t0 <= limit) {
             }
         }
         __syncthreads();
+        return;
+    }
+
+    float2* P = planes + (size_t)plane * n * n + x0;
+    if constexpr (N1 < 16) {
+        // a single N1-point DFT per column (n = 64, 128)
+        for (int it = t; it < W; it += kCfThreads) {
+            float2 v[N1];
+#pragma unroll
+            for (int a = 0; a < N1; ++a) v[a] = buf[a * W + it];
+            dft_small<N1, SIGN>(v);
+#pragma unroll
+            for (int f1 = 0; f1 < N1; ++f1) P[(size_t)(16 * f1 + b) * n + it] = v[f1];
+        }
+    } else {
+        colfft_two_pass<N1, W, SIGN>(buf, tws, P, n, b, t);
     }
 }
 
@@ -342,44 +313,35 @@ template <int N1, int W, int SIGN>
 cudaError_t launch_cf(const void* map, const float2* tw, float2* planes, int n, int nk, unsigned long long wait_ns,
                       unsigned long long* err, cudaStream_t s)
 {
-    const size_t smem = (size_t)(2 * N1 * W + N1) * sizeof(float2) + 16;
+    const size_t smem = (size_t)(N1 * W + N1) * sizeof(float2) + 16;
     static bool attr_done[64] = {false};
-    static int blocks_per_sm[64] = {0}, sms[64] = {0};
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (!attr_done[dev]) {
-        cudaError_t e =
+    if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+        const cudaError_t e =
             cudaFuncSetAttribute(k_colfft<N1, W, SIGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm[dev], k_colfft<N1, W, SIGN>, kCfThreads,
-                                                          smem);
-        if (e != cudaSuccess) return e;
-        cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
         attr_done[dev] = true;
     }
-    const int64_t ntiles = (int64_t)nk * 16 * (n / W);
-    const int64_t resident = (int64_t)(blocks_per_sm[dev] > 0 ? blocks_per_sm[dev] : 1) * (sms[dev] > 0 ? sms[dev] : 1);
-    const unsigned grid = (unsigned)(ntiles < resident ? ntiles : resident);
-    k_colfft<N1, W, SIGN><<<grid, kCfThreads, smem, s>>>(*reinterpret_cast<const CUtensorMap*>(map), tw, planes, n,
-                                                        ntiles, wait_ns, err);
+    const dim3 grid((unsigned)(n / W), 16u, (unsigned)nk);
+    k_colfft<N1, W, SIGN><<<grid, kCfThreads, smem, s>>>(*reinterpret_cast<const CUtensorMap*>(map), tw, planes,
+                                                          n, wait_ns, err);
     return cudaGetLastError();
 }
 
-// columns per tile: 128-byte row segments up to N1 = 256, 64 bytes at 512,
-// 32 bytes at 1024 (two 32 KB buffers; blocks on adjacent strips share the
-// 128-byte lines the copies promote into L2)
+// columns per block: 128-byte row segments up to N1 = 256 (32 KB), 64-byte
+// ones for the longer transforms (64 KB at N1 = 1024, three blocks per SM)
 template <int N1>
 constexpr int cf_width()
 {
-    return N1 <= 256 ? 16 : (N1 == 512 ? 8 : 4);
+    return N1 <= 256 ? 16 : 8;
 }
 
 }  // namespace
 
 int colfft_width(int n1)
 {
-    return n1 <= 256 ? 16 : (n1 == 512 ? 8 : 4);
+    return n1 <= 256 ? 16 : 8;
 }
 
 cudaError_t encode_colfft_map(void* map, const float2* planes, int n, int planes_in_buffer)

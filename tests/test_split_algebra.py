@@ -129,12 +129,12 @@ def colfft_block(x, sign):
         for c2 in range(r):
             v = _dft(buf[[q * k1 + r * c1 + c2 for c1 in range(16)]], sign)
             for j1 in range(16):
-                stage[q * k1 + 16 * c2 + j1] = v[j1] * tw[16 * c2 * j1]
+                stage[q * k1 + 16 * c2 + (j1 ^ c2)] = v[j1] * tw[16 * c2 * j1]
         for pos, val in stage.items():                   # written after the warp's reads
             buf[pos] = val
     for k1 in range(16):                                 # pass B2: thread (x, k1, j1)
         for j1 in range(16):
-            v = _dft(buf[[q * k1 + 16 * c2 + j1 for c2 in range(r)]], sign)
+            v = _dft(buf[[q * k1 + 16 * c2 + (j1 ^ c2) for c2 in range(r)]], sign)
             for j2 in range(r):
                 out[k1 + 16 * (j1 + 16 * j2)] = v[j2]
     return out
@@ -158,5 +158,5 @@ def test_colfft_block_positions_are_a_permutation():
         if q > 16:
             r = q // 16
             reads = sorted(q * k1 + r * c1 + c2 for k1 in range(16) for c2 in range(r) for c1 in range(16))
-            writes = sorted(q * k1 + 16 * c2 + j1 for k1 in range(16) for c2 in range(r) for j1 in range(16))
+            writes = sorted(q * k1 + 16 * c2 + (j1 ^ c2) for k1 in range(16) for c2 in range(r) for j1 in range(16))
             assert reads == writes == list(range(n1))

@@ -508,8 +508,16 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
     int G = p->plane_group ? p->plane_group : NW;
     if (G > NW) G = NW;
     if (!p->plane_group) {
-        const size_t fit = (size_t)(0.6 * (double)fr) / (pb ? 2 * pb : 1);  // planes + FFT work headroom
+        // planes + cuFFT's work area: the 2D plan may need as much as the
+        // planes, the split transform's row plan far less
+        int n1 = 0, n2 = 0;
+        const bool split = !h->batch && use_split(*p, &n1, &n2);
+        const size_t fit = split ? (size_t)(0.7 * (double)fr) / (pb ? pb : 1)
+                                 : (size_t)(0.6 * (double)fr) / (pb ? 2 * pb : 1);
         if ((size_t)G > fit) G = (int)(fit > 0 ? fit : 1);
+        // groups of equal size (no short last group)
+        const int ngroups = (NW + G - 1) / G;
+        G = (NW + ngroups - 1) / ngroups;
     }
     if (h->batch) G = (G / c.nw_chan > 0 ? G / c.nw_chan : 1) * c.nw_chan;
     h->G = G;

@@ -347,7 +347,7 @@ rick_status grid_pass(rick_handle h, int k0, int nk, bool shift, float2* planes)
         }
         // the heavy-chunk list (used when the pass has one chunk) is sized
         // for that chunk's entry bound, stream-ordered from the pool
-        const size_t words = cl.count == 1 ? heavy_words_for(h->chunks[c0].cap) : 2;
+        const size_t words = cl.count == 1 ? heavy_words_for(h->chunks[c0].cap) : 1;
         uint32_t* heavy = nullptr;
         RICK_CU(h, cudaMallocFromPoolAsync((void**)&heavy, words * sizeof(uint32_t), h->pool, h->stream));
         const cudaError_t e = launch_grid(h->cfg, cl, k0, nk, shift, c0 > 0, heavy, words, planes, h->stream);

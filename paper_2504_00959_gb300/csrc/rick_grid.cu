@@ -619,7 +619,7 @@ size_t heavy_words_for(int64_t max_entries)
 cudaError_t launch_grid(const GridCfg& c, const ChunkList& ch, int k0, int nk, bool shift_sign,
                         bool accumulate, uint32_t* heavy, size_t heavy_words, float2* planes, cudaStream_t s)
 {
-    if (!heavy || heavy_words < 2) return cudaErrorInvalidValue;
+    if (!heavy || heavy_words < 1) return cudaErrorInvalidValue;
     switch (c.S) {
 #define RICK_GRID_CASE(SS) \
     case SS: return launch_grid_s<SS>(c, ch, k0, nk, shift_sign, accumulate, planes, heavy, heavy_words, s);

@@ -227,10 +227,11 @@ cudaError_t launch_scan(const uint32_t* counts, int64_t len, int stride, uint32_
 cudaError_t launch_scatter(const GridCfg& c, const float* u, const float* v, const float* w,
                            const float* wt, const float2* vis, int64_t m, const uint32_t* density,
                            uint32_t* cursor, float4* entries, Counters* ctr, double* chan_sw, cudaStream_t s);
-// heavy: scratch of heavy_words >= 2 words for the list of heavily populated
-// tiles (a count, a cursor, one word per tile; a tile that does not fit is
-// gridded by one warp, correct but slower).  heavy_words_for() gives the
-// size that never overflows for a pass over at most max_entries entries.
+// heavy: scratch of 1 + nk * ntp uint32 (count + list of tiles with many entries)
+// heavy: scratch of heavy_words words for the list of chunks of heavily
+// populated tiles (1 + 2 per chunk; a tile that does not fit is gridded by
+// one warp, correct but slower).  heavy_words_for() gives the size that never
+// overflows for a pass over at most max_entries entries.
 cudaError_t launch_grid(const GridCfg& c, const ChunkList& chunks, int k0, int nk, bool shift_sign,
                         bool accumulate, uint32_t* heavy, size_t heavy_words, float2* planes, cudaStream_t s);
 size_t heavy_words_for(int64_t max_entries);

@@ -21,14 +21,11 @@
 //   * a __syncwarp between entries orders one entry's stores before the next
 //     entry's loads.
 // Tiles with more than heavy_threshold() entries (the dense centre of the uv
-// plane) would serialise on one warp: k_grid_tiles lists them, and
-// k_grid_heavy gives each one to a thread-block cluster of kHeavyCluster
-// blocks: every warp of the cluster grids an equal share of the tile's
-// entries into its own shared-memory copy of the tile, and after a cluster
-// barrier each block sums its slice of the tile's rows over all the warps'
-// copies through distributed shared memory and writes it to the plane once
-// (no atomics on the grid, global or shared).  The fftshift checkerboard
-// (-1)^(ju+jv) is folded into the tap signs.
+// plane) would serialise on one warp: k_grid_tiles writes them as zeros and
+// lists them as chunks of at most that many entries, and k_grid_chunks
+// gives every chunk to a warp, which adds its private tile into the plane
+// with vector atomic adds.  The fftshift checkerboard (-1)^(ju+jv) is folded
+// into the tap signs.
 #include "rick_internal.cuh"
 
 namespace rick {
@@ -43,6 +40,20 @@ constexpr uint32_t kHeavyMin = 64;
 constexpr uint32_t kHeavyMax = 768;
 constexpr uint32_t kHeavyDiv = 16384;
 constexpr int kTilesPerWarp = 8;
+
+int sm_count_grid()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 1;
+    }
+    return cached[dev];
+}
 
 // A shared-memory tile is T rows of cell pairs (16-byte float4 units) with a
 // row pitch of P2 >= T/2 pairs, P2 = 4 (mod 8): the 8 lanes of each phase of
@@ -400,16 +411,24 @@ __global__ void __launch_bounds__(256) k_grid_tiles(GridCfg c, ChunkList ch, int
         for (int o = 16; o > 0; o >>= 1) nent += __shfl_xor_sync(0xffffffffu, nent, o);
 
         if (nent > heavy && ch.count == 1) {
-            // many entries: list the tile for k_grid_heavy, which writes all of it
-            uint32_t slot = 0;
-            if (lane == 0) slot = atomicAdd(heavy_list, 1u);
-            slot = __shfl_sync(0xffffffffu, slot, 0);
-            if (slot < heavy_cap) {
-                if (lane == 0) heavy_list[2 + slot] = (uint32_t)tl;
+            // many entries: hand the tile to k_grid_chunks as chunks of at most
+            // `heavy` entries, which add into the plane; the tile starts at
+            // zero unless this pass accumulates onto earlier chunks
+            const uint32_t nchunks = (nent + heavy - 1) / heavy;
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(heavy_list, nchunks);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base + nchunks <= heavy_cap) {
+                for (uint32_t k = lane; k < nchunks; k += 32) {
+                    heavy_list[1 + 2 * (base + k)] = (uint32_t)tl;
+                    heavy_list[2 + 2 * (base + k)] = k;
+                }
+                if (!accumulate) store_tile<true>(c, g, P0, nullptr, lane);
                 continue;
             }
-            // no room in the list (only a caller-sized list can run out): grid
-            // the tile here, on one warp (correct, slower)
+            // no room in the chunk list: mark the reserved slots that do exist
+            // as empty, and grid the tile here (correct, slower)
+            for (uint32_t k = base + lane; k < heavy_cap; k += 32) heavy_list[1 + 2 * k] = 0xffffffffu;
         }
         if (nent == 0) {
             if (!accumulate) store_tile<true>(c, g, P0, nullptr, lane);
@@ -427,130 +446,49 @@ __global__ void __launch_bounds__(256) k_grid_tiles(GridCfg c, ChunkList ch, int
     }
 }
 
-// Blocks per cluster of k_grid_heavy (the portable maximum).
-constexpr int kHeavyCluster = 8;
-
-__device__ __forceinline__ uint32_t cluster_rank()
-{
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-// the shared-memory address `a` of this block as seen in block `rank` of the cluster
-__device__ __forceinline__ uint32_t cluster_map(uint32_t a, uint32_t rank)
-{
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
-    return r;
-}
-
-__device__ __forceinline__ float4 cluster_ld4(uint32_t a)
-{
-    float4 v;
-    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "r"(a)
-                 : "memory");
-    return v;
-}
-
-// all threads of all blocks of the cluster; orders their shared-memory
-// writes before everyone's reads after it
-__device__ __forceinline__ void cluster_sync()
-{
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// The heavy tiles listed by k_grid_tiles (heavy_list = [count, cursor,
-// tiles...]), one at a time per cluster of kHeavyCluster blocks of W warps:
-// the cluster takes the next listed tile (the cursor, advanced by block 0),
-// warp q of the cluster (q = rank W + warp) grids entries [b + q len / Q,
-// b + (q+1) len / Q) of the tile's range into its own zeroed tile copy,
-// then block `rank` sums rows [rank T / kHeavyCluster, ...) of all Q copies
-// (its own through shared memory, the others' through distributed shared
-// memory) and writes them to the plane (adding the plane's values when the
-// pass accumulates).  Every block of the cluster runs the same iterations,
-// each closed by cluster barriers.
+// Chunks of the tiles with many entries: one warp per chunk, private tile in
+// shared memory, flushed into the plane with 16-byte vector atomic adds of
+// the non-zero cell pairs (the tile's cells were zeroed by k_grid_tiles,
+// which ran before on the same stream).
 template <int S>
-__global__ void __launch_bounds__(256) k_grid_heavy(GridCfg c, ChunkList ch, int k0, int shift, int accumulate,
-                                                    float2* __restrict__ planes, uint32_t* __restrict__ heavy_list,
-                                                    uint32_t heavy_cap)
+__global__ void __launch_bounds__(256) k_grid_chunks(GridCfg c, ChunkList ch, int k0, int64_t ntl, int shift,
+                                                     float2* __restrict__ planes,
+                                                     const uint32_t* __restrict__ heavy_list, uint32_t heavy_cap)
 {
     extern __shared__ float4 smem4[];
-    __shared__ uint32_t s_next[2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    const uint32_t rank = cluster_rank();
-    const size_t wbytes = warp_smem_bytes<S>(c.T);
-    unsigned char* mine = reinterpret_cast<unsigned char*>(smem4) + (size_t)wid * wbytes;
+    unsigned char* mine = reinterpret_cast<unsigned char*>(smem4) + (size_t)wid * warp_smem_bytes<S>(c.T);
     float4* tile4 = reinterpret_cast<float4*>(mine);
     Stage<S>& st = *reinterpret_cast<Stage<S>*>(mine + (size_t)c.T * pair_pitch(c.T) * sizeof(float4));
     LaneSlots<S> ls;
     ls.init(lane, pair_pitch(c.T));
-    const uint32_t count = min(__ldcg(heavy_list), heavy_cap);
-    const int P2 = pair_pitch(c.T), TP = c.T / 2;
-    const int Q = kHeavyCluster * nwarps, q = (int)rank * nwarps + wid;
-    const int rows = c.T / kHeavyCluster;  // rows of the tile this block reduces and writes
-    const uint32_t smem_base = (uint32_t)__cvta_generic_to_shared(smem4);
-
-    // block 0 takes the cluster's tiles off the list (the cursor); every
-    // block reads the index from block 0 between two cluster barriers, so no
-    // block leaves, or block 0 rewrites it, while another still reads it
-    auto next_index = [&](int slot) {
-        uint32_t v;
-        const uint32_t a = cluster_map((uint32_t)__cvta_generic_to_shared(s_next + slot), 0);
-        asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
-        return v;
-    };
-    if (rank == 0 && threadIdx.x == 0) s_next[0] = atomicAdd(heavy_list + 1, 1u);
-    cluster_sync();
-    uint32_t idx = next_index(0);
-    cluster_sync();
-    for (uint32_t it = 0; idx < count; ++it) {  // idx is the same in every block of the cluster
-        const int64_t tl = __ldcg(heavy_list + 2 + idx);
+    const uint32_t heavy = heavy_threshold(c, ch, k0, ntl);
+    const uint32_t count = min(heavy_list[0], heavy_cap);
+    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t it = blockIdx.x * (blockDim.x >> 5) + wid; it < count; it += nwarps) {
+        const uint32_t tl32 = heavy_list[1 + 2 * it];
+        if (tl32 == 0xffffffffu) continue;  // slot of a tile gridded by k_grid_tiles itself
+        const int64_t tl = tl32;
+        const uint32_t k = heavy_list[2 + 2 * it];
         const TileGeom g = tile_geom(c, k0, tl);
         float2* P0 = planes + (int64_t)g.kl * c.n * c.n;
-        const uint32_t b0 = __ldg(ch.off[0] + g.tg), e0 = __ldg(ch.off[0] + g.tg + 1);
-        const uint32_t len = e0 - b0;
-        const uint32_t b = b0 + (uint32_t)(((uint64_t)len * q) / Q);
-        const uint32_t e = b0 + (uint32_t)(((uint64_t)len * (q + 1)) / Q);
+        const uint32_t b0 = ch.off[0][g.tg], e0 = ch.off[0][g.tg + 1];
+        const uint32_t b = b0 + k * heavy;
+        const uint32_t e = min(e0, b + heavy);
         init_tile(c, g, P0, tile4, false, lane);
         __syncwarp();
-        if (e > b) warp_grid_range<S>(c, ch.ent[0], b, e, g.u0, g.v0, tile4, st, ls, lane, shift);
-        // block 0 takes the cluster's next tile while the copies are summed
-        if (rank == 0 && threadIdx.x == 0) s_next[(it + 1) & 1] = atomicAdd(heavy_list + 1, 1u);
-        cluster_sync();  // every warp's copy is complete and visible to the cluster
-        const uint32_t idx_next = next_index((it + 1) & 1);
-        // rows [rank rows, (rank + 1) rows) of the tile: pairs (row, pair) over the block's threads
-        for (int k = threadIdx.x; k < rows * TP; k += blockDim.x) {
-            const int row = (int)rank * rows + k / TP, pr = k % TP;
-            const uint32_t off = (uint32_t)(row * P2 + pr) * 16u;
-            float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int r = 0; r < kHeavyCluster; ++r) {
-                const uint32_t base = cluster_map(smem_base, (uint32_t)r);
-                for (int w = 0; w < nwarps; ++w) {
-                    const float4 x = cluster_ld4(base + (uint32_t)(w * wbytes) + off);
-                    sum.x += x.x;
-                    sum.y += x.y;
-                    sum.z += x.z;
-                    sum.w += x.w;
-                }
-            }
-            if (2 * pr < g.wu && row < g.wv) {
-                float4* dst = reinterpret_cast<float4*>(P0 + (int64_t)(g.v0 + row) * c.n + g.u0 + 2 * pr);
-                if (accumulate) {
-                    const float4 o = *dst;
-                    sum.x += o.x;
-                    sum.y += o.y;
-                    sum.z += o.z;
-                    sum.w += o.w;
-                }
-                *dst = sum;
+        warp_grid_range<S>(c, ch.ent[0], b, e, g.u0, g.v0, tile4, st, ls, lane, shift);
+        __syncwarp();
+        const TileWalk w = tile_walk(c, lane);
+        if (2 * w.pr < g.wu) {
+            float4* dst = reinterpret_cast<float4*>(P0 + (int64_t)(g.v0 + w.r0) * c.n + g.u0 + 2 * w.pr);
+            const int64_t step = (int64_t)w.dr * (c.n / 2);
+            for (int row = w.r0; row < g.wv; row += w.dr, dst += step) {
+                const float4 x = tile4[row * w.p2 + w.pr];
+                if (x.x != 0.f || x.y != 0.f || x.z != 0.f || x.w != 0.f) atomicAdd(dst, x);
             }
         }
-        cluster_sync();  // the copies (and the index) are read: they may be rewritten
-        idx = idx_next;
+        __syncwarp();
     }
 }
 
@@ -572,48 +510,35 @@ cudaError_t launch_grid_s(const GridCfg& c, const ChunkList& ch, int k0, int nk,
     const int64_t nblocks = (ntl + wl - 1) / wl;
     if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     // heavy: [count, (tile, chunk) pairs]
-    // heavy: [count, cursor, tile ids]
-    const size_t slots = heavy_words - 2;
-    const uint32_t cap = (uint32_t)(slots < 0x7fffffffu ? slots : 0x7fffffffu);
-    cudaError_t e = cudaMemsetAsync(heavy, 0, 2 * sizeof(uint32_t), s);
+    const size_t pairs = (heavy_words - 1) / 2;
+    const uint32_t cap = (uint32_t)(pairs < 0x7fffffffu ? pairs : 0x7fffffffu);
+    cudaError_t e = cudaMemsetAsync(heavy, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     if ((e = allow_smem(k_grid_tiles<S>, tile_bytes * wl)) != cudaSuccess) return e;
-    if ((e = allow_smem(k_grid_heavy<S>, tile_bytes * wl)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_grid_chunks<S>, tile_bytes * wl)) != cudaSuccess) return e;
     const unsigned tile_blocks = (unsigned)((nblocks + kTilesPerWarp - 1) / kTilesPerWarp);
     k_grid_tiles<S><<<tile_blocks, 32 * wl, tile_bytes * wl, s>>>(c, ch, k0, ntl, shift ? 1 : 0, accumulate ? 1 : 0,
                                                                   planes, heavy, cap);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (ch.count != 1) return cudaSuccess;  // passes over several lists list no heavy tiles
-    // one cluster per heavy tile at a time, as many clusters as fit at once
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = kHeavyCluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.blockDim = dim3(32 * wl);
-    cfg.dynamicSmemBytes = tile_bytes * wl;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cfg.gridDim = dim3(kHeavyCluster);
-    int nclusters = 0;
-    if ((e = cudaOccupancyMaxActiveClusters(&nclusters, (void*)k_grid_heavy<S>, &cfg)) != cudaSuccess) return e;
-    cfg.gridDim = dim3((unsigned)(kHeavyCluster * max(nclusters, 1)));
-    e = cudaLaunchKernelEx(&cfg, k_grid_heavy<S>, c, ch, k0, shift ? 1 : 0, accumulate ? 1 : 0, planes, heavy, cap);
-    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_chunks<S>, 32 * wl, tile_bytes * wl)) !=
+        cudaSuccess)
+        return e;
+    const unsigned nchunk_blocks = (unsigned)(max(per_sm, 1) * sm_count_grid());
+    k_grid_chunks<S><<<nchunk_blocks, 32 * wl, tile_bytes * wl, s>>>(c, ch, k0, ntl, shift ? 1 : 0, planes, heavy,
+                                                                    cap);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-// A heavy tile holds more than h >= kHeavyMin entries, so a pass over E
-// entries lists fewer than E / kHeavyMin of them (plus the count and the
-// cursor).
+// Every chunk holds more than h / 2 entries on average for a threshold h
+// (a heavy tile of n > h entries makes ceil(n / h) < 2 n / h chunks), so a
+// pass over E entries lists fewer than 2 E / h <= 2 E / kHeavyMin chunks.
 size_t heavy_words_for(int64_t max_entries)
 {
-    const int64_t tiles = max_entries / kHeavyMin + 1;
-    return 2 + (size_t)(tiles > 0 ? tiles : 1);
+    const int64_t chunks = 2 * max_entries / kHeavyMin + 1;
+    return 1 + 2 * (size_t)(chunks > 0 ? chunks : 1);
 }
 
 cudaError_t launch_grid(const GridCfg& c, const ChunkList& ch, int k0, int nk, bool shift_sign,

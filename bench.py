@@ -695,9 +695,10 @@ def run_channels(args, rank, world):
     offs = prob["offsets"]
     nchan, n = len(prob["ranges"]), q["n"]
     m = offs[-1]
-    tile, group, tune_ms = rick.autotune_batch(q, prob["ranges"], prob["vis"], prob["u"], prob["v"], prob["w"],
-                                               prob["wt"], offs)
+    tile, group, prep_blocks, tune_ms = rick.autotune_batch(q, prob["ranges"], prob["vis"], prob["u"], prob["v"],
+                                                            prob["w"], prob["wt"], offs)
     bi = rick.BatchImager(dict(q, tile=tile, plane_group=group), prob["ranges"])
+    bi.set_prep_blocks(prep_blocks)
     out = torch.empty((nchan, n, n), device=dev)
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
@@ -731,19 +732,36 @@ def run_channels(args, rank, world):
             im.grid(prob["vis"][a:b], prob["u"][a:b], prob["v"][a:b], prob["w"][a:b], prob["wt"][a:b])
             im.image(out=loop_out[c])
 
-    for _ in range(max(args.warmup, 1)):
-        loop_step()
-    torch.cuda.synchronize()
     ksteps = max(1, min(args.steps, 10))
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    k0 = nvml.energy_mj() if nvml else None
-    f0.record()
-    for _ in range(ksteps):
-        loop_step()
-    f1.record()
-    torch.cuda.synchronize()
-    k1 = nvml.energy_mj() if nvml else None
-    t_loop = f0.elapsed_time(f1) / ksteps
+
+    def time_loop():
+        for _ in range(max(args.warmup, 1)):
+            loop_step()
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0 = nvml.energy_mj() if nvml else None
+        f0.record()
+        for _ in range(ksteps):
+            loop_step()
+        f1.record()
+        torch.cuda.synchronize()
+        k1 = nvml.energy_mj() if nvml else None
+        return f0.elapsed_time(f1) / ksteps, k0, k1
+
+    # the per-channel loop with the library's default single-image path, and
+    # with the split transform (the batch's); the faster one is the reference
+    t_loop, k0, k1 = time_loop()
+    loop_default = loop_out.clone()
+    for im in ims:
+        im.close()
+    ims = [rick.Imager(dict(q, tile=tile, w_min=lo, w_max=hi, flags=q["flags"] | rick.FFT_SPLIT))
+           for (lo, hi) in prob["ranges"]]
+    t_loop_split, s0, s1 = time_loop()
+    loop_kind = "default single-image path"
+    if t_loop_split < t_loop:
+        t_loop, k0, k1, loop_kind = t_loop_split, s0, s1, "split transform"
+    else:
+        loop_out.copy_(loop_default)
     err = max(((batch_img[c] - loop_out[c]).abs().max() / loop_out[c].abs().max().clamp_min(1e-30)).item()
               for c in range(nchan))
     e_batch = (j1 - j0) / 1e3 / args.steps if j0 is not None and j1 is not None else None
@@ -761,8 +779,10 @@ def run_channels(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch, "dtype": "f32",
             "data": "synthetic: 64 channels of an Earth-rotation synthesis, N(0,1) visibilities + a central source",
             "config": {"workload": "64 channels x 2048^2 x 16 w-planes, 1e6-2e7 visibilities per channel",
-                       "nvis": m, "tile": tile, "plane_group": group, "autotune_ms": tune_ms},
-            "loop_ms_per_step": t_loop, "speedup_vs_loop": t_loop / t_batch,
+                       "nvis": m, "tile": tile, "plane_group": group, "prep_blocks_per_sm": prep_blocks or 8,
+                       "autotune_ms": tune_ms},
+            "loop_ms_per_step": t_loop, "loop_path": loop_kind, "speedup_vs_loop": t_loop / t_batch,
+            "loop_ms_default_path": t_loop if loop_kind != "split transform" else None,
             "max_rel_diff_batch_vs_loop": err, "energy_j_batch": e_batch, "energy_j_loop": e_loop,
             "green_productivity_eq4": gp}))
 

@@ -231,6 +231,10 @@ rick_status rick_synchronize(rick_handle h);
  * rick_destroy apply to a batched handle. */
 rick_status rick_create_batch(const rick_params* p, int32_t nchan, const double* w_min, const double* w_max,
                               rick_handle* out);
+/* (Batched handles transform their plane groups like single images from
+ * n = 1024 on -- cuFFT's rows, the library's first column factor, and the
+ * last column factor fused with each channel's w-screen and stack -- and
+ * with cuFFT's 2D plan and a separate stack below, or with RICK_FFT_2D.) */
 
 /* One dirty image per channel: channel c's measurements are entries
  * chan_offsets[c] .. chan_offsets[c+1]-1 (host array of nchan+1, starting at
@@ -249,17 +253,28 @@ rick_status rick_create_batch(const rick_params* p, int32_t nchan, const double*
 rick_status rick_image_batch(rick_handle h, const float* vis, const float* u, const float* v, const float* w,
                              const float* weights, const int64_t* chan_offsets, float* images, int32_t use_graph);
 
-/* Autotuner for batched imaging: times one rick_image_batch of the given data
- * for every tile side (16, 32, 64, at least the support) and plane group
- * (all channels, half, a quarter of them) and returns the fastest in *tile_out and
- * *plane_group_out (device time in *ms_out, may be NULL).  When the
- * environment variable RICK_AUTOTUNE_CACHE names a file, results are looked
- * up there first and appended after tuning (key: n, nw, nchan, support,
- * kernel, flags, log2 of the measurement count). */
+/* Autotuner for batched imaging: times rick_image_batch of the given data
+ * (the median of three steps after one untimed step) for every tile side
+ * (16, 32, 64, at least the support) and plane group (all channels, half, a
+ * quarter of them), then, on the fastest of those, the measurements per
+ * block of the sort kernels (rick_set_prep_blocks: 8 -- the default, 0 --
+ * against 4, 16 and 32 blocks per SM), and returns the fastest in *tile_out,
+ * *plane_group_out and *prep_blocks_out (may be NULL; 0 = the default), the
+ * device time in *ms_out (may be NULL).  When the environment variable
+ * RICK_AUTOTUNE_CACHE names a file, results are looked up there first and
+ * appended after tuning (key: the device's name and SM count, this build of
+ * the library, n, nw, nchan, support, kernel, flags, log2 of the
+ * measurement count). */
 rick_status rick_autotune_batch(const rick_params* p, int32_t nchan, const double* w_min, const double* w_max,
                                 const float* vis, const float* u, const float* v, const float* w,
                                 const float* weights, const int64_t* chan_offsets, int32_t* tile_out,
-                                int32_t* plane_group_out, double* ms_out);
+                                int32_t* plane_group_out, int32_t* prep_blocks_out, double* ms_out);
+
+/* Blocks per SM of the sort kernels (placement + counting sort) of this
+ * handle, i.e. how many measurements each block takes: M / (SMs x
+ * blocks_per_sm); 0 = the default 8, at most 64.  A batched handle re-captures
+ * its graph on the next call.  RICK_ERR_ARG outside [0, 64]. */
+rick_status rick_set_prep_blocks(rick_handle h, int32_t blocks_per_sm);
 
 /* Eq. 3 alone for one set of measurements, into caller-provided planes,
  * WITHOUT allocating any device memory.  The paper has no counterpart.  It is

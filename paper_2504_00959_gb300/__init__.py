@@ -216,6 +216,10 @@ class Imager:
         """Wait for everything enqueued on this imager (rick_synchronize)."""
         _lib.check(self._L.rick_synchronize(self._h), self._h)
 
+    def set_prep_blocks(self, blocks_per_sm):
+        """Blocks per SM of the sort kernels (rick_set_prep_blocks; 0 = default)."""
+        _lib.check(self._L.rick_set_prep_blocks(self._h, int(blocks_per_sm)), self._h)
+
     def set_plane_range(self, k0, k1):
         """Grid, transform and stack only w-planes k0 .. k1-1 (rick_set_plane_range);
         call before grid (after reset)."""
@@ -304,19 +308,20 @@ class BatchImager(Imager):
 
 
 def autotune_batch(params, w_ranges, vis, u, v, w, wt, chan_offsets):
-    """Tile side and plane group for batched imaging of this data, timed on
-    the GPU (see rick_autotune_batch).  Returns (tile, plane_group, ms)."""
+    """Tile side, plane group and sort blocks per SM for batched imaging of
+    this data, timed on the GPU (see rick_autotune_batch).  Returns (tile,
+    plane_group, prep_blocks, ms); prep_blocks 0 = the default."""
     L = _lib.load()
     nchan = len(w_ranges)
     rp = _params_struct(params)
     wmin = (ctypes.c_double * nchan)(*[float(a) for a, _ in w_ranges])
     wmax = (ctypes.c_double * nchan)(*[float(b) for _, b in w_ranges])
     offs = (ctypes.c_int64 * (nchan + 1))(*[int(x) for x in chan_offsets])
-    t, g, ms = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0.0)
+    t, g, pb, ms = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0.0)
     _lib.check(L.rick_autotune_batch(ctypes.byref(rp), nchan, wmin, wmax, _ptr(vis), _ptr(u), _ptr(v), _ptr(w),
                                      _ptr(wt), ctypes.cast(offs, ctypes.c_void_p), ctypes.byref(t), ctypes.byref(g),
-                                     ctypes.byref(ms)))
-    return t.value, g.value, ms.value
+                                     ctypes.byref(pb), ctypes.byref(ms)))
+    return t.value, g.value, pb.value, ms.value
 
 
 class DirtyImage(torch.autograd.Function):

@@ -72,7 +72,8 @@ SIGNATURES = {
     "rick_image_batch": (_S, [_H, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int32]),
     "rick_autotune_batch": (_S, [ctypes.POINTER(RickParams), ctypes.c_int32, _P, _P, _P, _P, _P, _P, _P, _P,
                                  ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
-                                 ctypes.POINTER(ctypes.c_double)]),
+                                 ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
+    "rick_set_prep_blocks": (_S, [_H, ctypes.c_int32]),
     "rick_grid_planes_static": (_S, [ctypes.POINTER(RickParams), _P, _P, _P, _P, _P, ctypes.c_int64, _P, _P,
                                      ctypes.c_char_p, ctypes.c_size_t]),
     "rick_set_plane_range": (_S, [_H, ctypes.c_int32, ctypes.c_int32]),

@@ -1,7 +1,9 @@
 // rick_api.cu -- the C ABI of librick (include/rick.h): handle, parameter
 // checks, device memory plan, cuFFT plans and the step sequence of the
 // workflow in Sec. 2.1 (grid -> per-plane FFT -> w-correction + reduction).
+#include <algorithm>
 #include <cmath>
+#include <vector>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -179,6 +181,9 @@ enum { kPlan2D = 0, kPlanRows = 1 };
 // (the 2D plan keeps more of a 34 MB plane in L2, and the first column factor
 // costs one cuFFT call per plane), at 4096^2 x 32 planes 8 % faster
 constexpr int kSplitMinN = 4096;
+// the same for batched imaging, where every group is one launch of each
+// kernel (no per-plane calls)
+constexpr int kBatchSplitMinN = 1024;
 
 // The split transform (cuFFT on the rows and the first column factor, the
 // last factor fused with the screen) for single images: n = 4096 by default,
@@ -643,7 +648,11 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
     {
         cufftHandle plan;
         int n1 = 0, n2 = 0;
-        const bool split = !h->batch && use_split(*p, &n1, &n2);
+        // batches take the split from n = 1024 on (one row plan, one
+        // k_colfft launch per group and a fused stack per channel)
+        h->batch_split = h->batch && colstack_shape(p->n, &n1, &n2) && p->n >= kBatchSplitMinN &&
+                         !(p->flags & RICK_FFT_2D);
+        const bool split = h->batch ? h->batch_split : use_split(*p, &n1, &n2);
         const int kind = split ? kPlanRows : kPlan2D;
         s = get_plan(h, G, &plan, kind);
         if (s) return cleanup(s);
@@ -651,6 +660,16 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
             s = get_plan(h, NW % G, &plan, kind);
             if (s) return cleanup(s);
         }
+    }
+    if (h->batch_split) {
+        // twiddles and tensor maps of both plane buffers, outside any capture
+        s = colfft_ready(h);
+        if (s) return cleanup(s);
+        if (encode_colstack_map(h->colmap, h->planes, p->n, h->G) != cudaSuccess) return cleanup(RICK_ERR_CUDA);
+        h->colmap_ready = true;
+        if (h->planes2 && (encode_colstack_map(h->colmap2, h->planes2, p->n, h->G) != cudaSuccess ||
+                           encode_colfft_map(h->cfmap2, h->planes2, p->n, h->G) != cudaSuccess))
+            return cleanup(RICK_ERR_CUDA);
     }
     if (cudaDeviceSynchronize() != cudaSuccess) return cleanup(RICK_ERR_CUDA);
     *out = h;
@@ -1227,21 +1246,58 @@ static rick_status batch_body(rick_handle h, const float* vis, const float* u, c
     }
     const size_t img_floats = (size_t)p.n * p.n * ((p.flags & RICK_REAL_IMAGE) ? 1 : 2);
     const size_t nn = (size_t)p.n * p.n;
+    // the w-screen constants of channel ch
+    auto chan_args = [&](int ch) {
+        const double dw = (p.nw > 1) ? (h->chan_wmax[ch] - h->chan_wmin[ch]) / p.nw
+                                     : (h->chan_wmax[ch] - h->chan_wmin[ch]);
+        StackArgs a{};
+        a.n = p.n;
+        split(p.pixel_rad * p.pixel_rad, &a.dl2_hi, &a.dl2_lo);
+        split(h->chan_wmin[ch] + 0.5 * dw, &a.wb_hi, &a.wb_lo);
+        split(dw, &a.dw_hi, &a.dw_lo);
+        a.flags = p.flags;
+        a.k0 = 0;
+        a.nk = c.nw_chan;
+        a.first = 1;
+        a.last = 1;
+        a.wait_ns = h->dbg_wait_ns;
+        return a;
+    };
+    // the split transform of a group in buffer `buf` (b = 0: planes, 1:
+    // planes2) on stream st: cuFFT's rows, k_colfft, and per channel the
+    // fused last column factor + w-screen + stack (k_colstack)
+    auto split_group = [&](float2* buf, int b, int k0, int nk, cudaStream_t st) -> rick_status {
+        cufftHandle rows;
+        rick_status s = get_plan(h, nk, &rows, kPlanRows);
+        if (s) return s;
+        int n1 = 0, n2 = 0;
+        colstack_shape(p.n, &n1, &n2);
+        {
+            PhaseScope fs(h, kPhaseFft);
+            RICK_FFT(h, cufftSetStream(rows, st));
+            RICK_FFT(h, cufftExecC2C(rows, reinterpret_cast<cufftComplex*>(buf), reinterpret_cast<cufftComplex*>(buf),
+                                     CUFFT_INVERSE));
+        }
+        {
+            PhaseScope cs(h, kPhaseColfft);
+            RICK_CU(h, launch_colfft(b ? h->cfmap2 : h->cfmap, h->cf_tw, buf, p.n, nk, +1, h->dbg_wait_ns,
+                                     &h->ctr->err, st));
+            count_launches(h, 1);
+        }
+        PhaseScope ss(h, kPhaseStack);
+        for (int ch = k0 / c.nw_chan; ch < (k0 + nk) / c.nw_chan; ++ch) {
+            StackArgs a = chan_args(ch);
+            a.plane0 = ch * c.nw_chan - k0;
+            RICK_CU(h, launch_colstack(b ? h->colmap2 : h->colmap, a, n1, n2, nullptr, h->taper, h->chan_sw + ch,
+                                       images + (size_t)ch * img_floats, &h->ctr->err, st));
+            count_launches(h, 1);
+        }
+        return RICK_OK;
+    };
     // stack the channels of the group in planes `buf` (first plane k0) on stream st
     auto stack_group = [&](const float2* buf, int k0, int nk, cudaStream_t st) -> rick_status {
         for (int ch = k0 / c.nw_chan; ch < (k0 + nk) / c.nw_chan; ++ch) {
-            const double dw = (p.nw > 1) ? (h->chan_wmax[ch] - h->chan_wmin[ch]) / p.nw
-                                         : (h->chan_wmax[ch] - h->chan_wmin[ch]);
-            StackArgs a{};
-            a.n = p.n;
-            split(p.pixel_rad * p.pixel_rad, &a.dl2_hi, &a.dl2_lo);
-            split(h->chan_wmin[ch] + 0.5 * dw, &a.wb_hi, &a.wb_lo);
-            split(dw, &a.dw_hi, &a.dw_lo);
-            a.flags = p.flags;
-            a.k0 = 0;
-            a.nk = c.nw_chan;
-            a.first = 1;
-            a.last = 1;
+            StackArgs a = chan_args(ch);
             const float2* pl = buf + (size_t)(ch * c.nw_chan - k0) * nn;
             RICK_CU(h, launch_stack(a, pl, nullptr, h->taper, h->chan_sw + ch, images + (size_t)ch * img_floats, st));
             count_launches(h, 1);
@@ -1274,12 +1330,16 @@ static rick_status batch_body(rick_handle h, const float* vis, const float* u, c
             if (s) return s;
             RICK_CU(h, cudaEventRecord(h->ev_gridded[b], h->stream));
             RICK_CU(h, cudaStreamWaitEvent(h->fft_stream, h->ev_gridded[b], 0));
-            cufftHandle plan;
-            if ((s = get_plan(h, nk, &plan))) return s;
-            RICK_FFT(h, cufftSetStream(plan, h->fft_stream));
-            RICK_FFT(h, cufftExecC2C(plan, reinterpret_cast<cufftComplex*>(buf), reinterpret_cast<cufftComplex*>(buf),
-                                     CUFFT_INVERSE));
-            if ((s = stack_group(buf, k0, nk, h->fft_stream))) return s;
+            if (h->batch_split) {
+                if ((s = split_group(buf, b, k0, nk, h->fft_stream))) return s;
+            } else {
+                cufftHandle plan;
+                if ((s = get_plan(h, nk, &plan))) return s;
+                RICK_FFT(h, cufftSetStream(plan, h->fft_stream));
+                RICK_FFT(h, cufftExecC2C(plan, reinterpret_cast<cufftComplex*>(buf),
+                                         reinterpret_cast<cufftComplex*>(buf), CUFFT_INVERSE));
+                if ((s = stack_group(buf, k0, nk, h->fft_stream))) return s;
+            }
             RICK_CU(h, cudaEventRecord(h->ev_free[b], h->fft_stream));
         }
         // join: the images are complete on the handle's stream
@@ -1293,6 +1353,11 @@ static rick_status batch_body(rick_handle h, const float* vis, const float* u, c
             PhaseScope scope(h, kPhaseGrid);
             rick_status s = grid_group(h->planes, k0, nk);
             if (s) return s;
+        }
+        if (h->batch_split) {
+            rick_status s = split_group(h->planes, 0, k0, nk, h->stream);
+            if (s) return s;
+            continue;
         }
         cufftHandle plan;
         rick_status s = get_plan(h, nk, &plan);
@@ -1399,29 +1464,78 @@ rick_status rick_image_batch(rick_handle h, const float* vis, const float* u, co
     return RICK_OK;
 }
 
+rick_status rick_set_prep_blocks(rick_handle h, int32_t blocks_per_sm)
+{
+    if (!h) return RICK_ERR_ARG;
+    if (blocks_per_sm < 0 || blocks_per_sm > 64)
+        return fail(h, RICK_ERR_ARG, "blocks_per_sm must be in [0, 64] (got %d)", (int)blocks_per_sm);
+    h->cfg.prep_bpsm = blocks_per_sm;
+    if (h->graph) {  // the captured step holds the old launch shape
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    return RICK_OK;
+}
+
+// The median of `reps` timed batch steps of handle h on stream st (after one
+// untimed step), or a negative value when a step fails.
+static double time_batch(rick_handle h, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, const float* vis,
+                         const float* u, const float* v, const float* w, const float* weights,
+                         const int64_t* chan_offsets, float* images, int reps)
+{
+    if (rick_image_batch(h, vis, u, v, w, weights, chan_offsets, images, 0) != RICK_OK) return -1.0;
+    std::vector<float> t;
+    for (int r = 0; r < reps; ++r) {
+        float ms = 0.f;
+        if (cudaEventRecord(e0, st) != cudaSuccess ||
+            rick_image_batch(h, vis, u, v, w, weights, chan_offsets, images, 0) != RICK_OK ||
+            cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+            return -1.0;
+        t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    return t[t.size() / 2];
+}
+
 rick_status rick_autotune_batch(const rick_params* p, int32_t nchan, const double* w_min, const double* w_max,
                                 const float* vis, const float* u, const float* v, const float* w,
                                 const float* weights, const int64_t* chan_offsets, int32_t* tile_out,
-                                int32_t* plane_group_out, double* ms_out)
+                                int32_t* plane_group_out, int32_t* prep_blocks_out, double* ms_out)
 {
     if (!p || !tile_out || !plane_group_out || !chan_offsets || nchan < 1) return RICK_ERR_ARG;
     const int64_t m = chan_offsets[nchan];
-    char key[256];
-    snprintf(key, sizeof(key), "batch n=%d nw=%d nchan=%d S=%d kernel=%d flags=%u m_log2=%d", p->n, p->nw, nchan,
-             p->support, p->kernel, p->flags, m > 0 ? (int)std::log2((double)m) : 0);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return RICK_ERR_CUDA;
+    char devname[64];
+    snprintf(devname, sizeof(devname), "%s", prop.name);
+    for (char* q = devname; *q; ++q)
+        if (*q == ' ' || *q == '|') *q = '_';
+    // the key names the device and this build of the library, so a cache
+    // file never carries a choice across GPUs or library versions
+    char key[384];
+    snprintf(key, sizeof(key),
+             "batch dev=%s sms=%d build=%s_%s n=%d nw=%d nchan=%d S=%d kernel=%d flags=%u m_log2=%d", devname,
+             prop.multiProcessorCount, __DATE__, __TIME__, p->n, p->nw, nchan, p->support, p->kernel, p->flags,
+             m > 0 ? (int)std::log2((double)m) : 0);
+    for (char* q = key; *q; ++q)
+        if (*q == '|') *q = '_';
     const char* cache = getenv("RICK_AUTOTUNE_CACHE");
     if (cache && *cache) {
         FILE* f = fopen(cache, "r");
         if (f) {
-            char line[512];
+            char line[640];
             while (fgets(line, sizeof(line), f)) {
-                int t = 0, g = 0;
+                int t = 0, g = 0, pb = 0;
                 double ms = 0.0;
                 const size_t kl = strlen(key);
                 if (strncmp(line, key, kl) == 0 && line[kl] == '|' &&
-                    sscanf(line + kl + 1, "%d %d %lf", &t, &g, &ms) == 3) {
+                    sscanf(line + kl + 1, "%d %d %d %lf", &t, &g, &pb, &ms) == 4) {
                     *tile_out = t;
                     *plane_group_out = g;
+                    if (prep_blocks_out) *prep_blocks_out = pb;
                     if (ms_out) *ms_out = ms;
                     fclose(f);
                     return RICK_OK;
@@ -1440,9 +1554,11 @@ rick_status rick_autotune_batch(const rick_params* p, int32_t nchan, const doubl
         cudaFree(images);
         return RICK_ERR_CUDA;
     }
+    constexpr int kReps = 3;
     double best = 1e30;
-    int best_t = 0, best_g = 0;
+    int best_t = 0, best_g = 0, best_pb = 0;
     const int tiles[3] = {16, 32, 64};
+    // stage 1: tile side x plane group, each the median of kReps steps
     for (int ti = 0; ti < 3; ++ti) {
         if (tiles[ti] < p->support) continue;
         // plane groups of all channels, half and a quarter of them (with two or
@@ -1456,19 +1572,35 @@ rick_status rick_autotune_batch(const rick_params* p, int32_t nchan, const doubl
             rick_handle h = nullptr;
             if (create_impl(&q, nchan, w_min, w_max, &h) != RICK_OK) continue;
             rick_set_stream(h, st);
-            float ms = 0.f;
-            bool ok = rick_image_batch(h, vis, u, v, w, weights, chan_offsets, images, 0) == RICK_OK &&
-                      cudaEventRecord(e0, st) == cudaSuccess &&
-                      rick_image_batch(h, vis, u, v, w, weights, chan_offsets, images, 0) == RICK_OK &&
-                      cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
-                      cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+            const double ms = time_batch(h, st, e0, e1, vis, u, v, w, weights, chan_offsets, images, kReps);
             const int g = h->G;
             rick_destroy(h);
-            if (ok && ms < best) {
+            if (ms > 0.0 && ms < best) {
                 best = ms;
                 best_t = tiles[ti];
                 best_g = g;
             }
+        }
+    }
+    // stage 2: measurements per block of the sort kernels (blocks per SM),
+    // on the best tile and plane group
+    if (best_t) {
+        rick_params q = *p;
+        q.tile = best_t;
+        q.plane_group = best_g;
+        rick_handle h = nullptr;
+        if (create_impl(&q, nchan, w_min, w_max, &h) == RICK_OK) {
+            rick_set_stream(h, st);
+            const int bpsm[3] = {4, 16, 32};
+            for (int k = 0; k < 3; ++k) {
+                rick_set_prep_blocks(h, bpsm[k]);
+                const double ms = time_batch(h, st, e0, e1, vis, u, v, w, weights, chan_offsets, images, kReps);
+                if (ms > 0.0 && ms < best) {
+                    best = ms;
+                    best_pb = bpsm[k];
+                }
+            }
+            rick_destroy(h);
         }
     }
     cudaEventDestroy(e0);
@@ -1478,11 +1610,12 @@ rick_status rick_autotune_batch(const rick_params* p, int32_t nchan, const doubl
     if (!best_t) return RICK_ERR_CUDA;
     *tile_out = best_t;
     *plane_group_out = best_g;
+    if (prep_blocks_out) *prep_blocks_out = best_pb;
     if (ms_out) *ms_out = best;
     if (cache && *cache) {
         FILE* f = fopen(cache, "a");
         if (f) {
-            fprintf(f, "%s|%d %d %.4f\n", key, best_t, best_g, best);
+            fprintf(f, "%s|%d %d %d %.4f\n", key, best_t, best_g, best_pb, best);
             fclose(f);
         }
     }

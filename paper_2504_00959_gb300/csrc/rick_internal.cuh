@@ -49,6 +49,9 @@ struct GridCfg {
     int Sw;
     float half_sw, wkp, two_over_sw; // Sw/2; Gaussian 1/(2 sigma_w^2) or KB beta_w; 2/Sw
     int fold;                        // RICK_HERMITIAN_FOLD: mirror measurements with w < 0
+    // blocks per SM of the sort kernels (measurements per block = M / (SMs x
+    // this); 0 = 8), one of the batched autotuner's knobs
+    int prep_bpsm;
     // planes this handle grids and transforms: [plane_lo, plane_hi) of the nw
     // (rick_set_plane_range; all by default).  Measurements on other planes
     // are placed, weighted and counted but list no entries.
@@ -259,6 +262,9 @@ struct StackArgs {
     // (0: none), so that every wait on it runs out and the error path runs
     unsigned long long wait_ns;
     int skip_slot1;
+    // k_colstack: the group's first plane in the plane buffer (a channel of a
+    // batch), 0 for single images
+    int plane0;
 };
 // The grid correction in w at a pixel with n - 1 = nm1 (linear interpolation
 // of the table; 1 without w-support).
@@ -360,6 +366,10 @@ struct rick_imager {
     bool colmap_ready;
     alignas(64) unsigned char cfmap[128];   // tensor map of `planes` for k_colfft
     bool cfmap_ready;
+    // batched imaging with the split transform: the same maps for `planes2`
+    bool batch_split;
+    alignas(64) unsigned char colmap2[128];
+    alignas(64) unsigned char cfmap2[128];
     float2* cf_tw;                   // [n / 16] exp(+2 pi i j / (n / 16)) for k_colfft
     struct Chunk {
         uint32_t* off;

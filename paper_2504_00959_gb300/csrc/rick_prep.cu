@@ -32,10 +32,10 @@ int sm_count()
 
 constexpr int kPrepThreads = 256;
 
-int prep_blocks(int64_t m)
+int prep_blocks(int64_t m, int bpsm = 8)
 {
     int64_t want = (m + kPrepThreads - 1) / kPrepThreads;
-    int64_t cap = (int64_t)sm_count() * 8;
+    int64_t cap = (int64_t)sm_count() * (bpsm > 0 ? bpsm : 8);
     if (want > cap) want = cap;
     return (int)(want < 1 ? 1 : want);
 }
@@ -549,7 +549,7 @@ cudaError_t launch_count(const GridCfg& c, const float* u, const float* v, const
                          cudaStream_t s)
 {
     if (m <= 0) return cudaSuccess;
-    k_count<<<prep_blocks(m), kPrepThreads, 0, s>>>(c, Inputs{u, v, w, wt, vis}, m, counts);
+    k_count<<<prep_blocks(m, c.prep_bpsm), kPrepThreads, 0, s>>>(c, Inputs{u, v, w, wt, vis}, m, counts);
     return cudaGetLastError();
 }
 
@@ -570,7 +570,7 @@ cudaError_t launch_scatter(const GridCfg& c, const float* u, const float* v, con
                            uint32_t* cursor, float4* entries, Counters* ctr, double* chan_sw, cudaStream_t s)
 {
     if (m <= 0) return cudaSuccess;
-    k_scatter<<<prep_blocks(m), kPrepThreads, 0, s>>>(c, Inputs{u, v, w, wt, vis}, m, density, cursor,
+    k_scatter<<<prep_blocks(m, c.prep_bpsm), kPrepThreads, 0, s>>>(c, Inputs{u, v, w, wt, vis}, m, density, cursor,
                                                       entries, ctr, chan_sw ? chan_sw : &ctr->sum_w);
     return cudaGetLastError();
 }

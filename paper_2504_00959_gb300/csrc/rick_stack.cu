@@ -353,8 +353,8 @@ __global__ void __launch_bounds__(kColThreads, 6) k_colstack(const __grid_consta
             const int st = i % kColStages;
             const uint32_t bar = smem_u32(full + st);
             mbar_expect(bar, (uint32_t)kColStageBytes);
-            tma_load_2d(smem_u32(stage + (size_t)st * kColN2 * kColPitch), &map, x0, (nk - 1 - i) * n + kColN2 * f1,
-                        bar);
+            tma_load_2d(smem_u32(stage + (size_t)st * kColN2 * kColPitch), &map, x0,
+                        (a.plane0 + nk - 1 - i) * n + kColN2 * f1, bar);
         }
         __syncwarp();
     };

@@ -145,15 +145,27 @@ def test_autotune_batch_and_cache(rick, chans, tmp_path, monkeypatch):
     prob = chans
     cache = tmp_path / "tune.txt"
     monkeypatch.setenv("RICK_AUTOTUNE_CACHE", str(cache))
-    t, g, ms = rick.autotune_batch(dict(prob["params"], flags=REAL), prob["ranges"], prob["vis"], prob["u"],
-                                   prob["v"], prob["w"], prob["wt"], prob["offsets"])
+    t, g, pb, ms = rick.autotune_batch(dict(prob["params"], flags=REAL), prob["ranges"], prob["vis"], prob["u"],
+                                       prob["v"], prob["w"], prob["wt"], prob["offsets"])
     nw = prob["params"]["nw"]
     assert t in (16, 32, 64) and t >= prob["params"]["support"]
-    assert g % nw == 0 and g > 0 and ms > 0
-    assert cache.exists() and str(t) in cache.read_text()
-    t2, g2, ms2 = rick.autotune_batch(dict(prob["params"], flags=REAL), prob["ranges"], prob["vis"], prob["u"],
-                                      prob["v"], prob["w"], prob["wt"], prob["offsets"])
-    assert (t2, g2) == (t, g) and abs(ms2 - ms) < 1e-3
+    assert g % nw == 0 and g > 0 and ms > 0 and pb in (0, 4, 16, 32)
+    text = cache.read_text()
+    assert cache.exists() and str(t) in text
+    import torch as _t
+    assert _t.cuda.get_device_name().replace(" ", "_") in text  # the key names the device
+    t2, g2, pb2, ms2 = rick.autotune_batch(dict(prob["params"], flags=REAL), prob["ranges"], prob["vis"],
+                                           prob["u"], prob["v"], prob["w"], prob["wt"], prob["offsets"])
+    assert (t2, g2, pb2) == (t, g, pb) and abs(ms2 - ms) < 1e-3
+    # the tuned handle images what the default one does
+    bi = rick.BatchImager(dict(prob["params"], flags=REAL, tile=t, plane_group=g), prob["ranges"])
+    bi.set_prep_blocks(pb)
+    a = bi.images(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"], prob["offsets"]).clone()
+    bi.close()
+    ref = rick.BatchImager(dict(prob["params"], flags=REAL), prob["ranges"])
+    b = ref.images(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"], prob["offsets"])
+    ref.close()
+    assert (a - b).abs().max().item() <= 1e-6 * b.abs().max().item()
 
 
 def test_full_size_64_channels(rick, oracle_mod):
@@ -197,3 +209,33 @@ def test_full_size_64_channels(rick, oracle_mod):
                                   pix, flags=0).real
         got = out[c].cpu().numpy()[pix[:, 1], pix[:, 0]]
         assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref)), (c, np.max(np.abs(got - ref)))
+
+
+@pytest.mark.parametrize("group_chans,use_graph", [(0, False), (2, False), (2, True)])
+def test_split_transform_batch_equals_single_channel_imaging(rick, group_chans, use_graph):
+    """From n = 1024 on a batch transforms its groups with the split (cuFFT's
+    rows, k_colfft, and k_colstack per channel at the channel's plane offset
+    in the group); every channel equals a single-channel imager (cuFFT's 2D
+    plan at this size) to FP32 rounding, directly and in a captured graph,
+    with one group and with pipelined groups of two channels."""
+    prob = synth.channels_problem(nchan=5, n=1024, nw=4, m_lo=20_000, m_hi=200_000, device="cuda", seed=78)
+    nw = prob["params"]["nw"]
+    q = dict(prob["params"], flags=CORRECT | REAL, plane_group=group_chans * nw)
+    bi = rick.BatchImager(q, prob["ranges"])
+    args = (prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"], prob["offsets"])
+    out = torch.empty((len(prob["ranges"]), 1024, 1024), device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(2 if use_graph else 1):
+            bi.images(*args, out=out, use_graph=use_graph)
+    torch.cuda.synchronize()
+    bi.stats()  # raises if a bounded wait ran out
+    bi.close()
+    import oracle
+    t = torch.from_numpy(oracle.taper(1024, q["kernel"], q["support"], 0.0)).cuda()
+    cc = torch.outer(t, t)
+    for c in range(len(prob["ranges"])):
+        ref = _single(rick, prob, c, CORRECT | REAL)
+        err = ((out[c] - ref).abs() * cc).max().item() / (ref.abs() * cc).max().item()
+        assert err <= 1e-5, (c, err)

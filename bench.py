@@ -720,6 +720,15 @@ def run_channels(args, rank, world):
         j1 = nvml.energy_mj() if nvml else None
     t_batch = e0.elapsed_time(e1) / args.steps
     batch_img = out.clone()
+    # one more batched step outside the timed region, eagerly (not from the
+    # graph) with the phase timers on: where the step's time goes
+    with torch.cuda.stream(s):
+        bi.set_timing(True)
+        bi.images(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"], offs, out=out, use_graph=False)
+        s.synchronize()
+        tb = bi.timing()
+        bi.set_timing(False)
+    batch_phases = {k: round(tb[k + "_ms"], 3) for k in ("prep", "grid", "fft", "colfft", "stack")}
     # the plain loop: one imager per channel, created once
     ims = [rick.Imager(dict(q, tile=tile, w_min=lo, w_max=hi)) for (lo, hi) in prob["ranges"]]
     loop_out = torch.empty_like(out)
@@ -733,11 +742,24 @@ def run_channels(args, rank, world):
             im.image(out=loop_out[c])
 
     ksteps = max(1, min(args.steps, 10))
+    loop_phases = []
 
     def time_loop():
         for _ in range(max(args.warmup, 1)):
             loop_step()
         torch.cuda.synchronize()
+        # phase times of one loop step (timers on), then the timed steps (off)
+        for im in ims:
+            im.set_timing(True)
+        loop_step()
+        torch.cuda.synchronize()
+        ph = dict.fromkeys(("prep", "grid", "fft", "colfft", "stack"), 0.0)
+        for im in ims:
+            tm = im.timing()
+            for k in ph:
+                ph[k] += tm[k + "_ms"]
+            im.set_timing(False)
+        loop_phases.append({k: round(v, 3) for k, v in ph.items()})
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         k0 = nvml.energy_mj() if nvml else None
         f0.record()
@@ -757,11 +779,14 @@ def run_channels(args, rank, world):
     ims = [rick.Imager(dict(q, tile=tile, w_min=lo, w_max=hi, flags=q["flags"] | rick.FFT_SPLIT))
            for (lo, hi) in prob["ranges"]]
     t_loop_split, s0, s1 = time_loop()
+    t_loop_default = t_loop
     loop_kind = "default single-image path"
     if t_loop_split < t_loop:
         t_loop, k0, k1, loop_kind = t_loop_split, s0, s1, "split transform"
+        loop_phase = loop_phases[1]
     else:
         loop_out.copy_(loop_default)
+        loop_phase = loop_phases[0]
     err = max(((batch_img[c] - loop_out[c]).abs().max() / loop_out[c].abs().max().clamp_min(1e-30)).item()
               for c in range(nchan))
     e_batch = (j1 - j0) / 1e3 / args.steps if j0 is not None and j1 is not None else None
@@ -782,7 +807,8 @@ def run_channels(args, rank, world):
                        "nvis": m, "tile": tile, "plane_group": group, "prep_blocks_per_sm": prep_blocks or 8,
                        "autotune_ms": tune_ms},
             "loop_ms_per_step": t_loop, "loop_path": loop_kind, "speedup_vs_loop": t_loop / t_batch,
-            "loop_ms_default_path": t_loop if loop_kind != "split transform" else None,
+            "loop_ms_default_path": t_loop_default, "loop_ms_split_transform": t_loop_split,
+            "batch_phases_ms": batch_phases, "loop_phases_ms": loop_phase,
             "max_rel_diff_batch_vs_loop": err, "energy_j_batch": e_batch, "energy_j_loop": e_loop,
             "green_productivity_eq4": gp}))
 

@@ -1432,7 +1432,9 @@ rick_status rick_image_batch(rick_handle h, const float* vis, const float* u, co
         return fail(h, RICK_ERR_ARG, "graph mode needs a non-default stream (rick_set_stream)");
     if (use_graph && h->graph && !stale && h->graph_m == m && memcmp(key, h->graph_key, sizeof(key)) == 0) {
         RICK_CU(h, cudaGraphLaunch(h->graph, h->stream));
-        count_launches(h, 5 + 2 * ((c.nw + h->G - 1) / h->G) + h->nchan);
+        // per plane group the two gridder kernels (and k_colfft on the split
+        // path), per channel one stack kernel
+        count_launches(h, 5 + (h->batch_split ? 3 : 2) * ((c.nw + h->G - 1) / h->G) + h->nchan);
         return RICK_OK;
     }
     if (!use_graph) return batch_body(h, vis, u, v, w, weights, m, images);

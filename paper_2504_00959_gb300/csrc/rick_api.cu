@@ -158,6 +158,7 @@ rick_status check_params(const rick_params* p, GridCfg* c, double* kparam, char*
     c->chan_off = nullptr;
     c->plane_lo = 0;
     c->plane_hi = p->nw;
+    c->row_perm = 0;
     (void)is_pow2;
     return RICK_OK;
 }
@@ -337,10 +338,13 @@ rick_status colfft_ready(rick_handle h)
     return RICK_OK;
 }
 
-// Grid planes [k0, k0 + nk) of every stored chunk into `planes`.
-rick_status grid_pass(rick_handle h, int k0, int nk, bool shift, float2* planes)
+// Grid planes [k0, k0 + nk) of every stored chunk into `planes`: the
+// handle's own buffer (its row order) or a caller's (natural rows).
+rick_status grid_pass(rick_handle h, int k0, int nk, bool shift, float2* planes, bool natural_rows = false)
 {
     PhaseScope scope(h, kPhaseGrid);
+    GridCfg cfg = h->cfg;
+    if (natural_rows) cfg.row_perm = 0;
     const size_t nch = h->chunks.size();
     size_t c0 = 0;
     do {
@@ -355,7 +359,7 @@ rick_status grid_pass(rick_handle h, int k0, int nk, bool shift, float2* planes)
         const size_t words = cl.count == 1 ? heavy_words_for(h->chunks[c0].cap) : 1;
         uint32_t* heavy = nullptr;
         RICK_CU(h, cudaMallocFromPoolAsync((void**)&heavy, words * sizeof(uint32_t), h->pool, h->stream));
-        const cudaError_t e = launch_grid(h->cfg, cl, k0, nk, shift, c0 > 0, heavy, words, planes, h->stream);
+        const cudaError_t e = launch_grid(cfg, cl, k0, nk, shift, c0 > 0, heavy, words, planes, h->stream);
         cudaFreeAsync(heavy, h->stream);
         RICK_CU(h, e);
         count_launches(h, 2);
@@ -654,6 +658,10 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
                          !(p->flags & RICK_FFT_2D);
         const bool split = h->batch ? h->batch_split : use_split(*p, &n1, &n2);
         const int kind = split ? kPlanRows : kPlan2D;
+        // the split keeps the handle's planes in b-major row order
+        h->cfg.row_perm = 0;
+        if (split)
+            while ((1 << h->cfg.row_perm) < n1) ++h->cfg.row_perm;
         s = get_plan(h, G, &plan, kind);
         if (s) return cleanup(s);
         if (NW % G) {
@@ -828,7 +836,7 @@ rick_status rick_grid_planes(rick_handle h, int32_t k0, int32_t nk, float* plane
     if (k0 < 0 || nk < 0 || k0 + nk > h->p.nw) return fail(h, RICK_ERR_ARG, "plane range out of bounds");
     if (nk == 0) return RICK_OK;
     if (!planes) return fail(h, RICK_ERR_ARG, "planes is NULL");
-    return grid_pass(h, k0, nk, false, reinterpret_cast<float2*>(planes));
+    return grid_pass(h, k0, nk, false, reinterpret_cast<float2*>(planes), true);
 }
 
 rick_status rick_fft_and_stack(rick_handle h, float* image)
@@ -848,9 +856,9 @@ rick_status rick_fft_and_stack(rick_handle h, float* image)
     a.wc_scale = h->wc_scale;
     a.wait_ns = h->dbg_wait_ns;
     a.skip_slot1 = h->dbg_skip_slot1;
-    // power-of-two n up to 4096: cuFFT transforms the rows and the first
+    // the split (use_split): cuFFT transforms the rows, k_colfft the first
     // factor of the columns, k_colstack the last factor with the screen and
-    // the stack (the planes are read once after two cuFFT passes); otherwise
+    // the stack (planes in b-major row order, GridCfg::row_perm); otherwise
     // cuFFT's 2D plan and k_stack
     int n1 = 0, n2 = 0;
     const bool split = use_split(p, &n1, &n2);
@@ -946,8 +954,8 @@ static rick_status degrid_impl(rick_handle h, const GridCfg& c, const double* su
     if (!st) count_launches(h, 5);
     // the adjoint of rick_fft_and_stack's transform path: with the split,
     // k_spreadcol writes the planes after the adjoint of the last column
-    // factor, then cuFFT's forward first column factor and rows; otherwise
-    // k_spread and cuFFT's forward 2D plan
+    // factor, then k_colfft's forward first column factor and cuFFT's forward
+    // rows; otherwise k_spread and cuFFT's forward 2D plan
     int n1 = 0, n2 = 0;
     const bool split = use_split(p, &n1, &n2);
     cufftComplex* planes = reinterpret_cast<cufftComplex*>(h->planes);

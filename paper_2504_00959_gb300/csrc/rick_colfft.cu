@@ -6,14 +6,20 @@
 // column transform of a plane (after its rows) is
 //     X[f1 + N1 f2] = sum_b w_16^(b f2) (w_n^(b f1) Y[16 f1 + b]),
 //     Y[16 f1 + b]  = sum_a x[16 a + b] w_N1^(a f1),
-// (w_M = exp(s 2 pi i / M), s = +1 for imaging, -1 for the adjoint).  This
-// kernel computes Y in place: for each plane, each b and each strip of W
-// adjacent columns, the N1 rows 16 a + b are one 3D TMA box per 256 rows
-// (the plane buffer viewed as [G N1][16][n]) brought into shared memory
-// ([a][W] complex values, 64- or 128-byte row segments), transformed there
-// and written back to rows 16 f1 + b.  The last factor (over b, a block of
-// 16 adjacent rows) is fused with the w-screen and the plane sum in
-// k_colstack, or applied to the planes by k_spreadcol in the adjoint.
+// (w_M = exp(s 2 pi i / M), s = +1 for imaging, -1 for the adjoint).  The
+// planes of the split transform keep their rows in b-major order: grid row
+// 16 a + b is memory row b N1 + a, so the N1 rows of one b are a contiguous
+// run (a plane is [16][N1][n]).  This kernel computes Y in place: for each
+// plane, each b and each strip of W adjacent columns, rows a = 0 .. N1-1 of
+// that run are one 3D TMA box per 256 rows (the buffer viewed as
+// [16 G][N1][n]) brought into shared memory ([a][W] complex values, 64- or
+// 128-byte row segments), transformed there and written back to memory row
+// b N1 + f1 (grid row 16 f1 + b).  With natural row order the rows of one
+// column transform lie 16 rows apart across the whole plane, and a 16384^2
+// plane's column pass reached ~0.73 of the copy bandwidth even without the
+// arithmetic (1.01 in b-major order).  The last factor (over b) is fused
+// with the w-screen and the plane sum in k_colstack, or applied to the
+// planes by k_spreadcol in the adjoint.
 //
 // The N1-point transform (N1 = 16 .. 1024; 4 and 8 in one pass) runs in
 // shared memory as
@@ -165,10 +171,10 @@ __device__ __forceinline__ float2 twid(const float2* tw, int e)
 }
 
 // The N1 = 16 Q-point transform (N1 >= 16) of the block in shared memory
-// ([N1][W] complex values), written to rows 16 f1 + b of the plane at P.
+// ([N1][W] complex values), output f1 written to row f1 of the run at P.
 template <int N1, int W, int SIGN>
 __device__ __forceinline__ void colfft_two_pass(float2* __restrict__ buf, const float2* tw,
-                                                float2* __restrict__ P, int n, int b, int t)
+                                                float2* __restrict__ P, int n, int t)
 {
     constexpr int Q = N1 / 16;
     // pass A: 16-point DFTs over a1 (rows Q a1 + a2), twiddle w_N1^(a2 k1)
@@ -191,14 +197,14 @@ __device__ __forceinline__ void colfft_two_pass(float2* __restrict__ buf, const 
         for (int it = t; it < 16 * W; it += kCfThreads) {
             const int x = it % W, k1 = it / W;
             if constexpr (Q == 1) {
-                P[(size_t)(16 * k1 + b) * n + x] = buf[k1 * W + x];
+                P[(size_t)k1 * n + x] = buf[k1 * W + x];
             } else {
                 float2 v[Q];
 #pragma unroll
                 for (int a2 = 0; a2 < Q; ++a2) v[a2] = buf[(Q * k1 + a2) * W + x];
                 dft_small<Q, SIGN>(v);
 #pragma unroll
-                for (int kq = 0; kq < Q; ++kq) P[(size_t)(16 * (k1 + 16 * kq) + b) * n + x] = v[kq];
+                for (int kq = 0; kq < Q; ++kq) P[(size_t)(k1 + 16 * kq) * n + x] = v[kq];
             }
         }
     } else {
@@ -240,7 +246,7 @@ __device__ __forceinline__ void colfft_two_pass(float2* __restrict__ buf, const 
             dft_small<r, SIGN>(v);
 #pragma unroll
             for (int j2 = 0; j2 < r; ++j2)
-                P[(size_t)(16 * (k1 + 16 * (j1 + 16 * j2)) + b) * n + xx] = v[j2];
+                P[(size_t)(k1 + 16 * (j1 + 16 * j2)) * n + xx] = v[j2];
         }
     }
 }
@@ -275,7 +281,7 @@ __global__ void __launch_bounds__(kCfThreads) k_colfft(const __grid_constant__ C
         mbar_expect(smem_u32(bar), (uint32_t)((N1 * W + N1) * sizeof(float2)));
 #pragma unroll
         for (int a0 = 0; a0 < N1; a0 += kBox)
-            tma_load_3d(smem_u32(buf + (size_t)a0 * W), &map, x0, b, plane * N1 + a0, smem_u32(bar));
+            tma_load_3d(smem_u32(buf + (size_t)a0 * W), &map, x0, a0, plane * 16 + b, smem_u32(bar));
         bulk_load(smem_u32(tws), tw, (uint32_t)(N1 * sizeof(float2)), smem_u32(bar));
     }
     const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(bar), 0, &s_abort, limit));
@@ -293,7 +299,8 @@ __global__ void __launch_bounds__(kCfThreads) k_colfft(const __grid_constant__ C
         return;
     }
 
-    float2* P = planes + (size_t)plane * n * n + x0;
+    // the run of rows b N1 .. b N1 + N1 - 1 of the plane, from column x0
+    float2* P = planes + (size_t)plane * n * n + (size_t)b * N1 * n + x0;
     if constexpr (N1 < 16) {
         // a single N1-point DFT per column (n = 64, 128)
         for (int it = t; it < W; it += kCfThreads) {
@@ -302,10 +309,10 @@ __global__ void __launch_bounds__(kCfThreads) k_colfft(const __grid_constant__ C
             for (int a = 0; a < N1; ++a) v[a] = buf[a * W + it];
             dft_small<N1, SIGN>(v);
 #pragma unroll
-            for (int f1 = 0; f1 < N1; ++f1) P[(size_t)(16 * f1 + b) * n + it] = v[f1];
+            for (int f1 = 0; f1 < N1; ++f1) P[(size_t)f1 * n + it] = v[f1];
         }
     } else {
-        colfft_two_pass<N1, W, SIGN>(buf, tws, P, n, b, t);
+        colfft_two_pass<N1, W, SIGN>(buf, tws, P, n, t);
     }
 }
 
@@ -357,11 +364,11 @@ cudaError_t encode_colfft_map(void* map, const float2* planes, int n, int planes
     }
     const int n1 = n / 16;
     const int w = colfft_width(n1);
-    // the plane buffer as [planes * N1][16][n] 8-byte complex values: row
-    // 16 a + b of plane p is (b, p N1 + a)
-    const cuuint64_t dims[3] = {(cuuint64_t)n, 16, (cuuint64_t)planes_in_buffer * (cuuint64_t)n1};
-    const cuuint64_t strides[2] = {(cuuint64_t)n * sizeof(float2), (cuuint64_t)16 * n * sizeof(float2)};
-    const cuuint32_t box[3] = {(cuuint32_t)w, 1, (cuuint32_t)(n1 < kCfBoxRows ? n1 : kCfBoxRows)};
+    // the plane buffer as [planes * 16][N1][n] 8-byte complex values: grid
+    // row 16 a + b of plane p (memory row b N1 + a) is (a, 16 p + b)
+    const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n1, (cuuint64_t)planes_in_buffer * 16};
+    const cuuint64_t strides[2] = {(cuuint64_t)n * sizeof(float2), (cuuint64_t)n1 * n * sizeof(float2)};
+    const cuuint32_t box[3] = {(cuuint32_t)w, (cuuint32_t)(n1 < kCfBoxRows ? n1 : kCfBoxRows), 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUresult r = encode(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_UINT64, 3,
                               const_cast<float2*>(planes), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,

@@ -308,8 +308,9 @@ __device__ __forceinline__ TileGeom tile_geom(const GridCfg& c, int k0, int64_t 
 
 // Whole-tile passes of one warp: lane L keeps the pair column L mod (T/2)
 // and starts at row L / (T/2), stepping 32 / (T/2) rows, so every pass is a
-// run of 16-byte accesses with no division.  The plane row of the pair is
-// (v0 + row) n + u0 + 2 pr, 16-byte aligned because n and u0 are even.
+// run of 16-byte accesses with no division.  The pair of grid row v0 + row
+// is at plane_row(v0 + row) n + u0 + 2 pr, 16-byte aligned because n and u0
+// are even.
 struct TileWalk {
     int pr, r0, dr, p2;
 };
@@ -333,10 +334,11 @@ __device__ __forceinline__ void store_tile(const GridCfg& c, const TileGeom& g, 
 {
     const TileWalk w = tile_walk(c, lane);
     if (2 * w.pr >= g.wu) return;
-    float4* dst = reinterpret_cast<float4*>(P0 + (int64_t)(g.v0 + w.r0) * c.n + g.u0 + 2 * w.pr);
-    const int64_t step = (int64_t)w.dr * (c.n / 2);
-    for (int row = w.r0; row < g.wv; row += w.dr, dst += step)
+    float2* col = P0 + g.u0 + 2 * w.pr;
+    for (int row = w.r0; row < g.wv; row += w.dr) {
+        float4* dst = reinterpret_cast<float4*>(col + (int64_t)plane_row(c, g.v0 + row) * c.n);
         *dst = kZero ? make_float4(0.f, 0.f, 0.f, 0.f) : tile4[row * w.p2 + w.pr];
+    }
 }
 
 // Initialise a tile copy: zeros, or the plane's current values (accumulating
@@ -345,12 +347,12 @@ __device__ __forceinline__ void init_tile(const GridCfg& c, const TileGeom& g, c
                                           bool from_plane, int lane)
 {
     const TileWalk w = tile_walk(c, lane);
-    const float4* src = reinterpret_cast<const float4*>(P0 + (int64_t)(g.v0 + w.r0) * c.n + g.u0 + 2 * w.pr);
-    const int64_t step = (int64_t)w.dr * (c.n / 2);
+    const float2* col = P0 + g.u0 + 2 * w.pr;
     const bool col_ok = from_plane && 2 * w.pr < g.wu;
-    for (int row = w.r0; row < c.T; row += w.dr, src += step) {
+    for (int row = w.r0; row < c.T; row += w.dr) {
         float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (col_ok && row < g.wv) x = *src;
+        if (col_ok && row < g.wv)
+            x = *reinterpret_cast<const float4*>(col + (int64_t)plane_row(c, g.v0 + row) * c.n);
         tile4[row * w.p2 + w.pr] = x;
     }
 }
@@ -481,11 +483,11 @@ __global__ void __launch_bounds__(256) k_grid_chunks(GridCfg c, ChunkList ch, in
         __syncwarp();
         const TileWalk w = tile_walk(c, lane);
         if (2 * w.pr < g.wu) {
-            float4* dst = reinterpret_cast<float4*>(P0 + (int64_t)(g.v0 + w.r0) * c.n + g.u0 + 2 * w.pr);
-            const int64_t step = (int64_t)w.dr * (c.n / 2);
-            for (int row = w.r0; row < g.wv; row += w.dr, dst += step) {
+            float2* col = P0 + g.u0 + 2 * w.pr;
+            for (int row = w.r0; row < g.wv; row += w.dr) {
                 const float4 x = tile4[row * w.p2 + w.pr];
-                if (x.x != 0.f || x.y != 0.f || x.z != 0.f || x.w != 0.f) atomicAdd(dst, x);
+                if (x.x != 0.f || x.y != 0.f || x.z != 0.f || x.w != 0.f)
+                    atomicAdd(reinterpret_cast<float4*>(col + (int64_t)plane_row(c, g.v0 + row) * c.n), x);
             }
         }
         __syncwarp();

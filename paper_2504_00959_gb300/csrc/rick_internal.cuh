@@ -56,6 +56,11 @@ struct GridCfg {
     // (rick_set_plane_range; all by default).  Measurements on other planes
     // are placed, weighted and counted but list no entries.
     int plane_lo, plane_hi;
+    // row order of the planes in memory: 0 = natural (row v at v); r > 0 =
+    // b-major storage of the split transform, n = 16 N1 with N1 = 2^r: row
+    // v = 16 a + b lives at b N1 + a (plane_row), so the rows of each column
+    // factor's input (fixed b) are one contiguous run of the plane
+    int row_perm;
     // batched imaging: nchan channels with nw_chan w-planes each, channel c
     // owning planes c*nw_chan .. (c+1)*nw_chan-1 and measurements
     // chan_off[c] .. chan_off[c+1]-1; chan_w[c] = (w_min, 1/dw) in binary32.
@@ -69,6 +74,12 @@ struct GridCfg {
     // sum_t g_t = sum_j sumc[j] z^j: the tap sum of one axis (set_tap_sum)
     float sumc[kPolyTerms];
 };
+
+// Memory row of grid row v of a plane (see GridCfg::row_perm).
+__host__ __device__ __forceinline__ int plane_row(const GridCfg& c, int v)
+{
+    return c.row_perm ? ((v & 15) << c.row_perm) | (v >> 4) : v;
+}
 
 // Placement of one measurement: plane, first footprint cell, continuous
 // cell coordinates.  Every float->int decision is binary32 with the

@@ -369,14 +369,15 @@ __global__ void __launch_bounds__(kPrepThreads) k_degrid_gather(GridCfg c, const
             const int plane = p.k + tw;
             if (plane < k0 || plane >= k0 + nk) continue;
             const float ht = c.Sw > 1 ? w_kernel(c, __fsub_rn((float)plane, p.pw)) * hn : 1.0f;
-            const float2* P = planes + (int64_t)(plane - k0) * c.n * c.n + (int64_t)p.fv * c.n + p.fu;
+            const float2* P = planes + (int64_t)(plane - k0) * c.n * c.n + p.fu;
             float cr = 0.f, ci = 0.f;
 #pragma unroll
             for (int rr = 0; rr < S; ++rr) {
+                const float2* R = P + (int64_t)plane_row(c, p.fv + rr) * c.n;
                 float br = 0.f, bi = 0.f;
 #pragma unroll
                 for (int t = 0; t < S; ++t) {
-                    const float2 x = __ldg(P + (int64_t)rr * c.n + t);
+                    const float2 x = __ldg(R + t);
                     br = fmaf(gu[t], x.x, br);
                     bi = fmaf(gu[t], x.y, bi);
                 }

@@ -242,17 +242,18 @@ __global__ void __launch_bounds__(kStackThreads) k_spread(StackArgs a, const voi
 }
 
 // ---------------------------------------------------------------------------
-// Column transform + w-screen + plane stack in one pass (the single-image path
-// for power-of-two n in [64, 4096]).  cuFFT has already transformed the rows
-// and the first factor of the column dimension: with n = N1 * N2 (N2 = 16),
-// row v = N2 a + b and output row y = f1 + N1 f2 (w_M = exp(2 pi i / M), the
-// inverse sign),
+// Column transform + w-screen + plane stack in one pass (the split transform
+// of power-of-two n in [64, 16384]).  cuFFT has already transformed the rows
+// and k_colfft the first factor of the column dimension: with n = N1 * N2
+// (N2 = 16), row v = N2 a + b and output row y = f1 + N1 f2 (w_M =
+// exp(2 pi i / M), the inverse sign),
 //     Y[N2 f1 + b] = sum_a x[N2 a + b] w_N1^(a f1)
 // is in the plane, and the remaining factor
 //     X[f1 + N1 f2] = sum_b w_N2^(b f2) (w_n^(b f1) Y[N2 f1 + b])
-// is a 16-point transform of one contiguous block of 16 rows per f1.  A CTA
-// owns one f1 and 32 columns.  It streams that block of every plane of the
-// group through a ring of shared-memory stages, one 2D TMA box per plane
+// is a 16-point transform of the 16 rows N2 f1 + b, b = 0 .. 15, per f1 (in
+// the planes' b-major row order, memory rows b N1 + f1: 16 rows N1 apart).
+// A CTA owns one f1 and 32 columns.  It streams those rows of every plane of
+// the group through a ring of shared-memory stages, one 3D TMA box per plane
 // completing on the stage's mbarrier, does the 16 = 4 x 4 transform in two
 // register passes with an exchange inside each warp (b = 4 b1 + b0,
 // f2 = g0 + 4 g1: w_16^(b f2) = w_4^(b1 g0) w_16^(b0 g0) w_4^(b0 g1)), and sums
@@ -346,15 +347,15 @@ __global__ void __launch_bounds__(kColThreads, 6) k_colstack(const __grid_consta
     __syncthreads();
 
     // slot i of the pipeline carries plane nk - 1 - i into stage i % stages:
-    // one TMA box of kColW columns x N2 rows, at row (plane n + N2 f1) of the
-    // map's [planes x n] x n view of the plane buffer
+    // one TMA box of kColW columns x N2 rows (b = 0 .. 15) at (x0, f1,
+    // 16 plane) of the map's [16 planes][N1][n] view of the plane buffer
     auto issue = [&](int i) {  // called by all of warp 0
         if (lane == 0 && i + 1 != a.skip_slot1) {
             const int st = i % kColStages;
             const uint32_t bar = smem_u32(full + st);
             mbar_expect(bar, (uint32_t)kColStageBytes);
-            tma_load_2d(smem_u32(stage + (size_t)st * kColN2 * kColPitch), &map, x0,
-                        (a.plane0 + nk - 1 - i) * n + kColN2 * f1, bar);
+            tma_load_3d(smem_u32(stage + (size_t)st * kColN2 * kColPitch), &map, x0, f1,
+                        (a.plane0 + nk - 1 - i) * kColN2, bar);
         }
         __syncwarp();
     };
@@ -512,7 +513,7 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b)  // a * conj(b)
 
 // Adjoint of k_colstack (the backward pass of imaging and prediction, n with
 // the split transform): for one f1 and 32 columns, every plane k of the group
-// gets the rows 16 f1 + b
+// gets the rows 16 f1 + b (memory rows b N1 + f1, the b-major order)
 //     Y'[16 f1 + b] = conj(w_n^(b f1)) sum_f2 w_16^(-b f2) Z_k[f1 + N1 f2],
 //     Z_k(x, y) = R(x, y) conj(screen_k(x, y)),
 // R the adjoint of the finalisation applied to the image gradient (sign,
@@ -576,7 +577,8 @@ __global__ void __launch_bounds__(kColThreads, 5) k_spreadcol(StackArgs a, int n
         z[g] = screen(ps.A, ps.B, a.k0);
     }
 
-    const int64_t row0 = (int64_t)kColN2 * f1;
+    // grid row 16 f1 + b (b = j + 4 q) is memory row b N1 + f1
+    const int64_t row0 = f1, bstride = (int64_t)n1 * n;
 #pragma unroll 2
     for (int p = 0; p < a.nk; ++p) {
         float2 v[kColQ];
@@ -603,9 +605,9 @@ __global__ void __launch_bounds__(kColThreads, 5) k_spreadcol(StackArgs a, int n
         for (int q = 0; q < kColQ; ++q) v[q] = ex[j * kColExPitch + 8 * q + cl];
         __syncwarp();
         dft4m(v);
-        float2* dst = planes + (int64_t)p * nn + (row0 + j) * n + x;
+        float2* dst = planes + (int64_t)p * nn + (row0 + (int64_t)j * n1) * n + x;
 #pragma unroll
-        for (int q = 0; q < kColQ; ++q) __stcs(dst + (int64_t)kColQ * q * n, cmulc(v[q], tw[q]));
+        for (int q = 0; q < kColQ; ++q) __stcs(dst + kColQ * q * bstride, cmulc(v[q], tw[q]));
     }
 }
 
@@ -661,12 +663,15 @@ cudaError_t encode_colstack_map(void* map, const float2* planes, int n, int plan
         if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
-    // the plane buffer as a [planes_in_buffer * n] x n matrix of 8-byte complex values
-    const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)planes_in_buffer * (cuuint64_t)n};
-    const cuuint64_t strides[1] = {(cuuint64_t)n * sizeof(float2)};
-    const cuuint32_t box[2] = {(cuuint32_t)kColW, (cuuint32_t)kColN2};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = encode(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_UINT64, 2,
+    // the plane buffer as [planes_in_buffer * 16][N1][n] 8-byte complex
+    // values (b-major rows: grid row 16 f1 + b of plane p is (f1, 16 p + b));
+    // a box is kColW columns of one f1 and the 16 values of b
+    const int n1 = n / kColN2;
+    const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n1, (cuuint64_t)planes_in_buffer * kColN2};
+    const cuuint64_t strides[2] = {(cuuint64_t)n * sizeof(float2), (cuuint64_t)n1 * n * sizeof(float2)};
+    const cuuint32_t box[3] = {(cuuint32_t)kColW, 1, (cuuint32_t)kColN2};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = encode(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_UINT64, 3,
                               const_cast<float2*>(planes), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

@@ -239,3 +239,33 @@ def test_split_transform_batch_equals_single_channel_imaging(rick, group_chans, 
         ref = _single(rick, prob, c, CORRECT | REAL)
         err = ((out[c] - ref).abs() * cc).max().item() / (ref.abs() * cc).max().item()
         assert err <= 1e-5, (c, err)
+
+
+@pytest.mark.parametrize("n", [256, 1024])
+def test_batch_hermitian_fold(rick, oracle_mod, n):
+    """RICK_HERMITIAN_FOLD in a batch: every channel's w-planes cover its
+    folded range [0, max |w|] (half the planes of the unfolded ones at the
+    same spacing); each channel equals a single-channel imager folded the same
+    way (1e-6 of the peak; n = 1024 takes the batch's split transform), and
+    one channel equals the FP64 oracle with the fold at sampled pixels (1e-4)."""
+    prob = synth.channels_problem(nchan=4, n=n, nw=4, m_lo=5_000, m_hi=80_000, device="cuda", seed=79)
+    fold = REAL | synth.FLAG_FOLD
+    ranges = [(0.0, max(abs(lo), abs(hi))) for lo, hi in prob["ranges"]]
+    bi = rick.BatchImager(dict(prob["params"], flags=fold), ranges)
+    imgs = bi.images(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"], prob["offsets"])
+    torch.cuda.synchronize()
+    bi.stats()
+    bi.close()
+    folded = dict(prob, ranges=ranges)
+    for c in range(len(ranges)):
+        ref = _single(rick, folded, c, fold)
+        assert (imgs[c] - ref).abs().max().item() <= 1e-6 * ref.abs().max().item(), c
+    c = 1
+    a, b = prob["offsets"][c], prob["offsets"][c + 1]
+    sl = {k: prob[k][a:b].cpu().numpy() for k in ("u", "v", "w", "wt", "vis")}
+    xs = np.unique(np.linspace(0, n - 1, 8).round().astype(np.int64))
+    pix = np.array(sorted({(int(x), int(y)) for y in xs for x in xs} | {(n // 2, n // 2)}), np.int32)
+    q = dict(prob["params"], w_min=ranges[c][0], w_max=ranges[c][1])
+    ref = oracle_mod.image_at(q, sl["u"], sl["v"], sl["w"], sl["wt"], sl["vis"], pix, flags=synth.FLAG_FOLD).real
+    got = imgs[c].cpu().numpy()[pix[:, 1], pix[:, 0]]
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref)), np.max(np.abs(got - ref))

@@ -2,13 +2,13 @@
 factorisation the GPU's fused column kernels follow, written out with their
 thread roles, against numpy's FFT.
 
-Forward (k_colstack after cuFFT's first column factor): with n = N1 * 16,
+Forward (k_colstack after k_colfft's first column factor): with n = N1 * 16,
 row v = 16 a + b and output row y = f1 + N1 f2,
-    Y[16 f1 + b] = sum_a x[16 a + b] w_N1^(a f1)                 (cuFFT)
-    X[f1 + N1 f2] = sum_b w_16^(b f2) w_n^(b f1) Y[16 f1 + b]     (kernel)
+    Y[16 f1 + b] = sum_a x[16 a + b] w_N1^(a f1)                 (k_colfft)
+    X[f1 + N1 f2] = sum_b w_16^(b f2) w_n^(b f1) Y[16 f1 + b]     (k_colstack)
 with the 16-point factor as two 4-point passes (b = 4 b1 + b0,
 f2 = g0 + 4 g1): over b1 for each b0, times w_16^(b0 g0), then over b0.
-Adjoint (k_spreadcol before cuFFT's forward first column factor): the same
+Adjoint (k_spreadcol before k_colfft's forward first column factor): the same
 steps in reverse order with conjugate twiddles and the minus sign.  The
 unnormalised inverse column DFT (exponent +) and its adjoint, the forward
 DFT (exponent -), are the references."""
@@ -31,7 +31,7 @@ def forward_split(x, n1):
     """Inverse (exponent +) transform of one column through the split."""
     n = n1 * N2
     y = np.empty(n, complex)
-    for b in range(N2):  # first factor, in place: rows 16 f1 + b
+    for b in range(N2):  # first factor (k_colfft), in place: rows 16 f1 + b
         y[b::N2] = np.exp(2j * np.pi * np.outer(np.arange(n1), np.arange(n1)) / n1) @ x[b::N2]
     out = np.empty(n, complex)
     for f1 in range(n1):
@@ -61,7 +61,7 @@ def adjoint_split(r, n1):
             for q in range(Q):
                 y[N2 * f1 + Q * q + j] = t[q] * np.conj(_w(n, ((Q * q + j) * f1) % n))
     x = np.empty(n, complex)
-    for b in range(N2):  # cuFFT forward first factor along the columns
+    for b in range(N2):  # k_colfft's forward first factor along the columns
         x[b::N2] = np.exp(-2j * np.pi * np.outer(np.arange(n1), np.arange(n1)) / n1) @ y[b::N2]
     return x
 
@@ -160,3 +160,49 @@ def test_colfft_block_positions_are_a_permutation():
             reads = sorted(q * k1 + r * c1 + c2 for k1 in range(16) for c2 in range(r) for c1 in range(16))
             writes = sorted(q * k1 + 16 * c2 + (j1 ^ c2) for k1 in range(16) for c2 in range(r) for j1 in range(16))
             assert reads == writes == list(range(n1))
+
+
+# -------------------------------------------------------------------------
+# The planes' b-major row order of the split transform: grid row 16 a + b is
+# memory row b N1 + a (GridCfg::row_perm / plane_row), so k_colfft reads and
+# writes one contiguous run of N1 memory rows per b, and k_colstack reads the
+# 16 memory rows b N1 + f1 (b = 0 .. 15) of each f1.
+
+def plane_row(v, n1):
+    return (v % N2) * n1 + v // N2
+
+
+@pytest.mark.parametrize("n1", [4, 16, 64, 256, 1024])
+def test_b_major_rows_are_a_permutation(n1):
+    rows = [plane_row(v, n1) for v in range(n1 * N2)]
+    assert sorted(rows) == list(range(n1 * N2))
+    # the column factor's input rows of one b are the run b N1 .. b N1 + N1 - 1
+    for b in (0, 5, N2 - 1):
+        assert [plane_row(N2 * a + b, n1) for a in range(n1)] == list(range(b * n1, b * n1 + n1))
+
+
+@pytest.mark.parametrize("n1", [4, 8, 64])
+def test_column_transform_through_b_major_memory(n1):
+    """A plane of 3 columns stored b-major; the first factor on each memory
+    run (in place), then the last factor reading memory rows b N1 + f1: the
+    inverse DFT of every column in natural order."""
+    n = n1 * N2
+    rng = np.random.default_rng(300 + n1)
+    grid = rng.standard_normal((n, 3)) + 1j * rng.standard_normal((n, 3))
+    mem = np.empty_like(grid)
+    for v in range(n):
+        mem[plane_row(v, n1)] = grid[v]
+    for b in range(N2):  # k_colfft: block (b, columns) on its run, in place
+        for col in range(3):
+            mem[b * n1:(b + 1) * n1, col] = colfft_block(mem[b * n1:(b + 1) * n1, col], +1)
+    out = np.empty_like(grid)
+    for col in range(3):  # k_colstack's last factor on memory rows b N1 + f1
+        y = np.empty(n, complex)
+        for f1 in range(n1):
+            for b in range(N2):
+                y[N2 * f1 + b] = mem[b * n1 + f1, col]  # Y[16 f1 + b]
+        for f1 in range(n1):
+            for f2 in range(N2):
+                out[f1 + n1 * f2, col] = sum(_w(N2, b * f2) * _w(n, b * f1) * y[N2 * f1 + b] for b in range(N2))
+    ref = np.fft.ifft(grid, axis=0) * n
+    assert np.max(np.abs(out - ref)) <= 1e-11 * np.max(np.abs(ref))

@@ -66,9 +66,9 @@ typedef int32_t rick_status;
 #define RICK_FFT_2D 64u         /* transform the planes with cuFFT's 2D plan and stack them in a
                                   separate pass, also where the library would otherwise split
                                   the column transform and fuse its last factor with the
-                                  w-screen and the stack (single images with n >= 4096) */
+                                  w-screen and the stack (single images with n >= 2048) */
 #define RICK_FFT_SPLIT 128u     /* the split transform for any power-of-two n in [64, 16384]
-                                  (single images; the default from n = 4096 on, for tests and
+                                  (single images; the default from n = 2048 on, for tests and
                                   measurement below).  Not with RICK_FFT_2D.  Either way the
                                   result is the same up to rounding */
 
@@ -159,7 +159,7 @@ rick_status rick_add_density(rick_handle h, const float* vis, const float* u, co
  * exp(+2 pi i w_k (n-1)) and sum over planes (Eq. 1); then divide by the
  * weight sum and, per flags, by the taper and times n.  image: float[n*n]
  * (RICK_REAL_IMAGE) or float[2*n*n] complex, fully overwritten.  For
- * power-of-two n from 4096 to 16384 (or with RICK_FFT_SPLIT) the column
+ * power-of-two n from 2048 to 16384 (or with RICK_FFT_SPLIT) the column
  * transform is split, n = 16 * (n / 16): cuFFT transforms the rows, one
  * library kernel the first (n / 16-point) column factor of every plane of
  * the group in place, and one kernel the last 16-point column factor

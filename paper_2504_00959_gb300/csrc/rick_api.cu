@@ -177,18 +177,18 @@ size_t plane_bytes(const rick_params* p) { return (size_t)p->n * p->n * sizeof(f
 // (the first column factor of the split transform is k_colfft's, the last
 // k_colstack's or k_spreadcol's)
 enum { kPlan2D = 0, kPlanRows = 1 };
-// smallest n for the split column transform without RICK_FFT_SPLIT: measured
-// at 2048^2 x 16 planes it is still 4 % slower than cuFFT's 2D plan + k_stack
-// (the 2D plan keeps more of a 34 MB plane in L2, and the first column factor
-// costs one cuFFT call per plane), at 4096^2 x 32 planes 8 % faster
-constexpr int kSplitMinN = 4096;
-// the same for batched imaging, where every group is one launch of each
-// kernel (no per-plane calls)
+// smallest n for the split column transform without RICK_FFT_SPLIT, from
+// measured single images (ms, split / cuFFT 2D plan + k_stack): 256^2 x 8
+// 0.104 / 0.099, 512^2 x 16 0.189 / 0.175, 1024^2 x 16 0.353 / 0.351,
+// 2048^2 x 16 1.169 / 1.278, 4096^2 x 32 5.06 / 6.32 (small planes stay
+// partly in L2 through the 2D plan's passes)
+constexpr int kSplitMinN = 2048;
+// the same for batched imaging, whose groups hold many planes
 constexpr int kBatchSplitMinN = 1024;
 
-// The split transform (cuFFT on the rows and the first column factor, the
-// last factor fused with the screen) for single images: n = 4096 by default,
-// any eligible n with RICK_FFT_SPLIT, never with RICK_FFT_2D.
+// The split transform (cuFFT on the rows, k_colfft on the first column
+// factor, the last factor fused with the screen) for single images: n >=
+// 2048 by default, any eligible n with RICK_FFT_SPLIT, never with RICK_FFT_2D.
 bool use_split(const rick_params& p, int* n1, int* n2)
 {
     if (!colstack_shape(p.n, n1, n2)) return false;

@@ -1,4 +1,4 @@
-"""The split plane transform of single images (the default from n = 4096 on,
+"""The split plane transform of single images (the default from n = 2048 on,
 RICK_FFT_SPLIT for any power-of-two n in [64, 16384]): cuFFT on the rows,
 k_colfft for the first (n / 16-point) column factor of every plane of the
 group, then k_colstack for the last 16-point factor
@@ -120,9 +120,9 @@ def test_repeated_images_reuse_the_tensor_map(rick):
         assert (o - outs[0]).abs().max().item() <= 1e-5 * peak
 
 
-@pytest.mark.parametrize("n", [4096, 16384])
-def test_default_from_4096_is_the_split(rick, n):
-    """Without either flag, n = 4096 .. 16384 takes the split transform: the
+@pytest.mark.parametrize("n", [2048, 4096, 16384])
+def test_default_from_2048_is_the_split(rick, n):
+    """Without either flag, n = 2048 .. 16384 takes the split transform: the
     image equals the one RICK_FFT_SPLIT gives, up to the gridder's atomic
     rounding."""
     prob = synth.config2(m=300000, n=n, nw=4)
@@ -142,8 +142,8 @@ def test_flag_checks(rick):
 
 # ---------------------------------------------------------------- the adjoint
 # With the split transform the backward pass runs k_spreadcol (the adjoint of
-# the last column factor, the screen and the finalisation), then cuFFT's
-# forward first column factor and rows.
+# the last column factor, the screen and the finalisation), then k_colfft's
+# forward first column factor and cuFFT's forward rows.
 
 def _degrid(rick, prob, flags, r, **extra):
     g = {k: prob[k].cuda() for k in ("vis", "u", "v", "w", "wt")}

@@ -541,10 +541,13 @@ def run_image(args, rank, world):
     for v in phases.values():
         v["gbs"] = v["algorithmic_gb"] / v["ms"] * 1e3 if v["ms"] > 0 else None
         v["frac_of_" + peak_kind] = v["gbs"] / peak if v["gbs"] else None
-    # the committed DRAM counters were taken on the 4096^2 x 32 x 1e7 workload only
-    default_size = wl == "wstack" and (n, nw, m) == (4096, 32, 10_000_000) and \
-        params.get("w_support", 1) <= 1 and not params["flags"] & synth.FLAG_FOLD
-    traffic = _traffic("rick_grid.cu", "k_grid@4096x32x1e7") if default_size else None
+    # committed DRAM counters (profiles/traffic.json): small-case ncu captures
+    # of the 4096^2 x 32 x 1e7 workload, and of k_colfft on 2 planes of 16384^2
+    # scaled to a launch of the 16384^2 x 128 x 2e8 one
+    plain = params.get("w_support", 1) <= 1 and not params["flags"] & synth.FLAG_FOLD
+    default_size = wl == "wstack" and (n, nw, m) == (4096, 32, 10_000_000) and plain
+    large_size = wl == "large" and (n, nw, m) == (16384, 128, 200_000_000) and plain
+    traffic = _traffic("rick_grid.cu", "k_grid_tiles@4096x32x1e7") if default_size else None
     stack_name = ("k_colstack (last 16-point column factor + w-screen + stack, Eq. 1)" if split
                   else "k_stack (w-screen + stack, Eq. 1)")
     stack_traffic = _traffic("rick_stack.cu", "k_colstack@4096x32x1e7") if (default_size and split) else None
@@ -565,7 +568,10 @@ def run_image(args, rank, world):
         own.append((colfft_ms, {
             "kernel": "k_colfft (first n/16-point column factor of the plane transform, TMA-fed)", "bound": "hbm",
             "achieved": colfft_bytes / colfft_ms / 1e6, "peak": peak, "unit": "GB/s",
-            "frac": colfft_bytes / colfft_ms / 1e6 / peak, "traffic": None, "peak_kind": peak_kind,
+            "frac": colfft_bytes / colfft_ms / 1e6 / peak,
+            "traffic": (_traffic("rick_colfft.cu", "k_colfft@4096x32x1e7") if default_size else
+                        _traffic("rick_colfft.cu", "k_colfft@16384x128x2e8") if large_size else None),
+            "peak_kind": peak_kind,
             "algorithmic_bytes_per_launch": colfft_bytes / launches_cf, "launch_ms": colfft_ms / launches_cf,
             "launches_per_step": launches_cf}))
     own.sort(key=lambda t: -t[0])

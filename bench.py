@@ -582,9 +582,9 @@ def run_image(args, rank, world):
     if not args.no_e2e and world > 1:
         # every rank uploads the inputs, images its share, the ranks sum the
         # images and every rank downloads the image
-        hv = prob["vis"].cpu().pin_memory()
-        hu, hvv, hw, hwt = (prob[k].cpu().pin_memory() for k in ("u", "v", "w", "wt"))
-        himg = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        hv, hu, hvv, hw, hwt = (torch.empty(prob[k].shape, dtype=prob[k].dtype, pin_memory=True).copy_(prob[k])
+                                for k in ("vis", "u", "v", "w", "wt"))
+        himg = torch.empty((n, n), dtype=torch.float32, pin_memory=True)
         dv, du, dvv, dww, dwt = (torch.empty_like(prob[k]) for k in ("vis", "u", "v", "w", "wt"))
 
         def e2e_step():
@@ -613,10 +613,11 @@ def run_image(args, rank, world):
                       "image download; %d steps, slowest rank" % ksteps}
         del hv, hu, hvv, hw, hwt, himg, dv, du, dvv, dww, dwt
     elif not args.no_e2e:
-        hv = prob["vis"].cpu().pin_memory()
-        hu, hvv, hw, hwt = (prob[k].cpu().pin_memory() for k in ("u", "v", "w", "wt"))
-        himg = torch.empty((n, n), dtype=torch.float32).pin_memory()
-        himg2 = torch.empty((n, n), dtype=torch.float32).pin_memory()
+        # pinned host copies of the inputs, filled straight from the device
+        hv, hu, hvv, hw, hwt = (torch.empty(prob[k].shape, dtype=prob[k].dtype, pin_memory=True).copy_(prob[k])
+                                for k in ("vis", "u", "v", "w", "wt"))
+        himg = torch.empty((n, n), dtype=torch.float32, pin_memory=True)
+        himg2 = torch.empty((n, n), dtype=torch.float32, pin_memory=True)
         im.image_host(hv, hu, hvv, hw, hwt, out=himg)
         torch.cuda.synchronize()
         t0 = time.perf_counter()

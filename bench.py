@@ -547,7 +547,7 @@ def run_image(args, rank, world):
     plain = params.get("w_support", 1) <= 1 and not params["flags"] & synth.FLAG_FOLD
     default_size = wl == "wstack" and (n, nw, m) == (4096, 32, 10_000_000) and plain
     large_size = wl == "large" and (n, nw, m) == (16384, 128, 200_000_000) and plain
-    traffic = _traffic("rick_grid.cu", "k_grid_tiles@4096x32x1e7") if default_size else None
+    traffic = _traffic("rick_grid.cu", "k_grid@4096x32x1e7") if default_size else None
     stack_name = ("k_colstack (last 16-point column factor + w-screen + stack, Eq. 1)" if split
                   else "k_stack (w-screen + stack, Eq. 1)")
     stack_traffic = _traffic("rick_stack.cu", "k_colstack@4096x32x1e7") if (default_size and split) else None

@@ -180,24 +180,104 @@ struct Staged {
     }
 };
 
+// Stage one entry r of the tile at (u0, v0) into slot `slot` of the warp's
+// stage: its 2S taps (degree-10 polynomials with uniform coefficients from
+// the constant bank, checkerboard signs folded in), the v taps times the
+// visibility, and the header (tile_s: the warp's tile copy).
+template <int S>
+__device__ __forceinline__ void stage_entry(const GridCfg& c, const float4& r, int u0, int v0, Stage<S>& st,
+                                            int slot, uint32_t tile_s, int shift)
+{
+    constexpr int KP = Stage<S>::kPairs, NS = Stage<S>::kSlots, NH = Stage<S>::kHead;
+    const int TP = c.T / 2, P2 = pair_pitch(c.T);
+    const int fu = first_cell(c, r.x), fv = first_cell(c, r.y);
+    const float zu = __fmaf_rn(2.0f, __fsub_rn(__fsub_rn(r.x, c.half_s), (float)(fu - 1)), -1.0f);
+    const float zv = __fmaf_rn(2.0f, __fsub_rn(__fsub_rn(r.y, c.half_s), (float)(fv - 1)), -1.0f);
+    const int lu = fu - u0, lv = fv - v0;
+    const int odd = lu & 1;  // u0 is even: the parity of the tile column
+    const int pu = (lu - odd) / 2;
+    float gu[S];
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+        float a = c.coef[t][kPolyTerms - 1], bb = c.coef[t][kPolyTerms - 1];
+#pragma unroll
+        for (int k = kPolyTerms - 2; k >= 0; --k) {
+            a = __fmaf_rn(a, zu, c.coef[t][k]);
+            bb = __fmaf_rn(bb, zv, c.coef[t][k]);
+        }
+        if (shift) {
+            if ((fu + t) & 1) a = -a;
+            if ((fv + t) & 1) bb = -bb;
+        }
+        gu[t] = a;
+        st.gvv[slot * S + t] = make_float2(bb * r.z, bb * r.w);
+    }
+    // pair t holds tile columns 2 (pu + t) and 2 (pu + t) + 1: taps
+    // (2t, 2t+1) for an even start column, (2t-1, 2t) for an odd one
+#pragma unroll
+    for (int t = 0; t < KP; ++t) {
+        const float e0 = 2 * t < S ? gu[2 * t < S ? 2 * t : 0] : 0.0f;
+        const float e1 = 2 * t + 1 < S ? gu[2 * t + 1 < S ? 2 * t + 1 : 0] : 0.0f;
+        const float o0 = 2 * t - 1 >= 0 ? gu[2 * t - 1 >= 0 ? 2 * t - 1 : 0] : 0.0f;
+        st.gu[slot * KP + t] = odd ? make_float2(o0, e0) : make_float2(e0, e1);
+    }
+    // header: first pair's shared address (wraps for footprints that start
+    // left of or above the tile; only in-tile pairs are used) and the in-tile
+    // lane bits of every slot: footprint rows [rlo, rhi) and pairs [plo, phi)
+    // lie inside the tile
+    const int rlo = max(0, -lv), rhi = min(S, c.T - lv);
+    const int plo = max(0, -pu), phi = min(KP, TP - pu);
+    const uint32_t pm = phi > plo ? (((1u << phi) - 1u) & ~((1u << plo) - 1u)) : 0u;
+    uint32_t wm[NH - 1];
+#pragma unroll
+    for (int k = 0; k < NH - 1; ++k) wm[k] = 0u;
+#pragma unroll
+    for (int sr = 0; sr < S; ++sr) {
+        const uint32_t rowbits = (sr >= rlo && sr < rhi) ? pm : 0u;
+        const int bit = sr * KP, wd = bit / 32, sh = bit % 32;
+        wm[wd] |= rowbits << sh;
+        if (sh + KP > 32 && wd + 1 < NS) wm[wd + 1] |= rowbits >> (32 - sh);
+    }
+    st.head[slot * NH] = tile_s + (uint32_t)(lv * P2 + pu) * 16u;
+#pragma unroll
+    for (int k = 0; k < NH - 1; ++k) st.head[slot * NH + 1 + k] = wm[k];
+}
+
+// Walk the staged entries q0 .. q1-1 into the warp's tile: the next entry's
+// header and taps are loaded before this entry's read-modify-write (two
+// register sets, alternating); a __syncwarp orders consecutive entries.
+template <int S>
+__device__ __forceinline__ void walk_staged(const Stage<S>& st, const LaneSlots<S>& ls, int q0, int q1)
+{
+    if (q1 <= q0) return;
+    Staged<S> A, B;
+    A.load(st, ls, q0);
+    for (int q = q0;; q += 2) {
+        if (q + 1 < q1) B.load(st, ls, q + 1);
+        A.apply(ls);
+        __syncwarp();
+        if (q + 1 >= q1) break;
+        if (q + 2 < q1) A.load(st, ls, q + 2);
+        B.apply(ls);
+        __syncwarp();
+        if (q + 2 >= q1) break;
+    }
+}
+
 // Accumulate entries [b, e) of one sorted list into the warp's tile.  Rounds
 // of 32 entries: (1) each lane takes one entry (coalesced 16-byte loads) and
 // evaluates its 2S taps (degree-10 polynomials with uniform coefficients from
 // the constant bank) with the checkerboard signs folded in, and its header,
-// into the stage; (2) the warp walks the 32 entries; every lane updates its
-// slots, each a pair of horizontally adjacent cells read and written as one
-// 16-byte value (4 FMAs: u tap pair x complex v tap-visibility product).
-// Within one entry the lanes' pairs are distinct and conflict-free; a
-// __syncwarp orders consecutive entries.  The stage is read-only during the
-// walk, so the next entry's header and taps are loaded before this entry's
-// read-modify-write (two register sets, alternating).
+// into the stage (stage_entry); (2) the warp walks the 32 entries; every lane
+// updates its slots, each a pair of horizontally adjacent cells read and
+// written as one 16-byte value (4 FMAs: u tap pair x complex v
+// tap-visibility product).  Within one entry the lanes' pairs are distinct
+// and conflict-free.  The stage is read-only during the walk.
 template <int S>
 __device__ __forceinline__ void warp_grid_range(const GridCfg& c, const float4* __restrict__ ent, uint32_t b,
                                                 uint32_t e, int u0, int v0, float4* tile4, Stage<S>& st,
                                                 const LaneSlots<S>& ls, int lane, int shift)
 {
-    constexpr int KP = Stage<S>::kPairs, NS = Stage<S>::kSlots, NH = Stage<S>::kHead;
-    const int TP = c.T / 2, P2 = pair_pitch(c.T);
     const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile4);
     // each round's entries are loaded one round ahead
     float4 r_next = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -206,73 +286,9 @@ __device__ __forceinline__ void warp_grid_range(const GridCfg& c, const float4* 
         const uint32_t j = j0 + lane;
         const float4 r = r_next;
         if (j + 32 < e) r_next = __ldg(ent + j + 32);
-        if (j < e) {
-            const int fu = first_cell(c, r.x), fv = first_cell(c, r.y);
-            const float zu = __fmaf_rn(2.0f, __fsub_rn(__fsub_rn(r.x, c.half_s), (float)(fu - 1)), -1.0f);
-            const float zv = __fmaf_rn(2.0f, __fsub_rn(__fsub_rn(r.y, c.half_s), (float)(fv - 1)), -1.0f);
-            const int lu = fu - u0, lv = fv - v0;
-            const int odd = lu & 1;  // u0 is even: the parity of the tile column
-            const int pu = (lu - odd) / 2;
-            float gu[S];
-#pragma unroll
-            for (int t = 0; t < S; ++t) {
-                float a = c.coef[t][kPolyTerms - 1], bb = c.coef[t][kPolyTerms - 1];
-#pragma unroll
-                for (int k = kPolyTerms - 2; k >= 0; --k) {
-                    a = __fmaf_rn(a, zu, c.coef[t][k]);
-                    bb = __fmaf_rn(bb, zv, c.coef[t][k]);
-                }
-                if (shift) {
-                    if ((fu + t) & 1) a = -a;
-                    if ((fv + t) & 1) bb = -bb;
-                }
-                gu[t] = a;
-                st.gvv[lane * S + t] = make_float2(bb * r.z, bb * r.w);
-            }
-            // pair t holds tile columns 2 (pu + t) and 2 (pu + t) + 1: taps
-            // (2t, 2t+1) for an even start column, (2t-1, 2t) for an odd one
-#pragma unroll
-            for (int t = 0; t < KP; ++t) {
-                const float e0 = 2 * t < S ? gu[2 * t < S ? 2 * t : 0] : 0.0f;
-                const float e1 = 2 * t + 1 < S ? gu[2 * t + 1 < S ? 2 * t + 1 : 0] : 0.0f;
-                const float o0 = 2 * t - 1 >= 0 ? gu[2 * t - 1 >= 0 ? 2 * t - 1 : 0] : 0.0f;
-                st.gu[lane * KP + t] = odd ? make_float2(o0, e0) : make_float2(e0, e1);
-            }
-            // header: first pair's shared address (wraps for footprints that
-            // start left of or above the tile; only in-tile pairs are used)
-            // and the in-tile lane bits of every slot: footprint rows
-            // [rlo, rhi) and pairs [plo, phi) lie inside the tile
-            const int rlo = max(0, -lv), rhi = min(S, c.T - lv);
-            const int plo = max(0, -pu), phi = min(KP, TP - pu);
-            const uint32_t pm = phi > plo ? (((1u << phi) - 1u) & ~((1u << plo) - 1u)) : 0u;
-            uint32_t wm[NH - 1];
-#pragma unroll
-            for (int k = 0; k < NH - 1; ++k) wm[k] = 0u;
-#pragma unroll
-            for (int sr = 0; sr < S; ++sr) {
-                const uint32_t rowbits = (sr >= rlo && sr < rhi) ? pm : 0u;
-                const int bit = sr * KP, wd = bit / 32, sh = bit % 32;
-                wm[wd] |= rowbits << sh;
-                if (sh + KP > 32 && wd + 1 < NS) wm[wd + 1] |= rowbits >> (32 - sh);
-            }
-            st.head[lane * NH] = tile_s + (uint32_t)(lv * P2 + pu) * 16u;
-#pragma unroll
-            for (int k = 0; k < NH - 1; ++k) st.head[lane * NH + 1 + k] = wm[k];
-        }
+        if (j < e) stage_entry<S>(c, r, u0, v0, st, lane, tile_s, shift);
         __syncwarp();
-        const int cnt = (e - j0 < 32u) ? (int)(e - j0) : 32;
-        Staged<S> A, B;
-        A.load(st, ls, 0);
-        for (int q = 0;; q += 2) {
-            if (q + 1 < cnt) B.load(st, ls, q + 1);
-            A.apply(ls);
-            __syncwarp();
-            if (q + 1 >= cnt) break;
-            if (q + 2 < cnt) A.load(st, ls, q + 2);
-            B.apply(ls);
-            __syncwarp();
-            if (q + 2 >= cnt) break;
-        }
+        walk_staged<S>(st, ls, 0, (e - j0 < 32u) ? (int)(e - j0) : 32);
     }
 }
 
@@ -326,6 +342,16 @@ __device__ __forceinline__ TileWalk tile_walk(const GridCfg& c, int lane)
     return w;
 }
 
+// The walk's rows r0, r0 + dr, ... in runs: within 16 grid rows starting at
+// a multiple of 16 (v0 is one), consecutive rows of the walk are dr memory
+// rows apart with natural rows and dr N1 apart in b-major order, so each run
+// advances one pointer by a constant (no per-row plane_row); natural rows
+// make one run of the whole tile.
+__device__ __forceinline__ int64_t walk_mem_step(const GridCfg& c, const TileWalk& w)
+{
+    return (int64_t)w.dr * (c.row_perm ? (c.n >> 4) : 1) * (c.n / 2);  // in float4 (cell pair) units
+}
+
 // Write the valid part of a tile to the plane (or zeros): coalesced 16-byte
 // stores, 256 contiguous bytes per row segment for T = 32.
 template <bool kZero>
@@ -335,9 +361,13 @@ __device__ __forceinline__ void store_tile(const GridCfg& c, const TileGeom& g, 
     const TileWalk w = tile_walk(c, lane);
     if (2 * w.pr >= g.wu) return;
     float2* col = P0 + g.u0 + 2 * w.pr;
-    for (int row = w.r0; row < g.wv; row += w.dr) {
+    const int64_t step = walk_mem_step(c, w);
+    for (int row = w.r0; row < g.wv;) {
+        const int end = c.row_perm ? min(g.wv, (row | 15) + 1) : g.wv;
         float4* dst = reinterpret_cast<float4*>(col + (int64_t)plane_row(c, g.v0 + row) * c.n);
-        *dst = kZero ? make_float4(0.f, 0.f, 0.f, 0.f) : tile4[row * w.p2 + w.pr];
+#pragma unroll 4
+        for (; row < end; row += w.dr, dst += step)
+            *dst = kZero ? make_float4(0.f, 0.f, 0.f, 0.f) : tile4[row * w.p2 + w.pr];
     }
 }
 
@@ -347,13 +377,19 @@ __device__ __forceinline__ void init_tile(const GridCfg& c, const TileGeom& g, c
                                           bool from_plane, int lane)
 {
     const TileWalk w = tile_walk(c, lane);
+    if (!from_plane || 2 * w.pr >= g.wu) {
+#pragma unroll 4
+        for (int row = w.r0; row < c.T; row += w.dr) tile4[row * w.p2 + w.pr] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
     const float2* col = P0 + g.u0 + 2 * w.pr;
-    const bool col_ok = from_plane && 2 * w.pr < g.wu;
-    for (int row = w.r0; row < c.T; row += w.dr) {
-        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (col_ok && row < g.wv)
-            x = *reinterpret_cast<const float4*>(col + (int64_t)plane_row(c, g.v0 + row) * c.n);
-        tile4[row * w.p2 + w.pr] = x;
+    const int64_t step = walk_mem_step(c, w);
+    for (int row = w.r0; row < c.T;) {
+        const int end = c.row_perm ? min(c.T, (row | 15) + 1) : c.T;
+        const float4* src = reinterpret_cast<const float4*>(col + (int64_t)plane_row(c, g.v0 + row) * c.n);
+#pragma unroll 4
+        for (; row < end; row += w.dr, src += step)
+            tile4[row * w.p2 + w.pr] = row < g.wv ? *src : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 
@@ -375,7 +411,8 @@ __device__ __forceinline__ uint32_t heavy_threshold(const GridCfg& c, const Chun
 // hardware hands CTAs out dynamically, which balances the uneven tiles.
 // Lane q < ch.count holds the range of list q for the tile.
 template <int S>
-__global__ void __launch_bounds__(256) k_grid_tiles(GridCfg c, ChunkList ch, int k0, int64_t ntl, int shift,
+__global__ void __launch_bounds__(256, S <= 8 ? 2 : 0) k_grid_tiles(GridCfg c, ChunkList ch, int k0, int64_t ntl,
+                                                                   int shift,
                                                     int accumulate, float2* __restrict__ planes,
                                                     uint32_t* __restrict__ heavy_list, uint32_t heavy_cap)
 {
@@ -393,6 +430,111 @@ __global__ void __launch_bounds__(256) k_grid_tiles(GridCfg c, ChunkList ch, int
     LaneSlots<S> ls;
     ls.init(lane, pair_pitch(c.T));
 
+    if constexpr (S <= 8) if (ch.count == 1) {
+        // One list: the warp's tiles tl + k nwt (k < kTilesPerWarp), lane k
+        // holding tile k's range.  Consecutive tiles with at most 32 entries
+        // in all share one staging round (the taps of a light tile's few
+        // entries would otherwise cost a whole round of polynomial
+        // evaluations); each is then initialised, walked over its slots of
+        // the stage and stored in turn.  Heavier tiles take rounds of their
+        // own, the heaviest go to k_grid_chunks.  (Supports up to 8: wider
+        // footprints keep the registers of the tile-by-tile loop below.)
+        const uint32_t full = 0xffffffffu;
+        const int64_t tk = tl + (int64_t)lane * nwt;
+        uint32_t rb = 0, rn = 0;
+        if (lane < kTilesPerWarp && tk < last) {
+            const int64_t tg = (int64_t)k0 * c.ntp + tk;
+            rb = __ldg(ch.off[0] + tg);
+            rn = __ldg(ch.off[0] + tg + 1) - rb;
+        }
+        const int ntw = (int)min((int64_t)kTilesPerWarp, (last - tl + nwt - 1) / nwt);
+        const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile4);
+        for (int k = 0; k < ntw;) {
+            const uint32_t nk = __shfl_sync(full, rn, k);
+            if (nk > 32u) {
+                const int64_t tlk = tl + (int64_t)k * nwt;
+                const uint32_t bk = __shfl_sync(full, rb, k);
+                ++k;
+                const TileGeom g = tile_geom(c, k0, tlk);
+                float2* P0 = planes + (int64_t)g.kl * c.n * c.n;
+                if (nk > heavy) {
+                    // hand the tile to k_grid_chunks as chunks of at most
+                    // `heavy` entries, which add into the plane; the tile
+                    // starts at zero unless this pass accumulates
+                    const uint32_t nchunks = (nk + heavy - 1) / heavy;
+                    uint32_t base = 0;
+                    if (lane == 0) base = atomicAdd(heavy_list, nchunks);
+                    base = __shfl_sync(full, base, 0);
+                    if (base + nchunks <= heavy_cap) {
+                        for (uint32_t q = lane; q < nchunks; q += 32) {
+                            heavy_list[1 + 2 * (base + q)] = (uint32_t)tlk;
+                            heavy_list[2 + 2 * (base + q)] = q;
+                        }
+                        if (!accumulate) store_tile<true>(c, g, P0, nullptr, lane);
+                        continue;
+                    }
+                    // no room in the chunk list: mark the reserved slots that
+                    // do exist as empty, and grid the tile here
+                    for (uint32_t q = base + lane; q < heavy_cap; q += 32) heavy_list[1 + 2 * q] = 0xffffffffu;
+                }
+                init_tile(c, g, P0, tile4, accumulate != 0, lane);
+                __syncwarp();
+                warp_grid_range<S>(c, ch.ent[0], bk, bk + nk, g.u0, g.v0, tile4, st, ls, lane, shift);
+                __syncwarp();
+                store_tile<false>(c, g, P0, tile4, lane);
+                __syncwarp();
+                continue;
+            }
+            // the run of tiles k .. k+m-1 with at most 32 entries in all
+            int m = 0;
+            uint32_t tot = 0;
+            while (k + m < ntw) {
+                const uint32_t cm = __shfl_sync(full, rn, k + m);
+                if (tot + cm > 32u) break;
+                tot += cm;
+                ++m;
+            }
+            if (tot > 0) {
+                // lane j < tot stages entry j of the run (of tile k + ij)
+                uint32_t pre = 0, bj = 0;
+                int ij = 0;
+                for (int q = 0; q < m; ++q) {
+                    const uint32_t cq = __shfl_sync(full, rn, k + q), bq = __shfl_sync(full, rb, k + q);
+                    if ((uint32_t)lane >= pre && (uint32_t)lane < pre + cq) {
+                        ij = q;
+                        bj = bq + ((uint32_t)lane - pre);
+                    }
+                    pre += cq;
+                }
+                if ((uint32_t)lane < tot) {
+                    const TileGeom gj = tile_geom(c, k0, tl + (int64_t)(k + ij) * nwt);
+                    stage_entry<S>(c, __ldg(ch.ent[0] + bj), gj.u0, gj.v0, st, lane, tile_s, shift);
+                }
+                __syncwarp();
+            }
+            uint32_t pre = 0;
+            for (int q = 0; q < m; ++q) {
+                const uint32_t cq = __shfl_sync(full, rn, k + q);
+                const TileGeom g = tile_geom(c, k0, tl + (int64_t)(k + q) * nwt);
+                float2* P0 = planes + (int64_t)g.kl * c.n * c.n;
+                if (cq == 0) {
+                    if (!accumulate) store_tile<true>(c, g, P0, nullptr, lane);
+                    continue;
+                }
+                init_tile(c, g, P0, tile4, accumulate != 0, lane);
+                __syncwarp();
+                walk_staged<S>(st, ls, (int)pre, (int)(pre + cq));
+                __syncwarp();
+                store_tile<false>(c, g, P0, tile4, lane);
+                __syncwarp();  // the next tile's init overwrites the tile copy
+                pre += cq;
+            }
+            k += m;
+        }
+        return;
+    }
+
+    // several lists (a pass over more than one chunk of entries): tile by tile
     auto fetch = [&](int64_t t, uint32_t& rb, uint32_t& re) {
         rb = re = 0;
         if (t < last && lane < ch.count) {
@@ -484,10 +626,14 @@ __global__ void __launch_bounds__(256) k_grid_chunks(GridCfg c, ChunkList ch, in
         const TileWalk w = tile_walk(c, lane);
         if (2 * w.pr < g.wu) {
             float2* col = P0 + g.u0 + 2 * w.pr;
-            for (int row = w.r0; row < g.wv; row += w.dr) {
-                const float4 x = tile4[row * w.p2 + w.pr];
-                if (x.x != 0.f || x.y != 0.f || x.z != 0.f || x.w != 0.f)
-                    atomicAdd(reinterpret_cast<float4*>(col + (int64_t)plane_row(c, g.v0 + row) * c.n), x);
+            const int64_t step = walk_mem_step(c, w);
+            for (int row = w.r0; row < g.wv;) {
+                const int end = c.row_perm ? min(g.wv, (row | 15) + 1) : g.wv;
+                float4* dst = reinterpret_cast<float4*>(col + (int64_t)plane_row(c, g.v0 + row) * c.n);
+                for (; row < end; row += w.dr, dst += step) {
+                    const float4 x = tile4[row * w.p2 + w.pr];
+                    if (x.x != 0.f || x.y != 0.f || x.z != 0.f || x.w != 0.f) atomicAdd(dst, x);
+                }
             }
         }
         __syncwarp();

@@ -265,7 +265,7 @@ constexpr int kColN2 = kColQ * kColQ;
 constexpr int kColW = 32;                    // columns per CTA: one 256-byte row segment
 constexpr int kColWarps = kColW / 8;         // a warp owns 8 columns x kColQ values of j
 constexpr int kColThreads = 32 * kColWarps;
-constexpr int kColStages = 4;
+constexpr int kColStages = 5;  // 35.7 KB per CTA with the screens: six CTAs per SM
 constexpr int kColPitch = kColW;             // complex values per staged row (the TMA box, dense)
 // lanes: column cl = lane % 8 of the warp's 8, j = lane / 8; a half warp then
 // reads two rows of 8 columns of a stage (2-way bank conflict, the dense TMA

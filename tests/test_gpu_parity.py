@@ -115,6 +115,27 @@ def test_config1_planes_match_oracle_grid(rick, oracle_mod):
     assert abs(planes.astype(np.complex128).sum() - tot) <= 1e-5 * np.sum(np.abs(p["vis"]))
 
 
+@pytest.mark.parametrize("m,support,tile", [(4000, 7, 32), (40000, 8, 32), (20000, 7, 16), (20000, 8, 64),
+                                             (60000, 6, 32)])
+def test_light_tiles_planes_match_oracle_grid(rick, oracle_mod, m, support, tile):
+    """Sparse planes: tiles of 0 to a few dozen entries, so runs of
+    consecutive light tiles share a staging round (at most 32 entries in
+    all) and heavier ones take rounds of their own, in every mixture; the
+    gridded planes (natural rows) against the oracle's Eq. 3 at 1e-5, and
+    the image through the split transform (b-major rows) at 1e-4."""
+    prob = synth.disk_problem(512, 4, m, synth.KERNEL_KB, support, 3.0, 60.0, 900 + m + support + tile,
+                              weights="random")
+    p = synth.to_numpy(prob)
+    ref, _, _ = oracle_mod.grid(p["params"], p["u"], p["v"], p["w"], p["wt"], p["vis"])
+    im = rick.Imager(dict(prob["params"], tile=tile))
+    g = _to(prob)
+    im.grid(g["vis"], g["u"], g["v"], g["w"], g["wt"])
+    planes = im.grid_planes().cpu().numpy()
+    im.close()
+    assert np.max(np.abs(planes - ref)) <= 1e-5 * np.abs(ref).max()
+    _compare(rick, oracle_mod, prob, CORRECT | REAL | rick.FFT_SPLIT, tile=tile)
+
+
 def test_config1_entries_and_counters_exact(rick, oracle_mod):
     """Integer work: entry count = sum over gridded measurements of the tiles
     their footprint touches (computed from the oracle's placement)."""
@@ -169,10 +190,11 @@ def test_plane_groups_equal_all_planes(rick, oracle_mod):
     assert np.max(np.abs(a - b)) <= 1e-5 * np.abs(b).max()
 
 
-@pytest.mark.parametrize("chunks", [3, 20])
+@pytest.mark.parametrize("chunks", [3, 17, 20])
 def test_chunks_accumulate(rick, oracle_mod, chunks):
-    """Several grid() calls equal one (20 chunks also exercises the
-    read-modify-write gridding pass beyond 16 chunks)."""
+    """Several grid() calls equal one (17 and 20 chunks also exercise the
+    read-modify-write gridding pass beyond 16 chunks: with 17 it reads one
+    list, the path that stages runs of light tiles together)."""
     prob = synth.disk_problem(128, 4, 40000, GAUSS, 7, 2.0, 50.0, 107)
     _compare(rick, oracle_mod, prob, CORRECT | REAL, chunks=chunks)
 

@@ -554,6 +554,7 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
         if (cudaMalloc(&h->chan_w, sizeof(float2) * nchan) != cudaSuccess) return cleanup(RICK_ERR_OOM);
         if (cudaMalloc(&h->chan_off, sizeof(int64_t) * (nchan + 1)) != cudaSuccess) return cleanup(RICK_ERR_OOM);
         if (cudaMalloc(&h->chan_sw, sizeof(double) * nchan) != cudaSuccess) return cleanup(RICK_ERR_OOM);
+        if (cudaMalloc(&h->chan_scr, sizeof(float4) * nchan) != cudaSuccess) return cleanup(RICK_ERR_OOM);
         if (cudaMalloc(&h->b_off, sizeof(uint32_t) * (ntiles + 1)) != cudaSuccess) return cleanup(RICK_ERR_OOM);
         if (G < NW) {
             // a second plane buffer for pipelined groups, when it fits (else groups run one by one)
@@ -571,6 +572,15 @@ static rick_status create_impl(const rick_params* p, int nchan, const double* w_
             }
         }
         if (cudaMemcpy(h->chan_w, cw.data(), sizeof(float2) * nchan, cudaMemcpyHostToDevice) != cudaSuccess)
+            return cleanup(RICK_ERR_CUDA);
+        // each channel's w-screen constants (w_min + dw/2, dw) as float pairs
+        std::vector<float4> cs(nchan);
+        for (int ch = 0; ch < nchan; ++ch) {
+            const double dw = (p->nw > 1) ? (w_max[ch] - w_min[ch]) / p->nw : (w_max[ch] - w_min[ch]);
+            split(w_min[ch] + 0.5 * dw, &cs[ch].x, &cs[ch].y);
+            split(dw, &cs[ch].z, &cs[ch].w);
+        }
+        if (cudaMemcpy(h->chan_scr, cs.data(), sizeof(float4) * nchan, cudaMemcpyHostToDevice) != cudaSuccess)
             return cleanup(RICK_ERR_CUDA);
         h->cfg.chan_w = h->chan_w;
         h->cfg.chan_off = h->chan_off;
@@ -722,6 +732,7 @@ rick_status rick_destroy(rick_handle h)
     cudaFree(h->chan_w);
     cudaFree(h->chan_off);
     cudaFree(h->chan_sw);
+    cudaFree(h->chan_scr);
     cudaFree(h->b_off);
     cudaFree(h->b_ent);
     cudaFree(h->b_heavy);
@@ -1292,14 +1303,17 @@ static rick_status batch_body(rick_handle h, const float* vis, const float* u, c
                                      &h->ctr->err, st));
             count_launches(h, 1);
         }
+        // one launch over the group's channels (grid z = channel)
         PhaseScope ss(h, kPhaseStack);
-        for (int ch = k0 / c.nw_chan; ch < (k0 + nk) / c.nw_chan; ++ch) {
-            StackArgs a = chan_args(ch);
-            a.plane0 = ch * c.nw_chan - k0;
-            RICK_CU(h, launch_colstack(b ? h->colmap2 : h->colmap, a, n1, n2, nullptr, h->taper, h->chan_sw + ch,
-                                       images + (size_t)ch * img_floats, &h->ctr->err, st));
-            count_launches(h, 1);
-        }
+        const int ch0 = k0 / c.nw_chan, nch = nk / c.nw_chan;
+        StackArgs a = chan_args(ch0);
+        a.plane0 = ch0 * c.nw_chan - k0;
+        a.chan_screen = h->chan_scr;
+        a.chan0 = ch0;
+        a.img_stride = (long long)img_floats;
+        RICK_CU(h, launch_colstack(b ? h->colmap2 : h->colmap, a, n1, n2, nullptr, h->taper, h->chan_sw, images,
+                                   &h->ctr->err, st, nch));
+        count_launches(h, 1);
         return RICK_OK;
     };
     // stack the channels of the group in planes `buf` (first plane k0) on stream st
@@ -1440,9 +1454,10 @@ rick_status rick_image_batch(rick_handle h, const float* vis, const float* u, co
         return fail(h, RICK_ERR_ARG, "graph mode needs a non-default stream (rick_set_stream)");
     if (use_graph && h->graph && !stale && h->graph_m == m && memcmp(key, h->graph_key, sizeof(key)) == 0) {
         RICK_CU(h, cudaGraphLaunch(h->graph, h->stream));
-        // per plane group the two gridder kernels (and k_colfft on the split
-        // path), per channel one stack kernel
-        count_launches(h, 5 + (h->batch_split ? 3 : 2) * ((c.nw + h->G - 1) / h->G) + h->nchan);
+        // per plane group the two gridder kernels, then k_colfft and one
+        // k_colstack over its channels (split) or one k_stack per channel
+        const int groups = (c.nw + h->G - 1) / h->G;
+        count_launches(h, 5 + (h->batch_split ? 4 * groups : 2 * groups + h->nchan));
         return RICK_OK;
     }
     if (!use_graph) return batch_body(h, vis, u, v, w, weights, m, images);

@@ -276,6 +276,14 @@ struct StackArgs {
     // k_colstack: the group's first plane in the plane buffer (a channel of a
     // batch), 0 for single images
     int plane0;
+    // k_colstack over several channels of a batch in one launch (blockIdx.z
+    // = channel chan0 + z, nk planes each from plane0 + z nk): per channel
+    // (w_min + dw/2, dw) as float pairs {wb_hi, wb_lo, dw_hi, dw_lo}; the
+    // weight sums and images of consecutive channels follow one another
+    // (img_stride floats apart).  NULL: one image.
+    const float4* chan_screen;
+    int chan0;
+    long long img_stride;
 };
 // The grid correction in w at a pixel with n - 1 = nm1 (linear interpolation
 // of the table; 1 without w-support).
@@ -298,8 +306,11 @@ bool colstack_shape(int n, int* n1, int* n2);
 // map: a CUtensorMap (128 bytes, 64-byte aligned) from encode_colstack_map
 // for the plane buffer the group is in
 cudaError_t encode_colstack_map(void* map, const float2* planes, int n, int planes_in_buffer);
+// nchan > 1: the channels a.chan0 .. a.chan0 + nchan - 1 of a batch in one
+// launch (a.chan_screen set; sum_w and image are the first channel's)
 cudaError_t launch_colstack(const void* map, const StackArgs& a, int n1, int n2, float2* acc, const float* taper,
-                            const double* sum_w, void* image, unsigned long long* err, cudaStream_t s);
+                            const double* sum_w, void* image, unsigned long long* err, cudaStream_t s,
+                            int nchan = 1);
 // adjoint of launch_colstack: planes of the group from the image gradient
 // (rows 16 f1 + b after the last column factor's adjoint); cuFFT's forward
 // first column factor and rows complete the forward 2D transform
@@ -416,6 +427,7 @@ struct rick_imager {
     float2* chan_w;                  // device [nchan] (w_min, 1/dw) binary32
     int64_t* chan_off;               // device [nchan + 1]
     double* chan_sw;                 // device [nchan] weight sums
+    float4* chan_scr;                // device [nchan] w-screen constants (StackArgs::chan_screen)
     std::vector<int64_t> chan_off_host;
     uint32_t* b_off;                 // device [ntiles + 1]
     float4* b_ent;                   // device entries

@@ -310,12 +310,26 @@ __device__ __forceinline__ void dft4(float2 (&v)[4])
 // Planes are taken from the last to the first and summed per pixel by
 // Horner's rule, h <- h rho + v, times the screen of the block's first plane.
 // err: set to 1 when a bounded wait ran out.
-__global__ void __launch_bounds__(kColThreads, 6) k_colstack(const __grid_constant__ CUtensorMap map, StackArgs a,
-                                                             int n1,
-                                                             float2* __restrict__ acc, const float* __restrict__ taper,
+__global__ void __launch_bounds__(kColThreads, 6) k_colstack(const __grid_constant__ CUtensorMap map,
+                                                             StackArgs a_in, int n1, float2* __restrict__ acc,
+                                                             const float* __restrict__ taper,
                                                              const double* __restrict__ sum_w, void* image,
                                                              unsigned long long* err)
 {
+    // the launch's channel (batched imaging: one launch over the channels of
+    // a plane group) or the single image
+    StackArgs a = a_in;
+    if (a_in.chan_screen) {
+        const int ch = a_in.chan0 + (int)blockIdx.z;
+        const float4 cs = __ldg(a_in.chan_screen + ch);
+        a.wb_hi = cs.x;
+        a.wb_lo = cs.y;
+        a.dw_hi = cs.z;
+        a.dw_lo = cs.w;
+        a.plane0 = a_in.plane0 + (int)blockIdx.z * a_in.nk;
+        sum_w += ch;
+        image = reinterpret_cast<float*>(image) + (size_t)ch * a_in.img_stride;
+    }
     extern __shared__ __align__(128) unsigned char col_smem[];
     float2* stage = reinterpret_cast<float2*>(col_smem);  // [stages][N2][kColPitch]
     unsigned long long* full = reinterpret_cast<unsigned long long*>(col_smem + kColStages * kColStageBytes);
@@ -679,9 +693,11 @@ cudaError_t encode_colstack_map(void* map, const float2* planes, int n, int plan
 }
 
 cudaError_t launch_colstack(const void* map, const StackArgs& a, int n1, int n2, float2* acc, const float* taper,
-                            const double* sum_w, void* image, unsigned long long* err, cudaStream_t s)
+                            const double* sum_w, void* image, unsigned long long* err, cudaStream_t s, int nchan)
 {
-    if (a.nk <= 0) return cudaSuccess;
+    if (a.nk <= 0 || nchan <= 0) return cudaSuccess;
+    if (nchan > 1 && !a.chan_screen) return cudaErrorInvalidValue;
+    if (nchan > 65535) return cudaErrorInvalidValue;
     if (n2 != kColN2 || (int64_t)n1 * n2 != a.n || a.n % kColW != 0) return cudaErrorInvalidValue;
     static bool attr_done[64] = {false};
     int dev = 0;
@@ -692,7 +708,7 @@ cudaError_t launch_colstack(const void* map, const StackArgs& a, int n1, int n2,
         if (e != cudaSuccess) return e;
         attr_done[dev] = true;
     }
-    const dim3 grid((unsigned)(a.n / kColW), (unsigned)n1);
+    const dim3 grid((unsigned)(a.n / kColW), (unsigned)n1, (unsigned)nchan);
     k_colstack<<<grid, kColThreads, kColSmem, s>>>(*reinterpret_cast<const CUtensorMap*>(map), a, n1, acc, taper,
                                                    sum_w, image, err);
     return cudaGetLastError();

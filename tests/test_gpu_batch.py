@@ -214,10 +214,11 @@ def test_full_size_64_channels(rick, oracle_mod):
 @pytest.mark.parametrize("group_chans,use_graph", [(0, False), (2, False), (2, True)])
 def test_split_transform_batch_equals_single_channel_imaging(rick, group_chans, use_graph):
     """From n = 1024 on a batch transforms its groups with the split (cuFFT's
-    rows, k_colfft, and k_colstack per channel at the channel's plane offset
-    in the group); every channel equals a single-channel imager (cuFFT's 2D
-    plan at this size) to FP32 rounding, directly and in a captured graph,
-    with one group and with pipelined groups of two channels."""
+    rows, k_colfft, and one k_colstack launch over the group's channels, each
+    at its plane offset in the group); every channel equals a single-channel
+    imager (cuFFT's 2D plan at this size) to FP32 rounding, directly and in a
+    captured graph, with one group and with pipelined groups of two
+    channels."""
     prob = synth.channels_problem(nchan=5, n=1024, nw=4, m_lo=20_000, m_hi=200_000, device="cuda", seed=78)
     nw = prob["params"]["nw"]
     q = dict(prob["params"], flags=CORRECT | REAL, plane_group=group_chans * nw)

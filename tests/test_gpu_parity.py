@@ -123,16 +123,17 @@ def test_light_tiles_planes_match_oracle_grid(rick, oracle_mod, m, support, tile
     all) and heavier ones take rounds of their own, in every mixture.  The
     gridded planes (natural rows) equal those of a pass over two lists of
     the same measurements (tile by tile, no shared rounds) to FP32
-    reordering, and the oracle's Eq. 3 within the tap fit's error: per cell
-    2e-5 of the sum of the magnitudes of its terms (the fitted taps are
-    within 2e-6 of the kernel's peak; a cell of a sparse plane may be a
-    small sum of larger terms), plus 1e-6 of the peak.  The image through
-    the split transform (b-major rows) matches the oracle at 1e-4."""
+    reordering, and the oracle's Eq. 3 within the tap fit's error: each
+    fitted tap is within 2e-6 of the kernel's peak (the bound k_fit_taps
+    enforces), so a term of a cell is off by up to ~4e-6 of the term at the
+    footprint's centre, whatever the cell's own tap; a sparse plane's peak
+    cell holds one or a few terms while other cells sum several, hence 5e-5
+    of the peak here (the dense config-1 planes hold 1e-5).  The image
+    through the split transform (b-major rows) matches the oracle at 1e-4."""
     prob = synth.disk_problem(512, 4, m, synth.KERNEL_KB, support, 3.0, 60.0, 900 + m + support + tile,
                               weights="random")
     p = synth.to_numpy(prob)
     ref, _, _ = oracle_mod.grid(p["params"], p["u"], p["v"], p["w"], p["wt"], p["vis"])
-    mag, _, _ = oracle_mod.grid(p["params"], p["u"], p["v"], p["w"], p["wt"], np.abs(p["vis"]).astype(np.complex64))
     g = _to(prob)
     planes = []
     for parts in (1, 2):
@@ -145,8 +146,7 @@ def test_light_tiles_planes_match_oracle_grid(rick, oracle_mod, m, support, tile
         im.close()
     peak = np.abs(ref).max()
     assert np.max(np.abs(planes[0] - planes[1])) <= 1e-6 * peak
-    assert np.all(np.abs(planes[0] - ref) <= 2e-5 * np.abs(mag) + 1e-6 * peak), \
-        np.max(np.abs(planes[0] - ref) - 2e-5 * np.abs(mag))
+    assert np.max(np.abs(planes[0] - ref)) <= 5e-5 * peak
     _compare(rick, oracle_mod, prob, CORRECT | REAL | rick.FFT_SPLIT, tile=tile)
 
 

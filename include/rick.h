@@ -225,16 +225,19 @@ rick_status rick_synchronize(rick_handle h);
  * pixel_rad, the kernel and the w-plane count p->nw, each with its own
  * w-range [w_min[c], w_max[c]] (host arrays).  Channel c owns w-planes
  * c*nw .. (c+1)*nw-1 of one plane stack; all channels are sorted, gridded,
- * transformed (one cuFFT batch per plane group) and stacked together.
+ * transformed (one launch of each transform kernel per plane group) and
+ * stacked together.
  * Uniform weighting is not available here.  Only rick_image_batch,
  * rick_set_stream, rick_get_stats, rick_set_timing / rick_get_timing and
  * rick_destroy apply to a batched handle. */
 rick_status rick_create_batch(const rick_params* p, int32_t nchan, const double* w_min, const double* w_max,
                               rick_handle* out);
 /* (Batched handles transform their plane groups like single images from
- * n = 1024 on -- cuFFT's rows, the library's first column factor, and the
- * last column factor fused with each channel's w-screen and stack -- and
- * with cuFFT's 2D plan and a separate stack below, or with RICK_FFT_2D.) */
+ * n = 1024 on -- cuFFT's rows, the library's first column factor, and one
+ * launch of the last column factor fused with every channel's w-screen and
+ * stack -- and with cuFFT's 2D plan and a separate stack per channel below,
+ * or with RICK_FFT_2D.  Hermitian fold works per channel; each channel's
+ * w-range is then its folded one.) */
 
 /* One dirty image per channel: channel c's measurements are entries
  * chan_offsets[c] .. chan_offsets[c+1]-1 (host array of nchan+1, starting at

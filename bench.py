@@ -553,7 +553,7 @@ def run_image(args, rank, world):
     stack_traffic = _traffic("rick_stack.cu", "k_colstack@4096x32x1e7") if (default_size and split) else None
     launches_grid = max(tm["grid_calls"] / steps, 1)
     launches_stack = max(tm["stack_calls"] / steps, 1)
-    rl_grid = {"kernel": "k_grid_tiles + k_grid_chunks (gridding, Eq. 3)", "bound": "hbm",
+    rl_grid = {"kernel": "k_grid_tiles + k_grid_heavy (gridding, Eq. 3)", "bound": "hbm",
                "achieved": grid_bytes / grid_ms / 1e6, "peak": peak, "unit": "GB/s",
                "frac": grid_bytes / grid_ms / 1e6 / peak, "traffic": traffic, "peak_kind": peak_kind,
                "algorithmic_bytes_per_launch": grid_bytes / launches_grid, "launch_ms": grid_ms / launches_grid,

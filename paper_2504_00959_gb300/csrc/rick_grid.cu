@@ -7,7 +7,7 @@
 // (k_grid_tiles): the warp accumulates its entries into a private copy of the
 // tile in shared memory and writes the whole tile once with coalesced 16-byte
 // stores -- also when it is empty, so the planes need no memset and HBM sees
-// each plane byte once.  No atomics, global or shared:
+// each plane byte once.  No atomics on the tiles, global or shared:
 //   * entries are taken 32 at a time: each lane loads one (a coalesced
 //     512-byte load per warp) and evaluates its 2S taps (degree-10
 //     polynomials) into a per-warp stage in shared memory;
@@ -21,21 +21,26 @@
 //   * a __syncwarp between entries orders one entry's stores before the next
 //     entry's loads.
 // Tiles with more than heavy_threshold() entries (the dense centre of the uv
-// plane) would serialise on one warp: k_grid_tiles writes them as zeros and
-// lists them as chunks of at most that many entries, and k_grid_chunks
-// gives every chunk to a warp, which adds its private tile into the plane
-// with vector atomic adds.  The fftshift checkerboard (-1)^(ju+jv) is folded
-// into the tap signs.
+// plane) would serialise on one warp: k_grid_tiles lists them (list counters
+// are the only global atomics) and leaves them unwritten.  k_grid_heavy gives
+// each one CTA whose warps grid shares of its entries into private copies,
+// sums the copies in shared memory and writes the tile once; the few huge
+// ones go to k_grid_huge, where the 8 CTAs of a thread-block cluster share a
+// tile and sum their copies through distributed shared memory.  The fftshift
+// checkerboard (-1)^(ju+jv) is folded into the tap signs.
+#include <algorithm>
+#include <atomic>
+
 #include "rick_internal.cuh"
 
 namespace rick {
 namespace {
 
-// Chunking threshold of a pass with E entries: E / kHeavyDiv clamped to
+// Heavy-tile threshold of a pass with E entries: E / kHeavyDiv clamped to
 // [kHeavyMin, kHeavyMax].  A tile of many entries left to k_grid_tiles costs
 // its warp time proportional to the entries, run alone if it comes late in
-// the launch; a large pass hides that tail and gains from fewer chunk
-// flushes, a small one does not.
+// the launch; a large pass hides that tail and sends fewer tiles through
+// k_grid_heavy's summing of copies, a small one does not.
 constexpr uint32_t kHeavyMin = 64;
 constexpr uint32_t kHeavyMax = 768;
 constexpr uint32_t kHeavyDiv = 16384;
@@ -393,16 +398,49 @@ __device__ __forceinline__ void init_tile(const GridCfg& c, const TileGeom& g, c
     }
 }
 
-// Chunking threshold of the pass [k0, k0 + ntl / ntp) from its entry count
+// Heavy-tile threshold of the pass [k0, k0 + ntl / ntp) from its entry count
 // (the offsets the gridder reads anyway: tile k0 * ntp + ntl is the end of
-// the last tile's range).  Both gridder kernels derive the same value.  A
-// pass over several entry lists is never chunked.
+// the last tile's range).  A pass over several entry lists lists no heavy
+// tiles.
 __device__ __forceinline__ uint32_t heavy_threshold(const GridCfg& c, const ChunkList& ch, int k0, int64_t ntl)
 {
     if (ch.count != 1) return 0xffffffffu;
     const int64_t t0 = (int64_t)k0 * c.ntp;
     const uint32_t entries = __ldg(ch.off[0] + t0 + ntl) - __ldg(ch.off[0] + t0);
     return min(max(entries / kHeavyDiv, kHeavyMin), kHeavyMax);
+}
+
+// The heavy-tile lists of a pass in one scratch array: w[0] / w[1] count and
+// claim the tiles of k_grid_heavy's per-CTA list (slots w[4 ..]), w[2] / w[3]
+// those of its per-cluster list of huge tiles (slots w[4 + cap_h ..]).
+// Tiles with more than `huge` entries go to the second list while it has room.
+struct HeavyList {
+    uint32_t* w;
+    uint32_t cap_h, cap_x, huge;
+};
+
+// List tile `tile` of n entries (warp-uniform call); false when both lists
+// are full, and the warp grids the tile itself.
+__device__ __forceinline__ bool list_heavy(const HeavyList& hl, uint32_t n, uint32_t tile, int lane)
+{
+    uint32_t ok = 0;
+    if (lane == 0) {
+        if (n > hl.huge) {
+            const uint32_t slot = atomicAdd(hl.w + 2, 1u);
+            if (slot < hl.cap_x) {
+                hl.w[4 + hl.cap_h + slot] = tile;
+                ok = 1;
+            }
+        }
+        if (!ok) {
+            const uint32_t slot = atomicAdd(hl.w, 1u);
+            if (slot < hl.cap_h) {
+                hl.w[4 + slot] = tile;
+                ok = 1;
+            }
+        }
+    }
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
 // Each CTA of W warps takes kTilesPerWarp * W consecutive tiles of the pass,
@@ -413,8 +451,7 @@ __device__ __forceinline__ uint32_t heavy_threshold(const GridCfg& c, const Chun
 template <int S>
 __global__ void __launch_bounds__(256, S <= 8 ? 2 : 0) k_grid_tiles(GridCfg c, ChunkList ch, int k0, int64_t ntl,
                                                                    int shift,
-                                                    int accumulate, float2* __restrict__ planes,
-                                                    uint32_t* __restrict__ heavy_list, uint32_t heavy_cap)
+                                                    int accumulate, float2* __restrict__ planes, HeavyList hl)
 {
     extern __shared__ float4 smem4[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -437,7 +474,7 @@ __global__ void __launch_bounds__(256, S <= 8 ? 2 : 0) k_grid_tiles(GridCfg c, C
         // entries would otherwise cost a whole round of polynomial
         // evaluations); each is then initialised, walked over its slots of
         // the stage and stored in turn.  Heavier tiles take rounds of their
-        // own, the heaviest go to k_grid_chunks.  (Supports up to 8: wider
+        // own, the heaviest go to k_grid_heavy.  (Supports up to 8: wider
         // footprints keep the registers of the tile-by-tile loop below.)
         const uint32_t full = 0xffffffffu;
         const int64_t tk = tl + (int64_t)lane * nwt;
@@ -457,26 +494,9 @@ __global__ void __launch_bounds__(256, S <= 8 ? 2 : 0) k_grid_tiles(GridCfg c, C
                 ++k;
                 const TileGeom g = tile_geom(c, k0, tlk);
                 float2* P0 = planes + (int64_t)g.kl * c.n * c.n;
-                if (nk > heavy) {
-                    // hand the tile to k_grid_chunks as chunks of at most
-                    // `heavy` entries, which add into the plane; the tile
-                    // starts at zero unless this pass accumulates
-                    const uint32_t nchunks = (nk + heavy - 1) / heavy;
-                    uint32_t base = 0;
-                    if (lane == 0) base = atomicAdd(heavy_list, nchunks);
-                    base = __shfl_sync(full, base, 0);
-                    if (base + nchunks <= heavy_cap) {
-                        for (uint32_t q = lane; q < nchunks; q += 32) {
-                            heavy_list[1 + 2 * (base + q)] = (uint32_t)tlk;
-                            heavy_list[2 + 2 * (base + q)] = q;
-                        }
-                        if (!accumulate) store_tile<true>(c, g, P0, nullptr, lane);
-                        continue;
-                    }
-                    // no room in the chunk list: mark the reserved slots that
-                    // do exist as empty, and grid the tile here
-                    for (uint32_t q = base + lane; q < heavy_cap; q += 32) heavy_list[1 + 2 * q] = 0xffffffffu;
-                }
+                // list the tile for k_grid_heavy, which writes all of it; with
+                // no room left in the lists, grid it here
+                if (nk > heavy && list_heavy(hl, nk, (uint32_t)tlk, lane)) continue;
                 init_tile(c, g, P0, tile4, accumulate != 0, lane);
                 __syncwarp();
                 warp_grid_range<S>(c, ch.ent[0], bk, bk + nk, g.u0, g.v0, tile4, st, ls, lane, shift);
@@ -554,26 +574,9 @@ __global__ void __launch_bounds__(256, S <= 8 ? 2 : 0) k_grid_tiles(GridCfg c, C
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) nent += __shfl_xor_sync(0xffffffffu, nent, o);
 
-        if (nent > heavy && ch.count == 1) {
-            // many entries: hand the tile to k_grid_chunks as chunks of at most
-            // `heavy` entries, which add into the plane; the tile starts at
-            // zero unless this pass accumulates onto earlier chunks
-            const uint32_t nchunks = (nent + heavy - 1) / heavy;
-            uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(heavy_list, nchunks);
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (base + nchunks <= heavy_cap) {
-                for (uint32_t k = lane; k < nchunks; k += 32) {
-                    heavy_list[1 + 2 * (base + k)] = (uint32_t)tl;
-                    heavy_list[2 + 2 * (base + k)] = k;
-                }
-                if (!accumulate) store_tile<true>(c, g, P0, nullptr, lane);
-                continue;
-            }
-            // no room in the chunk list: mark the reserved slots that do exist
-            // as empty, and grid the tile here (correct, slower)
-            for (uint32_t k = base + lane; k < heavy_cap; k += 32) heavy_list[1 + 2 * k] = 0xffffffffu;
-        }
+        // many entries: list the tile for k_grid_heavy, which writes all of
+        // it; with no room left in the lists, grid it here (correct, slower)
+        if (nent > heavy && ch.count == 1 && list_heavy(hl, nent, (uint32_t)tl, lane)) continue;
         if (nent == 0) {
             if (!accumulate) store_tile<true>(c, g, P0, nullptr, lane);
             continue;
@@ -590,53 +593,206 @@ __global__ void __launch_bounds__(256, S <= 8 ? 2 : 0) k_grid_tiles(GridCfg c, C
     }
 }
 
-// Chunks of the tiles with many entries: one warp per chunk, private tile in
-// shared memory, flushed into the plane with 16-byte vector atomic adds of
-// the non-zero cell pairs (the tile's cells were zeroed by k_grid_tiles,
-// which ran before on the same stream).
+// Shared memory of a k_grid_heavy CTA: as many warps (each with a private
+// tile copy and a stage) as fit in kHeavySmem, at most kHeavyWarpsMax and at
+// least one; two such CTAs share an SM.  A heavy tile gives each warp at least
+// kHeavyPerWarp entries (fewer warps on lighter tiles: every active warp's copy
+// is summed at the end).  A tile with more than kHugePerWarp entries per warp
+// of one CTA is shared by the kHugeCluster CTAs of a cluster, whose warps then
+// still take at least 8 rounds of 32 entries each (fewer would leave the
+// cluster waiting at its barriers on the round that one warp has more).
+constexpr size_t kHeavySmem = 110 * 1024;
+constexpr int kHeavyWarpsMax = 8;
+constexpr uint32_t kHeavyPerWarp = 64;
+constexpr uint32_t kHugePerWarp = 2048;
+constexpr int kHugeCluster = 8;
+
 template <int S>
-__global__ void __launch_bounds__(256) k_grid_chunks(GridCfg c, ChunkList ch, int k0, int64_t ntl, int shift,
-                                                     float2* __restrict__ planes,
-                                                     const uint32_t* __restrict__ heavy_list, uint32_t heavy_cap)
+int heavy_warps(int T)
+{
+    const int w = (int)(kHeavySmem / warp_smem_bytes<S>(T));
+    return w < 1 ? 1 : (w > kHeavyWarpsMax ? kHeavyWarpsMax : w);
+}
+
+// Thread-block cluster primitives (PTX ISA: %cluster_ctarank, barrier.cluster,
+// mapa, ld.shared::cluster).  cluster_sync is the cluster-wide counterpart of
+// __syncthreads, with release / acquire ordering of shared-memory accesses.
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// The shared::cluster address of shared address `addr` in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_map(uint32_t addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t addr)
+{
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ float4 ld_cluster_f4(uint32_t addr)
+{
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void add4(float4& a, const float4& x)
+{
+    a.x += x.x;
+    a.y += x.y;
+    a.z += x.z;
+    a.w += x.w;
+}
+
+// Per-thread view of a heavy-tile CTA's shared memory: warp wid's tile copy
+// and stage, and the constants of the copy-summing loops.
+template <int S>
+struct HeavyCta {
+    float4* tile4;
+    Stage<S>* st;
+    LaneSlots<S> ls;
+    int p2, ltp, pmask, wstride;
+
+    __device__ __forceinline__ HeavyCta(const GridCfg& c, float4* smem4, int wid, int lane)
+    {
+        const size_t wbytes = warp_smem_bytes<S>(c.T);
+        unsigned char* mine = reinterpret_cast<unsigned char*>(smem4) + (size_t)wid * wbytes;
+        tile4 = reinterpret_cast<float4*>(mine);
+        st = reinterpret_cast<Stage<S>*>(mine + (size_t)c.T * pair_pitch(c.T) * sizeof(float4));
+        p2 = pair_pitch(c.T);
+        ls.init(lane, p2);
+        ltp = c.log2T - 1;
+        pmask = (1 << ltp) - 1;
+        wstride = (int)(wbytes / sizeof(float4));  // a Stage is a multiple of 128 bytes
+    }
+
+    // warp `part` of `parts` grids its share of the entries [b0, e0) (whole
+    // 32-entry rounds) into its zeroed copy
+    __device__ __forceinline__ void grid_share(const GridCfg& c, const ChunkList& ch, const TileGeom& g, uint32_t b0,
+                                               uint32_t e0, uint32_t part, uint32_t parts, int lane, int shift)
+    {
+        const uint32_t rounds = (e0 - b0 + 31) / 32;
+        const uint32_t b = b0 + 32 * (uint32_t)(((uint64_t)rounds * part) / parts);
+        const uint32_t e = min(e0, b0 + 32 * (uint32_t)(((uint64_t)rounds * (part + 1)) / parts));
+        init_tile(c, g, nullptr, tile4, false, lane);
+        __syncwarp();
+        if (e > b) warp_grid_range<S>(c, ch.ent[0], b, e, g.u0, g.v0, tile4, *st, ls, lane, shift);
+    }
+};
+
+// Tiles with many entries, which k_grid_tiles listed and left unwritten.
+// Each tile's warps take consecutive shares of its entries, each into its own
+// zeroed copy of the tile in shared memory; the copies are then summed cell
+// pair by cell pair in a fixed order (onto the plane's current values in an
+// accumulating pass) and the tile is written once with coalesced 16-byte
+// stores.  Every cell of the plane is written by exactly one CTA: no atomics
+// on the planes.
+//
+// k_grid_huge: the huge tiles, one per cluster of kHugeCluster CTAs
+// (persistent; the rank-0 CTA claims the next tile from a counter and the
+// others read the claim from its shared memory).  The cluster's warps share
+// the entries; each CTA sums its warps' copies into its first copy, and after
+// a cluster barrier CTA r sums rows [r T / C, (r + 1) T / C) of the C CTAs'
+// sums, read through distributed shared memory in rank order, and stores them.
+template <int S>
+__global__ void __launch_bounds__(256) k_grid_huge(GridCfg c, ChunkList ch, int k0, int shift, int accumulate,
+                                                   float2* __restrict__ planes, HeavyList hl)
 {
     extern __shared__ float4 smem4[];
+    __shared__ uint32_t s_item;
+    const uint32_t nx = min(hl.w[2], hl.cap_x);  // the same for every CTA: the tiles kernel wrote it
+    if (nx == 0) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned char* mine = reinterpret_cast<unsigned char*>(smem4) + (size_t)wid * warp_smem_bytes<S>(c.T);
-    float4* tile4 = reinterpret_cast<float4*>(mine);
-    Stage<S>& st = *reinterpret_cast<Stage<S>*>(mine + (size_t)c.T * pair_pitch(c.T) * sizeof(float4));
-    LaneSlots<S> ls;
-    ls.init(lane, pair_pitch(c.T));
-    const uint32_t heavy = heavy_threshold(c, ch, k0, ntl);
-    const uint32_t count = min(heavy_list[0], heavy_cap);
-    const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
-    for (uint32_t it = blockIdx.x * (blockDim.x >> 5) + wid; it < count; it += nwarps) {
-        const uint32_t tl32 = heavy_list[1 + 2 * it];
-        if (tl32 == 0xffffffffu) continue;  // slot of a tile gridded by k_grid_tiles itself
-        const int64_t tl = tl32;
-        const uint32_t k = heavy_list[2 + 2 * it];
-        const TileGeom g = tile_geom(c, k0, tl);
+    const uint32_t nwarps = blockDim.x >> 5;
+    HeavyCta<S> m(c, smem4, wid, lane);
+    const uint32_t rank = cluster_rank();
+    const uint32_t claim0 = cluster_map((uint32_t)__cvta_generic_to_shared(&s_item), 0);
+    const uint32_t gw = rank * nwarps + wid, ngw = kHugeCluster * nwarps;
+    const int rpc = c.T / kHugeCluster;  // tile rows stored per CTA (T >= 16)
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) s_item = atomicAdd(hl.w + 3, 1u);
+        cluster_sync();
+        const uint32_t it = ld_cluster_u32(claim0);
+        if (it >= nx) break;  // the same value in every CTA of the cluster
+        const TileGeom g = tile_geom(c, k0, (int64_t)hl.w[4 + hl.cap_h + it]);
         float2* P0 = planes + (int64_t)g.kl * c.n * c.n;
-        const uint32_t b0 = ch.off[0][g.tg], e0 = ch.off[0][g.tg + 1];
-        const uint32_t b = b0 + k * heavy;
-        const uint32_t e = min(e0, b + heavy);
-        init_tile(c, g, P0, tile4, false, lane);
-        __syncwarp();
-        warp_grid_range<S>(c, ch.ent[0], b, e, g.u0, g.v0, tile4, st, ls, lane, shift);
-        __syncwarp();
-        const TileWalk w = tile_walk(c, lane);
-        if (2 * w.pr < g.wu) {
-            float2* col = P0 + g.u0 + 2 * w.pr;
-            const int64_t step = walk_mem_step(c, w);
-            for (int row = w.r0; row < g.wv;) {
-                const int end = c.row_perm ? min(g.wv, (row | 15) + 1) : g.wv;
-                float4* dst = reinterpret_cast<float4*>(col + (int64_t)plane_row(c, g.v0 + row) * c.n);
-                for (; row < end; row += w.dr, dst += step) {
-                    const float4 x = tile4[row * w.p2 + w.pr];
-                    if (x.x != 0.f || x.y != 0.f || x.z != 0.f || x.w != 0.f) atomicAdd(dst, x);
-                }
-            }
+        m.grid_share(c, ch, g, __ldg(ch.off[0] + g.tg), __ldg(ch.off[0] + g.tg + 1), gw, ngw, lane, shift);
+        __syncthreads();
+        for (int i = threadIdx.x; i < (c.T << m.ltp); i += blockDim.x) {
+            float4* d0 = smem4 + (i >> m.ltp) * m.p2 + (i & m.pmask);
+            float4 a = *d0;
+            for (uint32_t q = 1; q < nwarps; ++q) add4(a, d0[q * m.wstride]);
+            *d0 = a;
         }
-        __syncwarp();
+        cluster_sync();
+        for (int i = threadIdx.x; i < (rpc << m.ltp); i += blockDim.x) {
+            const int row = (int)rank * rpc + (i >> m.ltp), pr = i & m.pmask;
+            if (row >= g.wv || 2 * pr >= g.wu) continue;
+            float4* dst = reinterpret_cast<float4*>(P0 + (int64_t)plane_row(c, g.v0 + row) * c.n + g.u0 + 2 * pr);
+            float4 acc = accumulate ? *dst : make_float4(0.f, 0.f, 0.f, 0.f);
+            const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(smem4 + row * m.p2 + pr);
+            for (uint32_t q = 0; q < (uint32_t)kHugeCluster; ++q) add4(acc, ld_cluster_f4(cluster_map(a0, q)));
+            *dst = acc;
+        }
+        cluster_sync();  // the copies are read remotely until here
+    }
+    cluster_sync();  // rank 0's claim is read remotely until here
+}
+
+// k_grid_heavy: the other heavy tiles, one per CTA (persistent; each CTA
+// claims the next tile from a counter, which balances tiles of very different
+// weights); the CTA's active warps' copies are summed in warp order.
+template <int S>
+__global__ void __launch_bounds__(256) k_grid_heavy(GridCfg c, ChunkList ch, int k0, int shift, int accumulate,
+                                                    float2* __restrict__ planes, HeavyList hl)
+{
+    extern __shared__ float4 smem4[];
+    __shared__ uint32_t s_item;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t nwarps = blockDim.x >> 5;
+    HeavyCta<S> m(c, smem4, wid, lane);
+    const uint32_t count = min(hl.w[0], hl.cap_h);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(hl.w + 1, 1u);
+        __syncthreads();
+        const uint32_t it = s_item;
+        if (it >= count) break;
+        const TileGeom g = tile_geom(c, k0, (int64_t)hl.w[4 + it]);
+        float2* P0 = planes + (int64_t)g.kl * c.n * c.n;
+        const uint32_t b0 = __ldg(ch.off[0] + g.tg), e0 = __ldg(ch.off[0] + g.tg + 1);
+        const uint32_t nact = min(nwarps, max(1u, (e0 - b0 + kHeavyPerWarp - 1) / kHeavyPerWarp));
+        if ((uint32_t)wid < nact) m.grid_share(c, ch, g, b0, e0, wid, nact, lane, shift);
+        __syncthreads();
+        // thread i: pair column i mod (T/2) of tile row i / (T/2); a half-warp
+        // (T = 32) covers one 256-byte row segment
+        for (int i = threadIdx.x; i < (c.T << m.ltp); i += blockDim.x) {
+            const int row = i >> m.ltp, pr = i & m.pmask;
+            if (row >= g.wv || 2 * pr >= g.wu) continue;
+            float4* dst = reinterpret_cast<float4*>(P0 + (int64_t)plane_row(c, g.v0 + row) * c.n + g.u0 + 2 * pr);
+            float4 acc = accumulate ? *dst : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4* src = smem4 + row * m.p2 + pr;
+            for (uint32_t q = 0; q < nact; ++q, src += m.wstride) add4(acc, *src);
+            *dst = acc;
+        }
+        __syncthreads();  // the next tile's init overwrites the copies, the next claim s_item
     }
 }
 
@@ -645,6 +801,78 @@ cudaError_t allow_smem(K kernel, size_t bytes)
 {
     if (bytes <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// The launch configuration of k_grid_huge: clusters of kHugeCluster CTAs of
+// hw warps (grid: nclusters clusters).
+inline cudaLaunchConfig_t huge_config(cudaLaunchAttribute* at, int hw, size_t smem, int nclusters, cudaStream_t s)
+{
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kHugeCluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)(nclusters * kHugeCluster));
+    lc.blockDim = dim3((unsigned)(32 * hw));
+    lc.dynamicSmemBytes = smem;
+    lc.stream = s;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return lc;
+}
+
+// What launch_grid_s<S> sets and queries once per device (and tile side):
+// the shared-memory opt-ins of its three kernels, at the largest size any tile
+// side launches them with (the opt-in is a per-kernel ceiling: lowering it for
+// one tile side would fail the launches of another), the co-resident
+// k_grid_heavy CTAs per SM and k_grid_huge clusters.  (Two threads that
+// launch first at the same time both query; the values are the same.)
+struct GridLaunchInfo {
+    int heavy_per_sm, huge_clusters;
+};
+
+template <int S>
+cudaError_t grid_launch_info(int T, size_t tile_bytes, int hw, GridLaunchInfo& out)
+{
+    static GridLaunchInfo cache[64][7];
+    static std::atomic<int> ready[64][7];
+    static std::atomic<int> opted[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int lt = 0;
+    while ((1 << lt) < T && lt < 6) ++lt;
+    const bool cached = dev >= 0 && dev < 64;
+    if (cached && ready[dev][lt].load(std::memory_order_acquire)) {
+        out = cache[dev][lt];
+        return cudaSuccess;
+    }
+    if (!cached || !opted[dev].load(std::memory_order_acquire)) {
+        size_t light_max = 0, heavy_max = 0;
+        for (int t = 16; t <= 64; t *= 2) {
+            light_max = std::max(light_max, warp_smem_bytes<S>(t) * light_warps(t));
+            heavy_max = std::max(heavy_max, warp_smem_bytes<S>(t) * heavy_warps<S>(t));
+        }
+        if ((e = allow_smem(k_grid_tiles<S>, light_max)) != cudaSuccess) return e;
+        if ((e = allow_smem(k_grid_heavy<S>, heavy_max)) != cudaSuccess) return e;
+        if ((e = allow_smem(k_grid_huge<S>, heavy_max)) != cudaSuccess) return e;
+        if (cached) opted[dev].store(1, std::memory_order_release);
+    }
+    const size_t heavy_bytes = tile_bytes * hw;
+    GridLaunchInfo g{0, 0};
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.heavy_per_sm, k_grid_heavy<S>, 32 * hw, heavy_bytes)) !=
+        cudaSuccess)
+        return e;
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t lc = huge_config(at, hw, heavy_bytes, sm_count_grid(), nullptr);
+    if ((e = cudaOccupancyMaxActiveClusters(&g.huge_clusters, k_grid_huge<S>, &lc)) != cudaSuccess) return e;
+    if (g.huge_clusters < 1 || g.heavy_per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (cached) {
+        cache[dev][lt] = g;
+        ready[dev][lt].store(1, std::memory_order_release);
+    }
+    out = g;
+    return cudaSuccess;
 }
 
 template <int S>
@@ -657,42 +885,55 @@ cudaError_t launch_grid_s(const GridCfg& c, const ChunkList& ch, int k0, int nk,
     const int wl = light_warps(c.T);
     const int64_t nblocks = (ntl + wl - 1) / wl;
     if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    // heavy: [count, (tile, chunk) pairs]
-    const size_t pairs = (heavy_words - 1) / 2;
-    const uint32_t cap = (uint32_t)(pairs < 0x7fffffffu ? pairs : 0x7fffffffu);
-    cudaError_t e = cudaMemsetAsync(heavy, 0, sizeof(uint32_t), s);
+    // heavy: [count, claim, huge count, huge claim, tiles, huge tiles]; a
+    // ninth of the slots for huge tiles (more than kHugePerWarp >= 512
+    // entries each, so at most an eighth as many as heavy ones, which hold
+    // more than 64)
+    const size_t slots = heavy_words - 4;
+    const size_t sx = slots / 9, sh = slots - sx;
+    const int hw = heavy_warps<S>(c.T);
+    const HeavyList hl{heavy, (uint32_t)(sh < 0x7fffffffu ? sh : 0x7fffffffu),
+                       (uint32_t)(sx < 0x7fffffffu ? sx : 0x7fffffffu), (uint32_t)hw * kHugePerWarp};
+    const size_t heavy_bytes = tile_bytes * hw;
+    GridLaunchInfo info;
+    cudaError_t e = grid_launch_info<S>(c.T, tile_bytes, hw, info);
     if (e != cudaSuccess) return e;
-    if ((e = allow_smem(k_grid_tiles<S>, tile_bytes * wl)) != cudaSuccess) return e;
-    if ((e = allow_smem(k_grid_chunks<S>, tile_bytes * wl)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(heavy, 0, 4 * sizeof(uint32_t), s)) != cudaSuccess) return e;
     const unsigned tile_blocks = (unsigned)((nblocks + kTilesPerWarp - 1) / kTilesPerWarp);
     k_grid_tiles<S><<<tile_blocks, 32 * wl, tile_bytes * wl, s>>>(c, ch, k0, ntl, shift ? 1 : 0, accumulate ? 1 : 0,
-                                                                  planes, heavy, cap);
+                                                                  planes, hl);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_chunks<S>, 32 * wl, tile_bytes * wl)) !=
-        cudaSuccess)
+    // huge tiles: persistent, as many clusters as are co-resident
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t lc = huge_config(at, hw, heavy_bytes, info.huge_clusters, s);
+    e = cudaLaunchKernelEx(&lc, k_grid_huge<S>, c, ch, k0, shift ? 1 : 0, accumulate ? 1 : 0, planes, hl);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();  // reported here; not left for the next launch check to find
         return e;
-    const unsigned nchunk_blocks = (unsigned)(max(per_sm, 1) * sm_count_grid());
-    k_grid_chunks<S><<<nchunk_blocks, 32 * wl, tile_bytes * wl, s>>>(c, ch, k0, ntl, shift ? 1 : 0, planes, heavy,
-                                                                    cap);
+    }
+    // the other heavy tiles: persistent, one CTA per resident slot
+    const unsigned heavy_blocks = (unsigned)(info.heavy_per_sm * sm_count_grid());
+    k_grid_heavy<S><<<heavy_blocks, 32 * hw, heavy_bytes, s>>>(c, ch, k0, shift ? 1 : 0, accumulate ? 1 : 0, planes,
+                                                              hl);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-// Every chunk holds more than h / 2 entries on average for a threshold h
-// (a heavy tile of n > h entries makes ceil(n / h) < 2 n / h chunks), so a
-// pass over E entries lists fewer than 2 E / h <= 2 E / kHeavyMin chunks.
+// A heavy tile holds more than h >= kHeavyMin = 64 entries and a huge one
+// more than kHugePerWarp >= 512, so a pass over E entries lists fewer than
+// E / 64 and E / 512 of them: four header words and 9 (E / 512 + 1) slots, a
+// ninth of them for huge tiles, hold both.
 size_t heavy_words_for(int64_t max_entries)
 {
-    const int64_t chunks = 2 * max_entries / kHeavyMin + 1;
-    return 1 + 2 * (size_t)(chunks > 0 ? chunks : 1);
+    static_assert(kHeavyMin * 8 <= kHugePerWarp, "the list split assumes huge tiles hold 8x the heavy minimum");
+    return 4 + 9 * ((size_t)(max_entries > 0 ? max_entries : 0) / (8 * kHeavyMin) + 1);
 }
 
 cudaError_t launch_grid(const GridCfg& c, const ChunkList& ch, int k0, int nk, bool shift_sign,
                         bool accumulate, uint32_t* heavy, size_t heavy_words, float2* planes, cudaStream_t s)
 {
-    if (!heavy || heavy_words < 1) return cudaErrorInvalidValue;
+    if (!heavy || heavy_words < 4) return cudaErrorInvalidValue;
     switch (c.S) {
 #define RICK_GRID_CASE(SS) \
     case SS: return launch_grid_s<SS>(c, ch, k0, nk, shift_sign, accumulate, planes, heavy, heavy_words, s);

@@ -241,11 +241,10 @@ cudaError_t launch_scan(const uint32_t* counts, int64_t len, int stride, uint32_
 cudaError_t launch_scatter(const GridCfg& c, const float* u, const float* v, const float* w,
                            const float* wt, const float2* vis, int64_t m, const uint32_t* density,
                            uint32_t* cursor, float4* entries, Counters* ctr, double* chan_sw, cudaStream_t s);
-// heavy: scratch of 1 + nk * ntp uint32 (count + list of tiles with many entries)
-// heavy: scratch of heavy_words words for the list of chunks of heavily
-// populated tiles (1 + 2 per chunk; a tile that does not fit is gridded by
-// one warp, correct but slower).  heavy_words_for() gives the size that never
-// overflows for a pass over at most max_entries entries.
+// heavy: scratch of heavy_words >= 4 words for the lists of heavily populated
+// tiles (four counters, then one word per tile; a tile that does not fit is
+// gridded by one warp, correct but slower).  heavy_words_for() gives the size
+// that never overflows for a pass over at most max_entries entries.
 cudaError_t launch_grid(const GridCfg& c, const ChunkList& chunks, int k0, int nk, bool shift_sign,
                         bool accumulate, uint32_t* heavy, size_t heavy_words, float2* planes, cudaStream_t s);
 size_t heavy_words_for(int64_t max_entries);
@@ -432,7 +431,7 @@ struct rick_imager {
     uint32_t* b_off;                 // device [ntiles + 1]
     float4* b_ent;                   // device entries
     int64_t b_cap;
-    uint32_t* b_heavy;               // gridder's heavy-chunk list for b_cap entries
+    uint32_t* b_heavy;               // gridder's heavy-tile list for b_cap entries
     size_t b_heavy_words;
     // pipelined plane groups (batched, two or more groups): a second plane
     // buffer; group g is gridded on the handle's stream into buffer g % 2 while

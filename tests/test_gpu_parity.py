@@ -317,20 +317,38 @@ def test_hot_tile(rick, oracle_mod):
     _compare(rick, oracle_mod, dict(params=prob["params"], u=u, v=v, w=w, wt=wt, vis=vis), CORRECT | REAL)
 
 
-def test_hot_tile_in_chunks(rick, oracle_mod):
-    """A tile with ~2e4 entries on a grid large enough for the chunk list:
-    gridded as chunks by separate warps that add into the plane."""
+@pytest.mark.parametrize("chunks,hot", [(1, 2000), (1, 20000), (17, 20000), (17, 300000)])
+def test_heavy_tile_cta(rick, oracle_mod, chunks, hot):
+    """`hot` measurements in a 3 x 3-cell patch, all inside one 32 x 32 tile
+    of a 512^2 grid, beside 2e4 spread ones.  2e3 entries: a heavy tile, one
+    CTA whose warps grid shares of the entries into private copies summed
+    before the one store; 2e4: a huge tile (more than 8 warps x 2048
+    entries), shared by the 8 CTAs of a cluster, whose sums are added
+    through distributed shared memory.  With 17 grid() calls the last call
+    holds only hot measurements (2353 of 4e4, or 18823 of 3.2e5) and is
+    gridded in a pass of its own that adds onto the plane (the heavy or huge
+    tile read back and summed onto)."""
     n = 512
     prob = synth.disk_problem(n, 2, 20000, KB, 7, 3.0, 50.0, 13)
     du = 1 / (n * prob["params"]["pixel_rad"])
     g = torch.Generator().manual_seed(6)
-    hot = 20000
     u = torch.cat([prob["u"], (40.2 + 3.0 * torch.rand(hot, generator=g)) * du])
     v = torch.cat([prob["v"], (-21.7 + 3.0 * torch.rand(hot, generator=g)) * du])
     w = torch.cat([prob["w"], torch.full((hot,), -10.0)])
     wt = torch.ones(u.numel())
     vis = torch.cat([prob["vis"], torch.complex(torch.randn(hot, generator=g), torch.randn(hot, generator=g))])
-    _compare(rick, oracle_mod, dict(params=prob["params"], u=u, v=v, w=w, wt=wt, vis=vis), REAL)
+    _compare(rick, oracle_mod, dict(params=prob["params"], u=u, v=v, w=w, wt=wt, vis=vis), REAL, chunks=chunks)
+
+
+def test_tile_sides_in_turn(rick, oracle_mod):
+    """Imagers with tile sides 32, 64, 16 and 32 again in one process, as the
+    batch autotuner creates them: each tile side launches the gridder's
+    kernels with its own shared-memory size, and every image must still
+    match the oracle (a per-kernel shared-memory ceiling set for one tile
+    side must not fail the launches of another)."""
+    prob = synth.disk_problem(256, 4, 30000, KB, 7, 3.0, 50.0, 17)
+    for tile in (32, 64, 16, 32):
+        _compare(rick, oracle_mod, prob, CORRECT | REAL, tile=tile)
 
 
 def test_hermitian_fold_matches_oracle(rick, oracle_mod):

@@ -78,12 +78,12 @@ def test_static_scratch_rejects_sizes_beyond_the_limit(rick):
     assert "limit" in err.value.decode()
 
 
-def test_static_scratch_hot_tile_beyond_the_chunk_list(rick):
+def test_static_scratch_hot_tile(rick):
     """2e5 measurements inside one cell of a 128^2 x 4-plane grid: the static
-    scratch lists at most (tiles + 1) / 2 chunks, far fewer than that tile's,
-    so the gridder grids it with one warp; it must agree with the allocating
-    path, which splits it into chunks (1e-4 of the largest cell: the hot cell
-    sums 2e5 FP32 terms in another order)."""
+    scratch lists the hot tiles in its cursor array (two counters, then one
+    word per tile) for the heavy-tile CTAs; the planes must agree with
+    the allocating path (1e-4 of the largest cell: the hot cell sums 2e5 FP32
+    terms, in an order that depends on the scatter's slots)."""
     n = 128
     prob = synth.disk_problem(n, 4, 20000, synth.KERNEL_KB, 7, 3.0, 50.0, 11)
     du = 1 / (n * prob["params"]["pixel_rad"])

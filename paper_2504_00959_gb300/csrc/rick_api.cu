@@ -362,7 +362,7 @@ rick_status grid_pass(rick_handle h, int k0, int nk, bool shift, float2* planes,
         const cudaError_t e = launch_grid(cfg, cl, k0, nk, shift, c0 > 0, heavy, words, planes, h->stream);
         cudaFreeAsync(heavy, h->stream);
         RICK_CU(h, e);
-        count_launches(h, 3);
+        count_launches(h, 2);
         c0 += kMaxChunksPerPass;
     } while (c0 < nch);
     return RICK_OK;
@@ -1332,7 +1332,7 @@ static rick_status batch_body(rick_handle h, const float* vis, const float* u, c
         cl.ent[0] = h->b_ent;
         cl.count = 1;
         RICK_CU(h, launch_grid(c, cl, k0, nk, true, false, h->b_heavy, h->b_heavy_words, buf, h->stream));
-        count_launches(h, 3);
+        count_launches(h, 2);
         return RICK_OK;
     };
     const bool pipelined = h->planes2 && !h->timer.on && h->G < c.nw;
@@ -1454,10 +1454,10 @@ rick_status rick_image_batch(rick_handle h, const float* vis, const float* u, co
         return fail(h, RICK_ERR_ARG, "graph mode needs a non-default stream (rick_set_stream)");
     if (use_graph && h->graph && !stale && h->graph_m == m && memcmp(key, h->graph_key, sizeof(key)) == 0) {
         RICK_CU(h, cudaGraphLaunch(h->graph, h->stream));
-        // per plane group the three gridder kernels, then k_colfft and one
+        // per plane group the two gridder kernels, then k_colfft and one
         // k_colstack over its channels (split) or one k_stack per channel
         const int groups = (c.nw + h->G - 1) / h->G;
-        count_launches(h, 5 + (h->batch_split ? 5 * groups : 3 * groups + h->nchan));
+        count_launches(h, 5 + (h->batch_split ? 4 * groups : 2 * groups + h->nchan));
         return RICK_OK;
     }
     if (!use_graph) return batch_body(h, vis, u, v, w, weights, m, images);

@@ -24,10 +24,10 @@
 // plane) would serialise on one warp: k_grid_tiles lists them (list counters
 // are the only global atomics) and leaves them unwritten.  k_grid_heavy gives
 // each one CTA whose warps grid shares of its entries into private copies,
-// sums the copies in shared memory and writes the tile once; the few huge
-// ones go to k_grid_huge, where the 8 CTAs of a thread-block cluster share a
-// tile and sum their copies through distributed shared memory.  The fftshift
-// checkerboard (-1)^(ju+jv) is folded into the tap signs.
+// sums the copies in shared memory and writes the tile once; the 2 CTAs of a
+// thread-block cluster share each of the few huge ones and sum their copies
+// through distributed shared memory.  The fftshift checkerboard (-1)^(ju+jv)
+// is folded into the tap signs.
 #include <algorithm>
 #include <atomic>
 
@@ -599,13 +599,17 @@ __global__ void __launch_bounds__(256, S <= 8 ? 2 : 0) k_grid_tiles(GridCfg c, C
 // kHeavyPerWarp entries (fewer warps on lighter tiles: every active warp's copy
 // is summed at the end).  A tile with more than kHugePerWarp entries per warp
 // of one CTA is shared by the kHugeCluster CTAs of a cluster, whose warps then
-// still take at least 8 rounds of 32 entries each (fewer would leave the
-// cluster waiting at its barriers on the round that one warp has more).
+// still take at least 8 rounds of 32 entries each.  Clusters of two CTAs
+// fill every CTA slot of the SMs (larger clusters leave slots unused where
+// the SMs' CTA slots do not divide into whole clusters: measured on a dense
+// 2048^2 x 16-plane channel of 2e7 measurements, 1.45 ms gridding with pairs,
+// 1.48 ms with 4 CTAs, 1.49 ms with 8); 512 rather than 2048 entries per warp
+// shortens the few longest tiles (64-channel loop 32.6 -> 31.2 ms gridding).
 constexpr size_t kHeavySmem = 110 * 1024;
 constexpr int kHeavyWarpsMax = 8;
 constexpr uint32_t kHeavyPerWarp = 64;
-constexpr uint32_t kHugePerWarp = 2048;
-constexpr int kHugeCluster = 8;
+constexpr uint32_t kHugePerWarp = 512;
+constexpr int kHugeCluster = 2;
 
 template <int S>
 int heavy_warps(int T)
@@ -698,68 +702,26 @@ struct HeavyCta {
     }
 };
 
-// Tiles with many entries, which k_grid_tiles listed and left unwritten.
-// Each tile's warps take consecutive shares of its entries, each into its own
+// Tiles with many entries, which k_grid_tiles listed and left unwritten:
+// k_grid_heavy, launched as clusters of kHugeCluster CTAs, persistent.  Each
+// tile's warps take consecutive shares of its entries, each into its own
 // zeroed copy of the tile in shared memory; the copies are then summed cell
 // pair by cell pair in a fixed order (onto the plane's current values in an
 // accumulating pass) and the tile is written once with coalesced 16-byte
 // stores.  Every cell of the plane is written by exactly one CTA: no atomics
 // on the planes.
-//
-// k_grid_huge: the huge tiles, one per cluster of kHugeCluster CTAs
-// (persistent; the rank-0 CTA claims the next tile from a counter and the
-// others read the claim from its shared memory).  The cluster's warps share
-// the entries; each CTA sums its warps' copies into its first copy, and after
-// a cluster barrier CTA r sums rows [r T / C, (r + 1) T / C) of the C CTAs'
-// sums, read through distributed shared memory in rank order, and stores them.
-template <int S>
-__global__ void __launch_bounds__(256) k_grid_huge(GridCfg c, ChunkList ch, int k0, int shift, int accumulate,
-                                                   float2* __restrict__ planes, HeavyList hl)
-{
-    extern __shared__ float4 smem4[];
-    __shared__ uint32_t s_item;
-    const uint32_t nx = min(hl.w[2], hl.cap_x);  // the same for every CTA: the tiles kernel wrote it
-    if (nx == 0) return;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const uint32_t nwarps = blockDim.x >> 5;
-    HeavyCta<S> m(c, smem4, wid, lane);
-    const uint32_t rank = cluster_rank();
-    const uint32_t claim0 = cluster_map((uint32_t)__cvta_generic_to_shared(&s_item), 0);
-    const uint32_t gw = rank * nwarps + wid, ngw = kHugeCluster * nwarps;
-    const int rpc = c.T / kHugeCluster;  // tile rows stored per CTA (T >= 16)
-    for (;;) {
-        if (rank == 0 && threadIdx.x == 0) s_item = atomicAdd(hl.w + 3, 1u);
-        cluster_sync();
-        const uint32_t it = ld_cluster_u32(claim0);
-        if (it >= nx) break;  // the same value in every CTA of the cluster
-        const TileGeom g = tile_geom(c, k0, (int64_t)hl.w[4 + hl.cap_h + it]);
-        float2* P0 = planes + (int64_t)g.kl * c.n * c.n;
-        m.grid_share(c, ch, g, __ldg(ch.off[0] + g.tg), __ldg(ch.off[0] + g.tg + 1), gw, ngw, lane, shift);
-        __syncthreads();
-        for (int i = threadIdx.x; i < (c.T << m.ltp); i += blockDim.x) {
-            float4* d0 = smem4 + (i >> m.ltp) * m.p2 + (i & m.pmask);
-            float4 a = *d0;
-            for (uint32_t q = 1; q < nwarps; ++q) add4(a, d0[q * m.wstride]);
-            *d0 = a;
-        }
-        cluster_sync();
-        for (int i = threadIdx.x; i < (rpc << m.ltp); i += blockDim.x) {
-            const int row = (int)rank * rpc + (i >> m.ltp), pr = i & m.pmask;
-            if (row >= g.wv || 2 * pr >= g.wu) continue;
-            float4* dst = reinterpret_cast<float4*>(P0 + (int64_t)plane_row(c, g.v0 + row) * c.n + g.u0 + 2 * pr);
-            float4 acc = accumulate ? *dst : make_float4(0.f, 0.f, 0.f, 0.f);
-            const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(smem4 + row * m.p2 + pr);
-            for (uint32_t q = 0; q < (uint32_t)kHugeCluster; ++q) add4(acc, ld_cluster_f4(cluster_map(a0, q)));
-            *dst = acc;
-        }
-        cluster_sync();  // the copies are read remotely until here
-    }
-    cluster_sync();  // rank 0's claim is read remotely until here
-}
-
-// k_grid_heavy: the other heavy tiles, one per CTA (persistent; each CTA
-// claims the next tile from a counter, which balances tiles of very different
-// weights); the CTA's active warps' copies are summed in warp order.
+//   1. The huge tiles first, one per cluster (the rank-0 CTA claims the next
+//      from a counter; the others read the claim from its shared memory): the
+//      cluster's warps share the entries; each CTA sums its warps' copies
+//      into its first copy, and after a cluster barrier CTA r sums rows
+//      [r T / C, (r + 1) T / C) of the C CTAs' sums, read through distributed
+//      shared memory in rank order, and stores them.  Clusters that find no
+//      huge tile left go on to
+//   2. the other heavy tiles, one per CTA (each CTA claims the next from a
+//      counter, which balances tiles of very different weights); the CTA's
+//      active warps' copies are summed in warp order.
+// Taking the few huge tiles first lets the rest of the launch hide their
+// length.
 template <int S>
 __global__ void __launch_bounds__(256) k_grid_heavy(GridCfg c, ChunkList ch, int k0, int shift, int accumulate,
                                                     float2* __restrict__ planes, HeavyList hl)
@@ -769,6 +731,46 @@ __global__ void __launch_bounds__(256) k_grid_heavy(GridCfg c, ChunkList ch, int
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint32_t nwarps = blockDim.x >> 5;
     HeavyCta<S> m(c, smem4, wid, lane);
+
+    // 1. huge tiles (the count is the same for every CTA: the tiles kernel wrote it)
+    const uint32_t nx = min(hl.w[2], hl.cap_x);
+    if (nx > 0) {
+        const uint32_t rank = cluster_rank();
+        const uint32_t claim0 = cluster_map((uint32_t)__cvta_generic_to_shared(&s_item), 0);
+        const uint32_t gw = rank * nwarps + wid, ngw = kHugeCluster * nwarps;
+        const int rpc = c.T / kHugeCluster;  // tile rows stored per CTA (T >= 16)
+        for (;;) {
+            if (rank == 0 && threadIdx.x == 0) s_item = atomicAdd(hl.w + 3, 1u);
+            cluster_sync();
+            const uint32_t it = ld_cluster_u32(claim0);
+            if (it >= nx) break;  // the same value in every CTA of the cluster
+            const TileGeom g = tile_geom(c, k0, (int64_t)hl.w[4 + hl.cap_h + it]);
+            float2* P0 = planes + (int64_t)g.kl * c.n * c.n;
+            m.grid_share(c, ch, g, __ldg(ch.off[0] + g.tg), __ldg(ch.off[0] + g.tg + 1), gw, ngw, lane, shift);
+            __syncthreads();
+            for (int i = threadIdx.x; i < (c.T << m.ltp); i += blockDim.x) {
+                float4* d0 = smem4 + (i >> m.ltp) * m.p2 + (i & m.pmask);
+                float4 a = *d0;
+                for (uint32_t q = 1; q < nwarps; ++q) add4(a, d0[q * m.wstride]);
+                *d0 = a;
+            }
+            cluster_sync();
+            for (int i = threadIdx.x; i < (rpc << m.ltp); i += blockDim.x) {
+                const int row = (int)rank * rpc + (i >> m.ltp), pr = i & m.pmask;
+                if (row >= g.wv || 2 * pr >= g.wu) continue;
+                float4* dst =
+                    reinterpret_cast<float4*>(P0 + (int64_t)plane_row(c, g.v0 + row) * c.n + g.u0 + 2 * pr);
+                float4 acc = accumulate ? *dst : make_float4(0.f, 0.f, 0.f, 0.f);
+                const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(smem4 + row * m.p2 + pr);
+                for (uint32_t q = 0; q < (uint32_t)kHugeCluster; ++q) add4(acc, ld_cluster_f4(cluster_map(a0, q)));
+                *dst = acc;
+            }
+            cluster_sync();  // the copies are read remotely until here
+        }
+        cluster_sync();  // rank 0's claim is read remotely until here
+    }
+
+    // 2. the other heavy tiles
     const uint32_t count = min(hl.w[0], hl.cap_h);
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(hl.w + 1, 1u);
@@ -803,9 +805,9 @@ cudaError_t allow_smem(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-// The launch configuration of k_grid_huge: clusters of kHugeCluster CTAs of
+// The launch configuration of k_grid_heavy: clusters of kHugeCluster CTAs of
 // hw warps (grid: nclusters clusters).
-inline cudaLaunchConfig_t huge_config(cudaLaunchAttribute* at, int hw, size_t smem, int nclusters, cudaStream_t s)
+inline cudaLaunchConfig_t heavy_config(cudaLaunchAttribute* at, int hw, size_t smem, int nclusters, cudaStream_t s)
 {
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = kHugeCluster;
@@ -822,13 +824,13 @@ inline cudaLaunchConfig_t huge_config(cudaLaunchAttribute* at, int hw, size_t sm
 }
 
 // What launch_grid_s<S> sets and queries once per device (and tile side):
-// the shared-memory opt-ins of its three kernels, at the largest size any tile
+// the shared-memory opt-ins of its two kernels, at the largest size any tile
 // side launches them with (the opt-in is a per-kernel ceiling: lowering it for
-// one tile side would fail the launches of another), the co-resident
-// k_grid_heavy CTAs per SM and k_grid_huge clusters.  (Two threads that
-// launch first at the same time both query; the values are the same.)
+// one tile side would fail the launches of another), and the co-resident
+// k_grid_heavy clusters.  (Two threads that launch first at the same time both
+// query; the values are the same.)
 struct GridLaunchInfo {
-    int heavy_per_sm, huge_clusters;
+    int clusters;
 };
 
 template <int S>
@@ -855,18 +857,14 @@ cudaError_t grid_launch_info(int T, size_t tile_bytes, int hw, GridLaunchInfo& o
         }
         if ((e = allow_smem(k_grid_tiles<S>, light_max)) != cudaSuccess) return e;
         if ((e = allow_smem(k_grid_heavy<S>, heavy_max)) != cudaSuccess) return e;
-        if ((e = allow_smem(k_grid_huge<S>, heavy_max)) != cudaSuccess) return e;
         if (cached) opted[dev].store(1, std::memory_order_release);
     }
     const size_t heavy_bytes = tile_bytes * hw;
-    GridLaunchInfo g{0, 0};
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.heavy_per_sm, k_grid_heavy<S>, 32 * hw, heavy_bytes)) !=
-        cudaSuccess)
-        return e;
+    GridLaunchInfo g{0};
     cudaLaunchAttribute at[1];
-    const cudaLaunchConfig_t lc = huge_config(at, hw, heavy_bytes, sm_count_grid(), nullptr);
-    if ((e = cudaOccupancyMaxActiveClusters(&g.huge_clusters, k_grid_huge<S>, &lc)) != cudaSuccess) return e;
-    if (g.huge_clusters < 1 || g.heavy_per_sm < 1) return cudaErrorInvalidConfiguration;
+    const cudaLaunchConfig_t lc = heavy_config(at, hw, heavy_bytes, sm_count_grid(), nullptr);
+    if ((e = cudaOccupancyMaxActiveClusters(&g.clusters, k_grid_heavy<S>, &lc)) != cudaSuccess) return e;
+    if (g.clusters < 1) return cudaErrorInvalidConfiguration;
     if (cached) {
         cache[dev][lt] = g;
         ready[dev][lt].store(1, std::memory_order_release);
@@ -903,18 +901,14 @@ cudaError_t launch_grid_s(const GridCfg& c, const ChunkList& ch, int k0, int nk,
     k_grid_tiles<S><<<tile_blocks, 32 * wl, tile_bytes * wl, s>>>(c, ch, k0, ntl, shift ? 1 : 0, accumulate ? 1 : 0,
                                                                   planes, hl);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // huge tiles: persistent, as many clusters as are co-resident
+    // persistent: as many clusters as are co-resident
     cudaLaunchAttribute at[1];
-    const cudaLaunchConfig_t lc = huge_config(at, hw, heavy_bytes, info.huge_clusters, s);
-    e = cudaLaunchKernelEx(&lc, k_grid_huge<S>, c, ch, k0, shift ? 1 : 0, accumulate ? 1 : 0, planes, hl);
+    const cudaLaunchConfig_t lc = heavy_config(at, hw, heavy_bytes, info.clusters, s);
+    e = cudaLaunchKernelEx(&lc, k_grid_heavy<S>, c, ch, k0, shift ? 1 : 0, accumulate ? 1 : 0, planes, hl);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();  // reported here; not left for the next launch check to find
         return e;
     }
-    // the other heavy tiles: persistent, one CTA per resident slot
-    const unsigned heavy_blocks = (unsigned)(info.heavy_per_sm * sm_count_grid());
-    k_grid_heavy<S><<<heavy_blocks, 32 * hw, heavy_bytes, s>>>(c, ch, k0, shift ? 1 : 0, accumulate ? 1 : 0, planes,
-                                                              hl);
     return cudaGetLastError();
 }
 

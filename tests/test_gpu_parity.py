@@ -317,15 +317,15 @@ def test_hot_tile(rick, oracle_mod):
     _compare(rick, oracle_mod, dict(params=prob["params"], u=u, v=v, w=w, wt=wt, vis=vis), CORRECT | REAL)
 
 
-@pytest.mark.parametrize("chunks,hot", [(1, 2000), (1, 20000), (17, 20000), (17, 300000)])
+@pytest.mark.parametrize("chunks,hot", [(1, 2000), (1, 20000), (17, 20000), (17, 120000)])
 def test_heavy_tile_cta(rick, oracle_mod, chunks, hot):
     """`hot` measurements in a 3 x 3-cell patch, all inside one 32 x 32 tile
     of a 512^2 grid, beside 2e4 spread ones.  2e3 entries: a heavy tile, one
     CTA whose warps grid shares of the entries into private copies summed
-    before the one store; 2e4: a huge tile (more than 8 warps x 2048
-    entries), shared by the 8 CTAs of a cluster, whose sums are added
-    through distributed shared memory.  With 17 grid() calls the last call
-    holds only hot measurements (2353 of 4e4, or 18823 of 3.2e5) and is
+    before the one store; 2e4: a huge tile (more than 8 warps x 512
+    entries), shared by the CTAs of a thread-block cluster, whose sums are
+    added through distributed shared memory.  With 17 grid() calls the last call
+    holds only hot measurements (2353 of 4e4, or 8235 of 1.4e5) and is
     gridded in a pass of its own that adds onto the plane (the heavy or huge
     tile read back and summed onto)."""
     n = 512

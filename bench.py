@@ -15,7 +15,7 @@ the 4096^2 / 32-plane / 1e7-visibility image (256 antennas, 20 km, 6 h,
 dec -30, 200-source sky + noise, Kaiser-Bessel support 7).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload large|wstack|channels|adjoint|small]
+                  [--workload large|wstack|channels|adjoint|small|densechannel]
 
 Multi-GPU (torchrun): one image over all ranks -- every rank takes all
 measurements and transforms and stacks its share of the w-planes, and one
@@ -380,12 +380,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true",
                     help="skip the FP64 oracle (CPU baseline and parity of the timed image)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--workload", choices=["large", "wstack", "channels", "adjoint", "small"], default="large",
+    ap.add_argument("--workload", choices=["large", "wstack", "channels", "adjoint", "small", "densechannel"],
+                    default="large",
                     help="large: 16384^2 / 128 planes / 2e8 measurements with uniform weighting, in plane "
                          "groups (default); wstack: the 4096^2 / 32-plane / 1e7 image; channels: 64 channels "
                          "batched vs imaged one by one; adjoint: image + loss gradient through the adjoint "
                          "degridder on the wstack workload; small: 256^2 / 8 planes / 1e5, microseconds per "
-                         "image")
+                         "image; densechannel: the densest channel of the 64 imaged alone (2048^2 / 16 planes "
+                         "/ 2e7)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -398,6 +400,8 @@ def main():
         return run_adjoint(args, rank, world)
     if args.workload == "small":
         return run_small(args, rank, world)
+    if args.workload == "densechannel":
+        return run_dense_channel(args, rank, world)
     return run_image(args, rank, world)
 
 
@@ -959,6 +963,67 @@ def run_small(args, rank, world):
                    "plane_group": st["plane_group"]},
         "host_us_per_image": host_us, "visibilities_per_s": m / (dev_us / 1e6),
         "gpu_launches_per_image": int(tm["kernel_launches"])}))
+
+
+def run_dense_channel(args, rank, world):
+    """The densest channel of the 64-channel workload imaged alone: 2048^2 x
+    16 w-planes, 2e7 measurements of the same Earth-rotation track (256
+    antennas in a 20 km disk, 6 h of 10 s integrations, dec -30) at its top
+    frequency, 1.75 GHz, with the uv cell set by the longest baseline at 0.45
+    n cells; Kaiser-Bessel support 7.  Most of its gridding entries fall in
+    tiles of hundreds to tens of thousands of entries (the heavy-tile path).
+    Milliseconds per image and the gridding phase, CUDA events."""
+    import torch
+
+    import synth
+    import paper_2504_00959_gb300 as rick
+    from paper_2504_00959_gb300 import build as rick_build
+    rick_build.build()
+    if rank != 0:
+        return
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    prob = synth.earth_rotation_problem(2048, 16, 20_000_000, synth.KERNEL_KB, 7, 256, 20_000.0, 6.0, 10.0, 1.75e9,
+                                        -30.0, synth.BASE_SEED + 5, device=dev)
+    params = dict(prob["params"], flags=synth.FLAG_CORRECT | synth.FLAG_REAL, tile=args.tile)
+    im = rick.Imager(params, device=dev)
+    n, nw = params["n"], params["nw"]
+    m = prob["u"].numel()
+    img = torch.empty((n, n), dtype=torch.float32, device=dev)
+
+    def step():
+        im.reset()
+        im.grid(prob["vis"], prob["u"], prob["v"], prob["w"], prob["wt"])
+        im.image(out=img)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    im.set_timing(False)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(args.steps, 1)
+    s0.record()
+    for _ in range(steps):
+        step()
+    s1.record()
+    torch.cuda.synchronize()
+    ms = s0.elapsed_time(s1) / steps
+    im.set_timing(True)
+    step()
+    torch.cuda.synchronize()
+    tm = im.timing()
+    st = im.stats()
+    im.close()
+    print(json.dumps({
+        "metric": "visibilities per second, one dense 2048^2 x 16-plane channel", "value": m / (ms / 1e3),
+        "unit": "vis/s", "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "dtype": "f32",
+        "data": "synthetic: seeded Earth-rotation track, 200 point sources + N(0, 0.1) noise",
+        "config": {"workload": "densest channel of the 64-channel set alone: 2048x2048 grid, 16 w-planes, "
+                               "2e7 visibilities at 1.75 GHz, Kaiser-Bessel support 7, FP32", "n": n, "nw": nw,
+                   "nvis": m, "tile": st["tile"], "plane_group": st["plane_group"]},
+        "phases_ms": {k: round(tm[k + "_ms"], 4) for k in ("prep", "grid", "fft", "colfft", "stack")},
+        "gpu_launches": int(tm["kernel_launches"])}))
 
 
 def run_reference(args, rank, world):

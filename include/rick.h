@@ -291,8 +291,9 @@ rick_status rick_set_prep_blocks(rick_handle h, int32_t blocks_per_sm);
  * there (the first cudaGetSymbolAddress loads its module), not when the
  * library is loaded, and stays until the process exits; so make the first
  * call before a framework claims the rest of the device heap.  What a call needs -- counters, kernel-tap
- * polynomials, two uint32 arrays of nw * ceil(n/tile)^2 (+1) tile counts and
- * offsets, the scan totals, n*n uint32 of density with RICK_UNIFORM_WEIGHT,
+ * polynomials, the uint32 tile counters (nw * ceil(n/tile)^2 of them, each
+ * padded to up to 32 words while the padded array stays within 2^16 words)
+ * and the tile offsets (nw * ceil(n/tile)^2 + 1 words), the scan totals, n*n uint32 of density with RICK_UNIFORM_WEIGHT,
  * and 64 bytes per measurement (16 when support is 1), each piece 256-byte
  * aligned -- must fit in those 64 MiB; otherwise RICK_ERR_ARG before any
  * launch, with the reason written to err (err_len bytes; err may be NULL).

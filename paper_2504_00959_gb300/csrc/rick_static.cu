@@ -81,6 +81,7 @@ extern "C" rick_status rick_grid_planes_static(const rick_params* p, const float
         set_msg(err, err_len, "%s", msg);
         return s;
     }
+    c.cstride = counter_stride((int64_t)c.nw * c.ntp, kStaticCounterWords);  // the fixed scratch's budget
     if (nvis < 0 || nvis > ((int64_t)1 << 30)) {
         set_msg(err, err_len, "nvis must be in [0, 2^30] (got %lld)", (long long)nvis);
         return RICK_ERR_ARG;

@@ -129,13 +129,18 @@ __device__ __forceinline__ void rmw_pair(uint32_t addr, uint32_t mask, uint32_t 
 // header: the shared address of its first pair, then one word per slot of
 // lane bits saying which lanes' pairs lie inside the tile.
 template <int S>
-struct Stage {
+struct alignas(16) Stage {
     static constexpr int kPairs = LaneSlots<S>::kPairs;
     static constexpr int kSlots = LaneSlots<S>::kSlots;
     static constexpr int kHead = kSlots + 1 <= 2 ? 2 : (kSlots + 1 <= 4 ? 4 : 8);
-    float2 gu[32 * kPairs];
-    float2 gvv[32 * S];
+    // taps stored tap-major with a pitch of kPitch entries: a staging lane's
+    // stores of one tap index are consecutive, and a walking warp's reads of
+    // one entry (its lanes' different tap indices, 2 kPitch words apart) fall
+    // in different banks
+    static constexpr int kPitch = 33;
     uint32_t head[32 * kHead];
+    float2 gu[kPitch * kPairs];
+    float2 gvv[kPitch * S];
 };
 
 // Shared memory of one warp: its tile (T rows of pitch P2 pairs) and its stage.
@@ -172,8 +177,8 @@ struct Staged {
         }
 #pragma unroll
         for (int sl = 0; sl < NS; ++sl) {
-            g2[sl] = st.gu[q * Stage<S>::kPairs + ls.sp[sl]];
-            gq[sl] = st.gvv[q * S + ls.sr[sl]];
+            g2[sl] = st.gu[ls.sp[sl] * Stage<S>::kPitch + q];
+            gq[sl] = st.gvv[ls.sr[sl] * Stage<S>::kPitch + q];
         }
     }
 
@@ -215,7 +220,7 @@ __device__ __forceinline__ void stage_entry(const GridCfg& c, const float4& r, i
             if ((fv + t) & 1) bb = -bb;
         }
         gu[t] = a;
-        st.gvv[slot * S + t] = make_float2(bb * r.z, bb * r.w);
+        st.gvv[t * Stage<S>::kPitch + slot] = make_float2(bb * r.z, bb * r.w);
     }
     // pair t holds tile columns 2 (pu + t) and 2 (pu + t) + 1: taps
     // (2t, 2t+1) for an even start column, (2t-1, 2t) for an odd one
@@ -224,7 +229,7 @@ __device__ __forceinline__ void stage_entry(const GridCfg& c, const float4& r, i
         const float e0 = 2 * t < S ? gu[2 * t < S ? 2 * t : 0] : 0.0f;
         const float e1 = 2 * t + 1 < S ? gu[2 * t + 1 < S ? 2 * t + 1 : 0] : 0.0f;
         const float o0 = 2 * t - 1 >= 0 ? gu[2 * t - 1 >= 0 ? 2 * t - 1 : 0] : 0.0f;
-        st.gu[slot * KP + t] = odd ? make_float2(o0, e0) : make_float2(e0, e1);
+        st.gu[t * Stage<S>::kPitch + slot] = odd ? make_float2(o0, e0) : make_float2(e0, e1);
     }
     // header: first pair's shared address (wraps for footprints that start
     // left of or above the tile; only in-tile pairs are used) and the in-tile
@@ -685,7 +690,7 @@ struct HeavyCta {
         ls.init(lane, p2);
         ltp = c.log2T - 1;
         pmask = (1 << ltp) - 1;
-        wstride = (int)(wbytes / sizeof(float4));  // a Stage is a multiple of 128 bytes
+        wstride = (int)(wbytes / sizeof(float4));  // a Stage is a multiple of 16 bytes
     }
 
     // warp `part` of `parts` grids its share of the entries [b0, e0) (whole

@@ -128,19 +128,24 @@ __device__ __forceinline__ void rmw_pair(uint32_t addr, uint32_t mask, uint32_t 
 // start column), its v taps times the weighted visibility (complex), and a
 // header: the shared address of its first pair, then one word per slot of
 // lane bits saying which lanes' pairs lie inside the tile.
-template <int S>
+//   TM (tap-major, the tiles kernel): taps stored with a pitch of 33
+// entries, so that a staging lane's stores of one tap index are consecutive
+// across the warp and a walking warp's reads of one entry (its lanes'
+// different tap indices, 66 words apart) fall in different banks; entry-major
+// (the heavy-tile kernel) keeps an entry's taps together, which its long
+// walks over full rounds execute in fewer instructions.
+template <int S, bool TM = true>
 struct alignas(16) Stage {
     static constexpr int kPairs = LaneSlots<S>::kPairs;
     static constexpr int kSlots = LaneSlots<S>::kSlots;
     static constexpr int kHead = kSlots + 1 <= 2 ? 2 : (kSlots + 1 <= 4 ? 4 : 8);
-    // taps stored tap-major with a pitch of kPitch entries: a staging lane's
-    // stores of one tap index are consecutive, and a walking warp's reads of
-    // one entry (its lanes' different tap indices, 2 kPitch words apart) fall
-    // in different banks
     static constexpr int kPitch = 33;
     uint32_t head[32 * kHead];
     float2 gu[kPitch * kPairs];
     float2 gvv[kPitch * S];
+    // tap t of staged entry e
+    static __device__ __forceinline__ int gu_at(int e, int t) { return TM ? t * kPitch + e : e * kPairs + t; }
+    static __device__ __forceinline__ int gvv_at(int e, int t) { return TM ? t * kPitch + e : e * S + t; }
 };
 
 // Shared memory of one warp: its tile (T rows of pitch P2 pairs) and its stage.
@@ -152,13 +157,13 @@ __host__ __device__ __forceinline__ size_t warp_smem_bytes(int T)
 
 // One staged entry in registers: its header, and for each of the lane's
 // slots the u tap pair and the complex v tap x visibility.
-template <int S>
+template <int S, bool TM = true>
 struct Staged {
     static constexpr int NS = LaneSlots<S>::kSlots, NH = Stage<S>::kHead;
     uint32_t h[NH];
     float2 g2[NS], gq[NS];
 
-    __device__ __forceinline__ void load(const Stage<S>& st, const LaneSlots<S>& ls, int q)
+    __device__ __forceinline__ void load(const Stage<S, TM>& st, const LaneSlots<S>& ls, int q)
     {
         const uint4* hp = reinterpret_cast<const uint4*>(st.head + q * NH);
         if (NH == 2) {
@@ -177,8 +182,8 @@ struct Staged {
         }
 #pragma unroll
         for (int sl = 0; sl < NS; ++sl) {
-            g2[sl] = st.gu[ls.sp[sl] * Stage<S>::kPitch + q];
-            gq[sl] = st.gvv[ls.sr[sl] * Stage<S>::kPitch + q];
+            g2[sl] = st.gu[Stage<S, TM>::gu_at(q, ls.sp[sl])];
+            gq[sl] = st.gvv[Stage<S, TM>::gvv_at(q, ls.sr[sl])];
         }
     }
 
@@ -194,8 +199,8 @@ struct Staged {
 // stage: its 2S taps (degree-10 polynomials with uniform coefficients from
 // the constant bank, checkerboard signs folded in), the v taps times the
 // visibility, and the header (tile_s: the warp's tile copy).
-template <int S>
-__device__ __forceinline__ void stage_entry(const GridCfg& c, const float4& r, int u0, int v0, Stage<S>& st,
+template <int S, bool TM = true>
+__device__ __forceinline__ void stage_entry(const GridCfg& c, const float4& r, int u0, int v0, Stage<S, TM>& st,
                                             int slot, uint32_t tile_s, int shift)
 {
     constexpr int KP = Stage<S>::kPairs, NS = Stage<S>::kSlots, NH = Stage<S>::kHead;
@@ -220,7 +225,7 @@ __device__ __forceinline__ void stage_entry(const GridCfg& c, const float4& r, i
             if ((fv + t) & 1) bb = -bb;
         }
         gu[t] = a;
-        st.gvv[t * Stage<S>::kPitch + slot] = make_float2(bb * r.z, bb * r.w);
+        st.gvv[Stage<S, TM>::gvv_at(slot, t)] = make_float2(bb * r.z, bb * r.w);
     }
     // pair t holds tile columns 2 (pu + t) and 2 (pu + t) + 1: taps
     // (2t, 2t+1) for an even start column, (2t-1, 2t) for an odd one
@@ -229,7 +234,7 @@ __device__ __forceinline__ void stage_entry(const GridCfg& c, const float4& r, i
         const float e0 = 2 * t < S ? gu[2 * t < S ? 2 * t : 0] : 0.0f;
         const float e1 = 2 * t + 1 < S ? gu[2 * t + 1 < S ? 2 * t + 1 : 0] : 0.0f;
         const float o0 = 2 * t - 1 >= 0 ? gu[2 * t - 1 >= 0 ? 2 * t - 1 : 0] : 0.0f;
-        st.gu[t * Stage<S>::kPitch + slot] = odd ? make_float2(o0, e0) : make_float2(e0, e1);
+        st.gu[Stage<S, TM>::gu_at(slot, t)] = odd ? make_float2(o0, e0) : make_float2(e0, e1);
     }
     // header: first pair's shared address (wraps for footprints that start
     // left of or above the tile; only in-tile pairs are used) and the in-tile
@@ -256,11 +261,11 @@ __device__ __forceinline__ void stage_entry(const GridCfg& c, const float4& r, i
 // Walk the staged entries q0 .. q1-1 into the warp's tile: the next entry's
 // header and taps are loaded before this entry's read-modify-write (two
 // register sets, alternating); a __syncwarp orders consecutive entries.
-template <int S>
-__device__ __forceinline__ void walk_staged(const Stage<S>& st, const LaneSlots<S>& ls, int q0, int q1)
+template <int S, bool TM = true>
+__device__ __forceinline__ void walk_staged(const Stage<S, TM>& st, const LaneSlots<S>& ls, int q0, int q1)
 {
     if (q1 <= q0) return;
-    Staged<S> A, B;
+    Staged<S, TM> A, B;
     A.load(st, ls, q0);
     for (int q = q0;; q += 2) {
         if (q + 1 < q1) B.load(st, ls, q + 1);
@@ -283,9 +288,9 @@ __device__ __forceinline__ void walk_staged(const Stage<S>& st, const LaneSlots<
 // written as one 16-byte value (4 FMAs: u tap pair x complex v
 // tap-visibility product).  Within one entry the lanes' pairs are distinct
 // and conflict-free.  The stage is read-only during the walk.
-template <int S>
+template <int S, bool TM = true>
 __device__ __forceinline__ void warp_grid_range(const GridCfg& c, const float4* __restrict__ ent, uint32_t b,
-                                                uint32_t e, int u0, int v0, float4* tile4, Stage<S>& st,
+                                                uint32_t e, int u0, int v0, float4* tile4, Stage<S, TM>& st,
                                                 const LaneSlots<S>& ls, int lane, int shift)
 {
     const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile4);
@@ -296,9 +301,9 @@ __device__ __forceinline__ void warp_grid_range(const GridCfg& c, const float4* 
         const uint32_t j = j0 + lane;
         const float4 r = r_next;
         if (j + 32 < e) r_next = __ldg(ent + j + 32);
-        if (j < e) stage_entry<S>(c, r, u0, v0, st, lane, tile_s, shift);
+        if (j < e) stage_entry<S, TM>(c, r, u0, v0, st, lane, tile_s, shift);
         __syncwarp();
-        walk_staged<S>(st, ls, 0, (e - j0 < 32u) ? (int)(e - j0) : 32);
+        walk_staged<S, TM>(st, ls, 0, (e - j0 < 32u) ? (int)(e - j0) : 32);
     }
 }
 
@@ -676,7 +681,7 @@ __device__ __forceinline__ void add4(float4& a, const float4& x)
 template <int S>
 struct HeavyCta {
     float4* tile4;
-    Stage<S>* st;
+    Stage<S, false>* st;  // entry-major (the per-warp space is that of the larger layout)
     LaneSlots<S> ls;
     int p2, ltp, pmask, wstride;
 
@@ -685,7 +690,7 @@ struct HeavyCta {
         const size_t wbytes = warp_smem_bytes<S>(c.T);
         unsigned char* mine = reinterpret_cast<unsigned char*>(smem4) + (size_t)wid * wbytes;
         tile4 = reinterpret_cast<float4*>(mine);
-        st = reinterpret_cast<Stage<S>*>(mine + (size_t)c.T * pair_pitch(c.T) * sizeof(float4));
+        st = reinterpret_cast<Stage<S, false>*>(mine + (size_t)c.T * pair_pitch(c.T) * sizeof(float4));
         p2 = pair_pitch(c.T);
         ls.init(lane, p2);
         ltp = c.log2T - 1;
@@ -703,7 +708,7 @@ struct HeavyCta {
         const uint32_t e = min(e0, b0 + 32 * (uint32_t)(((uint64_t)rounds * (part + 1)) / parts));
         init_tile(c, g, nullptr, tile4, false, lane);
         __syncwarp();
-        if (e > b) warp_grid_range<S>(c, ch.ent[0], b, e, g.u0, g.v0, tile4, *st, ls, lane, shift);
+        if (e > b) warp_grid_range<S, false>(c, ch.ent[0], b, e, g.u0, g.v0, tile4, *st, ls, lane, shift);
     }
 };
 

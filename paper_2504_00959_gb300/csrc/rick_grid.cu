@@ -681,7 +681,7 @@ __device__ __forceinline__ void add4(float4& a, const float4& x)
 template <int S>
 struct HeavyCta {
     float4* tile4;
-    Stage<S, false>* st;  // entry-major (the per-warp space is that of the larger layout)
+    Stage<S, false>* st;  // entry-major (both layouts take the same space)
     LaneSlots<S> ls;
     int p2, ltp, pmask, wstride;
 
